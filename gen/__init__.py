@@ -365,7 +365,9 @@ def sync_words(spec: DfaSpec, letters, count: int, seed: int, maxlen: int = 64):
                 if best is None or len(im) < len(best):
                     best, bl = im, li
             if len(best) == len(S):
-                break
+                # no single letter shrinks the set: take a random letter and keep going
+                bl = int(below(d[di % len(d)], len(letters))); di += 1
+                best = np.unique(cols[S, bl])
             S = best
             w.append(bl)
         if len(S) != 1:

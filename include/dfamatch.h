@@ -1,0 +1,245 @@
+/*
+ * dfamatch.h - C ABI of the GB300 speculative chunked DFA membership test.
+ *
+ * The operation is the DFA membership test of Ko, Jung, Han & Burgstaller,
+ * "A Speculative Parallel DFA Membership Test for Multicore, SIMD and Cloud
+ * Computing Environments": given A = (Q, Sigma, delta, q0, F) and a string
+ * Str, compute delta*(q0, Str) and whether it lies in F (Sec. 2.1,
+ * Algorithm 1).  The library computes it with the paper's speculative method
+ * (Algorithm 3): the input is partitioned into chunks (Eqs. 6, 7, 10), every
+ * chunk after the first is matched from each state of the initial-state set
+ * I_sigma of its reverse-lookahead symbol (Eq. 11), and the resulting state
+ * maps are combined in order (Eqs. 8, 9).  The result is identical to
+ * Algorithm 1 for every input (the method is failure-free, Sec. 4.4).
+ *
+ * All entry points return an int status: DFA_OK (0) or a negative DFA_E*
+ * code.  No function throws, exits or prints.  A dfa_t is immutable after
+ * creation and may be used from several host threads at once; a
+ * dfa_server_t is used from one host thread (its worker runs internally).
+ * Device pointers are CUDA device addresses of the current device; "stream"
+ * arguments are cudaStream_t values passed as void* (NULL = legacy default
+ * stream).
+ */
+#ifndef DFAMATCH_H
+#define DFAMATCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define DFA_OK 0
+#define DFA_EINVAL (-1)   /* bad argument: delta entry out of range, q0/finals >= num_states, ... */
+#define DFA_ESYMBOL (-2)  /* an input byte is not in Sigma (byte_to_symbol maps it to 0xFF) */
+#define DFA_ENOMEM (-3)   /* host or device allocation failed */
+#define DFA_ECUDA (-4)    /* a CUDA call failed (no device, launch error, ...) */
+#define DFA_ETIMEOUT (-5) /* a bounded device wait gave up (server only) */
+#define DFA_EBUDGET (-6)  /* server admission refused: request larger than the HBM budget */
+#define DFA_EAGAIN (-7)   /* server: queue full, retry later */
+#define DFA_ENOSPACE (-8) /* caller's workspace is smaller than the size query returned */
+#define DFA_EHOSTONLY (-9)/* the dfa_t was created with dfa_create_host and has no device image */
+
+typedef struct dfa_s dfa_t;
+typedef struct dfa_batch_s dfa_batch_t;
+typedef struct dfa_server_s dfa_server_t;
+
+/* Result of one membership test (12 bytes, also the device-side layout). */
+typedef struct {
+    uint32_t final_state; /* delta*(q0, Str) in the caller's state numbering;
+                             == num_states when the run ended in the implicit
+                             error state q_e (a -1 entry of delta was taken)  */
+    uint8_t accept;       /* 1 iff final_state is in F                          */
+    uint8_t reserved[3];
+    int32_t status;       /* DFA_OK, or DFA_ESYMBOL (then final_state/accept are 0) */
+} dfa_result_t;
+
+/* Static properties of a compiled DFA (Eqs. 11, 12, 18 and the device layout). */
+typedef struct {
+    uint32_t num_states;     /* |Q| as given                                       */
+    uint32_t num_symbols;    /* |Sigma| as given                                   */
+    uint32_t num_states_ext; /* |Q| + 1: the implicit error state q_e is state |Q| */
+    uint32_t num_classes;    /* alphabet classes after merging identical columns   */
+    uint32_t i_max;          /* Eq. (12): max_sigma |I_sigma|                      */
+    uint32_t num_excluded;   /* non-accepting absorbing states left out of every I */
+    uint32_t state_bytes;    /* 1 (uint8 table) or 2 (uint16 table)                */
+    uint32_t placement;      /* 0 = table in shared memory, 1 = table read through L2 */
+    uint32_t states_per_thread; /* chains one thread advances together (planner's K) */
+    uint32_t q0;
+    uint64_t table_bytes;    /* device transition-table image, incl. identity row  */
+    uint64_t device_bytes;   /* all device memory held by this dfa_t               */
+    double gamma;            /* Eq. (18): I_max / |Q|                              */
+    double mean_iset;        /* mean |I_c| over the classes                        */
+} dfa_info_t;
+
+/* Optional per-call planning overrides; pass NULL for the defaults. */
+typedef struct {
+    uint32_t num_chunks;   /* P; 0 = chosen by the planner                         */
+    uint32_t multiplicity; /* the per-chunk state count m in Eqs. (5)-(7)/(10);
+                              0 = 1 (a chunk's states run on parallel lanes)      */
+    uint32_t lookahead;    /* reverse-lookahead symbols r: 1 = Algorithm 3 (default),
+                              0 = Algorithm 2 (every chunk matched from all of Q)  */
+    uint32_t reserved;
+    void *match_begin_event; /* optional cudaEvent_t recorded on the stream right before  */
+    void *match_end_event;   /* ... and right after the match kernel (for timing it alone) */
+} dfa_match_opts_t;
+
+/* ------------------------------------------------------------- DFA objects */
+
+/*
+ * Compile a DFA (Sec. 2.1) and upload it to the current CUDA device.
+ *   delta          num_states*num_symbols int32, row-major: delta[q*num_symbols + a]
+ *                  is the target of state q on symbol a, or -1 for the implicit
+ *                  error state q_e (numbered num_states).  Copied.
+ *   q0             start state, < num_states.
+ *   finals         num_finals accepting states (< num_states, duplicates allowed). Copied.
+ *   byte_to_symbol 256 entries mapping an input byte to a symbol (< num_symbols),
+ *                  or 0xFF for "not in Sigma"; NULL = identity (needs num_symbols == 256).
+ * Limits: 1 <= num_states <= 4095 (a chunk's chains must fit one thread block),
+ * 1 <= num_symbols <= 256.
+ * Compilation (Algorithm 3 lines 1-7, done once): bytes with identical delta
+ * columns share a class; I_c (Eq. 11) and I_max (Eq. 12) are computed; the
+ * class-major table (uint8 states if |Q|+1 <= 256, else uint16) is placed in
+ * shared memory if it fits, otherwise read through L2.
+ * Errors: DFA_EINVAL, DFA_ENOMEM, DFA_ECUDA.  *out is NULL on error.
+ */
+int dfa_create(uint32_t num_states, uint32_t num_symbols, const int32_t *delta, uint32_t q0,
+               const uint32_t *finals, uint32_t num_finals, const uint8_t *byte_to_symbol,
+               dfa_t **out);
+
+/* Same compilation without any CUDA call; the result supports dfa_info,
+ * dfa_class_of_bytes and dfa_iset only (match calls return DFA_EHOSTONLY). */
+int dfa_create_host(uint32_t num_states, uint32_t num_symbols, const int32_t *delta,
+                    uint32_t q0, const uint32_t *finals, uint32_t num_finals,
+                    const uint8_t *byte_to_symbol, dfa_t **out);
+
+/* Free a DFA and its device memory.  NULL is ignored.  No launch may still use it. */
+void dfa_destroy(dfa_t *dfa);
+
+int dfa_info(const dfa_t *dfa, dfa_info_t *out);
+
+/* out[256]: alphabet class of every byte, 0xFFFF for bytes not in Sigma. */
+int dfa_class_of_bytes(const dfa_t *dfa, uint16_t *out);
+
+/* Initial-state set I_c of class c (Eq. 11, ascending state ids), written to
+ * states[0..cap); *count receives |I_c| (even when larger than cap).
+ * c == num_classes returns the start set {q0} used for the first chunk;
+ * c == num_classes + 1 returns all of Q (the set Algorithm 2 matches). */
+int dfa_iset(const dfa_t *dfa, uint32_t c, uint32_t *states, uint32_t cap, uint32_t *count);
+
+/*
+ * Eqs. (6)-(7) with unit weights and per-chunk state count m (Eq. 10):
+ * starts[0] = 0, starts[k] = floor(n*(m+k-1)/(m+P-1)) for 1 <= k < P,
+ * starts[P] = n; chunk k covers [starts[k], starts[k+1]).  starts has P+1
+ * entries, caller-owned.  Host only.  Errors: DFA_EINVAL (P == 0 or m == 0).
+ */
+int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t *starts);
+
+/* ------------------------------------------------------------- matching */
+
+/*
+ * Synchronous membership test.  str may be a host or a device pointer
+ * (detected with cudaPointerGetAttributes); host input is copied to the
+ * device first (asynchronously when the host buffer is pinned).  Runs on the
+ * legacy default stream; its device staging buffer and workspace are kept
+ * per device between calls (grown on demand, calls are serialised by a
+ * lock).  *out is a host struct.  Errors: DFA_EINVAL, DFA_ESYMBOL (also
+ * in out->status), DFA_ENOMEM, DFA_ECUDA, DFA_EHOSTONLY.
+ */
+int dfa_match(const dfa_t *dfa, const uint8_t *str, uint64_t len, const dfa_match_opts_t *opts,
+              dfa_result_t *out);
+
+/* Number of chunks P the planner uses for a single test of len bytes
+ * (opts->num_chunks when given); the partition is then dfa_partition(len, P, m). */
+int dfa_plan_chunks(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts, uint32_t *P);
+
+/* Device workspace needed by dfa_match_async for (dfa, len, opts). */
+int dfa_match_workspace_size(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts,
+                             uint64_t *bytes);
+
+/*
+ * Asynchronous membership test on `stream`: dev_str (device, len bytes) ->
+ * dev_out (one device dfa_result_t).  dev_workspace must hold at least the
+ * size returned by dfa_match_workspace_size; it is owned by the caller and
+ * must not be used by another launch until this one completes.  Launches
+ * only kernels and memsets (no allocation, no host synchronisation), so it
+ * can be captured in a CUDA graph.  A byte outside Sigma is reported in
+ * dev_out->status.  Errors (returned): DFA_EINVAL, DFA_ENOSPACE, DFA_ECUDA.
+ */
+int dfa_match_async(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
+                    const dfa_match_opts_t *opts, dfa_result_t *dev_out, void *dev_workspace,
+                    uint64_t workspace_bytes, void *stream);
+
+/*
+ * Batched membership tests: count independent tests (dfas[i], strs[i],
+ * lens[i]) run in one persistent launch (plus four small planning launches).
+ * dfas may repeat (tests are grouped by DFA); strs are device pointers;
+ * results go to dev_out[0..count) (device).  Host arrays are read before
+ * the call returns; strings must stay valid until the stream reaches the end
+ * of the work.  Allocates and frees its own workspace and synchronises the
+ * stream.  For repeated launches use dfa_batch_prepare / dfa_batch_launch.
+ */
+int dfa_match_batch(uint32_t count, const dfa_t *const *dfas, const uint8_t *const *strs,
+                    const uint64_t *lens, const dfa_match_opts_t *opts, dfa_result_t *dev_out,
+                    void *stream);
+
+/*
+ * Prepared batch: plans the tests on the host (chunk counts per test chosen
+ * from each DFA's tuning record), uploads the descriptors and allocates the
+ * workspace once (synchronous).  dfa_batch_launch then issues only kernels
+ * and memsets on `stream` (capturable); dfa_batch_graph_launch captures the
+ * launch into a CUDA graph on first use and replays it afterwards.  The
+ * dfas and strings must outlive the batch.
+ */
+int dfa_batch_prepare(uint32_t count, const dfa_t *const *dfas, const uint8_t *const *strs,
+                      const uint64_t *lens, const dfa_match_opts_t *opts, dfa_batch_t **out);
+int dfa_batch_launch(dfa_batch_t *batch, dfa_result_t *dev_out, void *stream);
+int dfa_batch_graph_launch(dfa_batch_t *batch, dfa_result_t *dev_out, void *stream);
+/* Optional cudaEvent_t pair recorded around the match kernel by later
+ * dfa_batch_launch calls (NULL, NULL to stop).  Not applied to graph launches. */
+int dfa_batch_set_events(dfa_batch_t *batch, void *match_begin_event, void *match_end_event);
+/* Kernel launches one dfa_batch_launch issues (for accounting). */
+int dfa_batch_num_kernels(const dfa_batch_t *batch, uint32_t *n);
+void dfa_batch_destroy(dfa_batch_t *batch);
+
+/* Human-readable text for a status code (static storage). */
+const char *dfa_strerror(int status);
+
+/* ------------------------------------------------------------- serving */
+
+typedef struct {
+    uint64_t ticket;        /* value returned by dfa_server_submit            */
+    dfa_result_t result;
+    double submit_s;        /* host steady-clock seconds at submission        */
+    double done_s;          /* host seconds when the result was on the host   */
+} dfa_completion_t;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, launches, bytes_matched;
+    uint64_t bytes_in_flight, max_bytes_in_flight;
+} dfa_server_stats_t;
+
+/*
+ * A serving loop on the current device: requests (dfa, host string) are
+ * admitted while the bytes in flight stay within hbm_budget_bytes, grouped
+ * into batches as they arrive and launched on max_inflight streams, so new
+ * requests start while earlier batches still run (continuous batching).
+ * DFAs must stay alive while requests on them are pending.
+ */
+int dfa_server_create(uint64_t hbm_budget_bytes, uint32_t max_inflight, dfa_server_t **out);
+/* Copies str (host memory) into a pinned staging buffer and queues it.
+ * Errors: DFA_EBUDGET (len > budget), DFA_EAGAIN, DFA_EINVAL, DFA_ENOMEM. */
+int dfa_server_submit(dfa_server_t *srv, const dfa_t *dfa, const uint8_t *str, uint64_t len,
+                      uint64_t *ticket);
+/* Moves up to max finished requests into out[0..*n). Non-blocking. */
+int dfa_server_poll(dfa_server_t *srv, dfa_completion_t *out, uint32_t max, uint32_t *n);
+/* Blocks until every submitted request has completed (or timeout_s passes: DFA_ETIMEOUT). */
+int dfa_server_drain(dfa_server_t *srv, double timeout_s);
+int dfa_server_stats(const dfa_server_t *srv, dfa_server_stats_t *out);
+void dfa_server_destroy(dfa_server_t *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFAMATCH_H */

@@ -1,0 +1,658 @@
+// C ABI of libdfamatch (declared in include/dfamatch.h): DFA creation and
+// upload, the planner (partition of Eqs. 6-7/10 and launch layout), and the
+// synchronous, asynchronous and batched match calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "dfa_internal.h"
+
+namespace dfam {
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap);
+int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
+int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
+                uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr);
+
+constexpr uint32_t kTilesPerCta = 8;       // persistent CTAs each get about this many tiles
+constexpr uint64_t kMinChunk = 512;        // bytes; shorter chunks cost more in tile overhead
+constexpr uint64_t kBatchChunk = 8192;     // default chunk length for batched tests
+constexpr uint64_t kMaxChunk = 1ull << 31; // chunk lengths are 32-bit on the device
+
+inline uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t ptot, uint32_t nblk,
+                   uint32_t grid, uint32_t stride, bool inline_desc) {
+    WsLayout w;
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) { uint64_t r = o; o = up(o + bytes, 256); return r; };
+    w.dfas = take(inline_desc ? 0 : sizeof(DevDfa) * ndfa);
+    w.tests = take(inline_desc ? 0 : sizeof(DevTest) * ntests);
+    w.groups = take(inline_desc ? 0 : sizeof(DevGroup) * ngroups);
+    w.chunk_test = take(4ull * ptot);
+    w.chunk_cls = take(2ull * ptot);
+    w.cost = take(4ull * ptot);
+    w.off = take(4ull * (ptot + 1));
+    w.bsum = take(4ull * (nblk + 1));
+    w.tile_first = take(4ull * (ptot + 1));
+    w.tile_base = take(4ull * (ngroups + 1));
+    w.num_tiles = take(4);
+    w.test_err = take(8ull * ntests);  // test_err[ntests] then arrived[ntests]
+    w.first_cta = take(4ull * ntests);
+    w.last_cta = take(4ull * ntests);
+    w.seg_hdr = take(16ull * (grid + ntests));
+    w.seg_vals = take(2ull * stride * (grid + ntests));
+    w.total = o;
+    return w;
+}
+
+void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
+    lp.chunk_test = reinterpret_cast<uint32_t*>(base + w.chunk_test);
+    lp.chunk_cls = reinterpret_cast<uint16_t*>(base + w.chunk_cls);
+    lp.cost = reinterpret_cast<uint32_t*>(base + w.cost);
+    lp.off = reinterpret_cast<uint32_t*>(base + w.off);
+    lp.bsum = reinterpret_cast<uint32_t*>(base + w.bsum);
+    lp.tile_first = reinterpret_cast<uint32_t*>(base + w.tile_first);
+    lp.tile_base = reinterpret_cast<uint32_t*>(base + w.tile_base);
+    lp.num_tiles = reinterpret_cast<uint32_t*>(base + w.num_tiles);
+    lp.test_err = reinterpret_cast<uint32_t*>(base + w.test_err);
+    lp.arrived = lp.test_err + lp.ntests;
+    lp.first_cta = reinterpret_cast<uint32_t*>(base + w.first_cta);
+    lp.last_cta = reinterpret_cast<uint32_t*>(base + w.last_cta);
+    lp.seg_hdr = reinterpret_cast<uint32_t*>(base + w.seg_hdr);
+    lp.seg_vals = reinterpret_cast<uint16_t*>(base + w.seg_vals);
+}
+
+// Launch-specific copy of a DFA's device descriptor.
+DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
+    DevDfa x = d->dev;
+    const uint32_t vmax = lookahead ? std::max(d->h.imax, 1u) : d->h.qe;
+    x.cost_max = std::max((vmax + x.K - 1) / x.K, 2u);
+    x.vcap = vmax;
+    return x;
+}
+
+// Chunk count for one test (Sec. 4.1's partition is applied per test with P chunks).
+uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_opts_t* o,
+                     bool batched) {
+    uint64_t P;
+    if (o && o->num_chunks) {
+        P = o->num_chunks;
+    } else if (batched) {
+        uint64_t L = d->tuned_chunk_len ? d->tuned_chunk_len : kBatchChunk;
+        P = (n + L - 1) / L;
+    } else {
+        // enough lane tasks for kTilesPerCta tiles on every CTA, chunks >= kMinChunk
+        double mean_cost = 0;
+        const HostDfa& h = d->h;
+        for (uint32_t c = 0; c < h.C; ++c) {
+            uint32_t sz = h.iset_off[c + 1] - h.iset_off[c];
+            mean_cost += std::max((sz + h.K - 1) / h.K, 2u);
+        }
+        mean_cost = h.C ? mean_cost / h.C : 2.0;
+        double want = (double)grid * kThreads * kTilesPerCta * 0.9 / mean_cost;
+        uint64_t by_len = n / (d->tuned_chunk_len ? d->tuned_chunk_len : kMinChunk);
+        P = std::min<uint64_t>((uint64_t)want, by_len);
+    }
+    P = std::max<uint64_t>(P, (n + kMaxChunk - 1) / kMaxChunk);
+    P = std::max<uint64_t>(P, 1);
+    P = std::min<uint64_t>(P, 1ull << 30);
+    return (uint32_t)P;
+}
+
+int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
+            const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out) {
+    if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
+    const uint32_t lookahead = opts ? (opts->lookahead == 0 ? 0u : 1u) : 1u;
+    const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
+    Prepared p;
+    // group tests by DFA (stable), unique DFAs in first-seen order
+    std::map<const dfa_t*, uint32_t> idx;
+    std::vector<const dfa_t*> uniq;
+    for (uint32_t i = 0; i < count; ++i) {
+        const dfa_t* d = dfas[i];
+        if (!d) return DFA_EINVAL;
+        if (!d->on_device) return DFA_EHOSTONLY;
+        if (lens[i] && !strs[i]) return DFA_EINVAL;
+        if (!lookahead && d->h.qe > 4096) return DFA_EINVAL;
+        if (!idx.count(d)) {
+            idx[d] = (uint32_t)uniq.size();
+            uniq.push_back(d);
+        }
+    }
+    for (const dfa_t* d : uniq) {
+        DevDfa x = launch_desc(d, lookahead);
+        p.dfas.push_back(x);
+        p.kmax = std::max(p.kmax, x.K);
+        p.vcap = std::max(p.vcap, x.vcap);
+        if (x.placement == kSmem) p.table_cap = std::max(p.table_cap, (uint32_t)up(x.table_bytes, 16));
+    }
+    p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap);
+    int rc = match_grid(p.smem, p.kmax, &p.grid);
+    if (rc != DFA_OK) return rc;
+    std::vector<uint32_t> order(count);
+    for (uint32_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return idx[dfas[a]] < idx[dfas[b]]; });
+    uint64_t chunks = 0;
+    for (uint32_t j = 0; j < count; ++j) {
+        const uint32_t i = order[j];
+        const dfa_t* d = dfas[i];
+        DevTest t{};
+        t.str = strs[i];
+        t.n = lens[i];
+        t.dfa = idx[d];
+        t.P = plan_chunks(d, lens[i], p.grid, opts, batched);
+        t.m = m;
+        t.chunk_base = (uint32_t)chunks;
+        t.lookahead = lookahead;
+        t.out = i;
+        if (p.groups.empty() || p.groups.back().dfa != t.dfa) {
+            DevGroup g{};
+            g.first_chunk = (uint32_t)chunks;
+            g.dfa = t.dfa;
+            g.first_test = j;
+            p.groups.push_back(g);
+        }
+        t.group = (uint32_t)p.groups.size() - 1;
+        chunks += t.P;
+        p.groups.back().end_chunk = (uint32_t)chunks;
+        if (chunks > 0xF0000000ull) return DFA_EINVAL;
+        p.tests.push_back(t);
+    }
+    p.ptot = (uint32_t)chunks;
+    p.nblk = (p.ptot + 1023) / 1024;
+    p.ws = ws_layout((uint32_t)p.dfas.size(), count, (uint32_t)p.groups.size(), p.ptot, p.nblk,
+                     p.grid, p.vcap, false);
+    *out = std::move(p);
+    return DFA_OK;
+}
+
+void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out) {
+    std::memset(&lp, 0, sizeof lp);
+    lp.ntests = (uint32_t)p.tests.size();
+    lp.ngroups = (uint32_t)p.groups.size();
+    lp.ptot = p.ptot;
+    lp.nblk = p.nblk;
+    lp.grid = p.grid;
+    lp.seg_stride = p.vcap;
+    lp.smem_table_cap = p.table_cap;
+    lp.vcap = p.vcap;
+    lp.dfas = reinterpret_cast<const DevDfa*>(ws + p.ws.dfas);
+    lp.tests = reinterpret_cast<const DevTest*>(ws + p.ws.tests);
+    lp.groups = reinterpret_cast<const DevGroup*>(ws + p.ws.groups);
+    bind(lp, ws, p.ws);
+    lp.results = out;
+}
+
+int upload_desc(const Prepared& p, uint8_t* ws) {
+    if (cudaMemcpy(ws + p.ws.dfas, p.dfas.data(), sizeof(DevDfa) * p.dfas.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ws + p.ws.tests, p.tests.data(), sizeof(DevTest) * p.tests.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ws + p.ws.groups, p.groups.data(), sizeof(DevGroup) * p.groups.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return DFA_ECUDA;
+    return DFA_OK;
+}
+
+int upload_desc_async(const Prepared& p, uint8_t* ws, uint8_t* pinned, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // pinned holds a host copy laid out like the workspace's descriptor area
+    const uint64_t nd = sizeof(DevDfa) * p.dfas.size(), nt = sizeof(DevTest) * p.tests.size(),
+                   ng = sizeof(DevGroup) * p.groups.size();
+    std::memcpy(pinned + p.ws.dfas, p.dfas.data(), nd);
+    std::memcpy(pinned + p.ws.tests, p.tests.data(), nt);
+    std::memcpy(pinned + p.ws.groups, p.groups.data(), ng);
+    const uint64_t span = p.ws.groups + ng;
+    return cudaMemcpyAsync(ws, pinned, span, cudaMemcpyHostToDevice, st) == cudaSuccess ? DFA_OK
+                                                                                          : DFA_ECUDA;
+}
+
+uint64_t desc_span(const Prepared& p) { return p.ws.groups + sizeof(DevGroup) * p.groups.size(); }
+
+int launch_prepared(const Prepared& p, uint8_t* ws, dfa_result_t* out, void* stream) {
+    LaunchPlan lp;
+    fill_plan(p, lp, ws, out);
+    return launch_plan(lp, p.kmax, p.smem, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+namespace {
+
+// Single-test plan with descriptors carried by value (no upload needed).
+struct Single {
+    LaunchPlan lp;
+    WsLayout ws;
+    uint32_t smem, kmax;
+};
+
+int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Single* s) {
+    if (!d) return DFA_EINVAL;
+    if (!d->on_device) return DFA_EHOSTONLY;
+    const uint32_t lookahead = opts ? (opts->lookahead == 0 ? 0u : 1u) : 1u;
+    if (!lookahead && d->h.qe > 4096) return DFA_EINVAL;
+    const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
+    DevDfa x = launch_desc(d, lookahead);
+    const uint32_t tcap = x.placement == kSmem ? (uint32_t)up(x.table_bytes, 16) : 0u;
+    s->kmax = x.K;
+    s->smem = match_smem_bytes(tcap, x.K, x.vcap);
+    uint32_t grid = 0;
+    int rc = match_grid(s->smem, s->kmax, &grid);
+    if (rc != DFA_OK) return rc;
+    const uint32_t P = plan_chunks(d, len, grid, opts, false);
+    LaunchPlan& lp = s->lp;
+    std::memset(&lp, 0, sizeof lp);
+    lp.ntests = 1;
+    lp.ngroups = 1;
+    lp.ptot = P;
+    lp.nblk = (P + 1023) / 1024;
+    lp.grid = grid;
+    lp.seg_stride = x.vcap;
+    lp.smem_table_cap = tcap;
+    lp.vcap = x.vcap;
+    lp.dfas = d->dev_desc_for(lookahead);
+    lp.tests = nullptr;
+    lp.groups = nullptr;
+    lp.test1.str = nullptr;
+    lp.test1.n = len;
+    lp.test1.dfa = 0;
+    lp.test1.P = P;
+    lp.test1.m = m;
+    lp.test1.chunk_base = 0;
+    lp.test1.group = 0;
+    lp.test1.lookahead = lookahead;
+    lp.test1.out = 0;
+    lp.group1.first_chunk = 0;
+    lp.group1.end_chunk = P;
+    lp.group1.dfa = 0;
+    lp.group1.first_test = 0;
+    s->ws = ws_layout(1, 1, 1, P, lp.nblk, grid, x.vcap, true);
+    return DFA_OK;
+}
+
+}  // namespace
+}  // namespace dfam
+
+using namespace dfam;
+
+// ------------------------------------------------------------------ dfa_t
+
+const DevDfa* dfa_s::dev_desc_for(uint32_t lookahead) const {
+    return lookahead ? dev_desc : dev_desc + 1;
+}
+
+static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0,
+                         const uint32_t* finals, uint32_t nf, const uint8_t* b2s, bool device,
+                         dfa_t** out) {
+    if (!out) return DFA_EINVAL;
+    *out = nullptr;
+    dfa_t* d = new (std::nothrow) dfa_t();
+    if (!d) return DFA_ENOMEM;
+    int rc = compile_dfa(Q, S, delta, q0, finals, nf, b2s, &d->h);
+    if (rc != DFA_OK) {
+        delete d;
+        return rc;
+    }
+    const HostDfa& h = d->h;
+    // device-side descriptor (pointers filled below)
+    DevDfa& x = d->dev;
+    std::memset(&x, 0, sizeof x);
+    x.qe = h.qe;
+    x.qpad = h.qpad;
+    x.C = h.C;
+    x.sb = h.sb;
+    x.placement = h.placement;
+    x.table_bytes = (uint32_t)h.table.size();
+    x.q0 = h.q0;
+    x.imax = h.imax;
+    x.K = h.K;
+    if (device) {
+        if (cudaGetDevice(&d->device) != cudaSuccess) {
+            delete d;
+            return DFA_ECUDA;
+        }
+        uint64_t o = 0;
+        auto take = [&](uint64_t bytes) { uint64_t r = o; o = up(o + bytes, 256); return r; };
+        const uint64_t o_desc = take(2 * sizeof(DevDfa));
+        const uint64_t o_table = take(h.table.size());
+        const uint64_t o_b16 = take(512), o_b32 = take(1024), o_bc = take(512);
+        const uint64_t o_ioff = take(4 * h.iset_off.size()), o_iset = take(2 * h.iset.size());
+        const uint64_t o_pos = take(2 * h.pos.size()), o_acc = take(h.accept.size());
+        uint8_t* blk = nullptr;
+        if (cudaMalloc(&blk, o) != cudaSuccess) {
+            cudaGetLastError();
+            delete d;
+            return DFA_ENOMEM;
+        }
+        d->dev_block = blk;
+        d->dev_bytes = o;
+        x.table = blk + o_table;
+        x.byte_off16 = reinterpret_cast<const uint16_t*>(blk + o_b16);
+        x.byte_off32 = reinterpret_cast<const uint32_t*>(blk + o_b32);
+        x.byte_class = reinterpret_cast<const uint16_t*>(blk + o_bc);
+        x.iset_off = reinterpret_cast<const uint32_t*>(blk + o_ioff);
+        x.iset = reinterpret_cast<const uint16_t*>(blk + o_iset);
+        x.pos = reinterpret_cast<const uint16_t*>(blk + o_pos);
+        x.accept = blk + o_acc;
+        d->dev_desc = reinterpret_cast<DevDfa*>(blk + o_desc);
+        DevDfa descs[2] = {launch_desc(d, 1), launch_desc(d, 0)};
+        bool ok = cudaMemcpy(blk + o_desc, descs, sizeof descs, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_table, h.table.data(), h.table.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_b16, h.byte_off16.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_b32, h.byte_off32.data(), 1024, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_bc, h.byte_class.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_ioff, h.iset_off.data(), 4 * h.iset_off.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_iset, h.iset.data(), 2 * h.iset.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_pos, h.pos.data(), 2 * h.pos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_acc, h.accept.data(), h.accept.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        if (!ok) {
+            cudaFree(blk);
+            delete d;
+            return DFA_ECUDA;
+        }
+        d->on_device = true;
+    }
+    *out = d;
+    return DFA_OK;
+}
+
+extern "C" {
+
+int dfa_create(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const uint32_t* finals,
+               uint32_t nf, const uint8_t* b2s, dfa_t** out) {
+    return create_common(Q, S, delta, q0, finals, nf, b2s, true, out);
+}
+
+int dfa_create_host(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0,
+                    const uint32_t* finals, uint32_t nf, const uint8_t* b2s, dfa_t** out) {
+    return create_common(Q, S, delta, q0, finals, nf, b2s, false, out);
+}
+
+void dfa_destroy(dfa_t* d) {
+    if (!d) return;
+    if (d->dev_block) cudaFree(d->dev_block);
+    delete d;
+}
+
+int dfa_info(const dfa_t* d, dfa_info_t* o) {
+    if (!d || !o) return DFA_EINVAL;
+    const HostDfa& h = d->h;
+    std::memset(o, 0, sizeof *o);
+    o->num_states = h.Q;
+    o->num_symbols = h.S;
+    o->num_states_ext = h.qe;
+    o->num_classes = h.C;
+    o->i_max = h.imax;
+    o->num_excluded = h.num_excluded;
+    o->state_bytes = h.sb;
+    o->placement = h.placement;
+    o->states_per_thread = h.K;
+    o->q0 = h.q0;
+    o->table_bytes = h.table.size();
+    o->device_bytes = d->dev_bytes;
+    o->gamma = h.gamma;
+    o->mean_iset = h.mean_iset;
+    return DFA_OK;
+}
+
+int dfa_class_of_bytes(const dfa_t* d, uint16_t* out) {
+    if (!d || !out) return DFA_EINVAL;
+    std::memcpy(out, d->h.byte_class.data(), 512);
+    return DFA_OK;
+}
+
+int dfa_iset(const dfa_t* d, uint32_t c, uint32_t* states, uint32_t cap, uint32_t* count) {
+    if (!d || !count || c > d->h.C + 1) return DFA_EINVAL;
+    const HostDfa& h = d->h;
+    const uint32_t a = h.iset_off[c], b = h.iset_off[c + 1];
+    *count = b - a;
+    for (uint32_t i = 0; i < b - a && i < cap; ++i) states[i] = h.iset[a + i];
+    return DFA_OK;
+}
+
+int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t* starts) {
+    if (P == 0 || m == 0 || !starts) return DFA_EINVAL;
+    for (uint32_t k = 0; k <= P; ++k) starts[k] = chunk_start(n, P, m, k);
+    return DFA_OK;
+}
+
+int dfa_match_workspace_size(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts,
+                             uint64_t* bytes) {
+    if (!bytes) return DFA_EINVAL;
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    *bytes = s.ws.total;
+    return DFA_OK;
+}
+
+int dfa_match_async(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
+                    const dfa_match_opts_t* opts, dfa_result_t* dev_out, void* ws,
+                    uint64_t ws_bytes, void* stream) {
+    if (!dev_out || (len && !dev_str) || !ws) return DFA_EINVAL;
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    if (ws_bytes < s.ws.total) return DFA_ENOSPACE;
+    s.lp.test1.str = dev_str;
+    bind(s.lp, static_cast<uint8_t*>(ws), s.ws);
+    s.lp.results = dev_out;
+    return launch_plan(s.lp, s.kmax, s.smem, static_cast<cudaStream_t>(stream), nullptr,
+                       opts ? opts->match_begin_event : nullptr,
+                       opts ? opts->match_end_event : nullptr);
+}
+
+// Per-device buffers of the synchronous path (grown on demand, never shrunk).
+struct SyncBuffers {
+    std::mutex mu;
+    uint8_t* str = nullptr;
+    uint64_t str_cap = 0;
+    uint8_t* ws = nullptr;
+    uint64_t ws_cap = 0;
+};
+static SyncBuffers g_sync[64];
+
+static int grow_dev(uint8_t** p, uint64_t* cap, uint64_t need) {
+    if (*cap >= need) return DFA_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return DFA_ENOMEM;
+    }
+    *cap = need;
+    return DFA_OK;
+}
+
+int dfa_plan_chunks(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, uint32_t* P) {
+    if (!P) return DFA_EINVAL;
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    *P = s.lp.ptot;
+    return DFA_OK;
+}
+
+int dfa_match(const dfa_t* d, const uint8_t* str, uint64_t len, const dfa_match_opts_t* opts,
+              dfa_result_t* out) {
+    if (!d || !out || (len && !str)) return DFA_EINVAL;
+    if (!d->on_device) return DFA_EHOSTONLY;
+    bool on_dev = false;
+    if (len) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, str) == cudaSuccess)
+            on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+        cudaGetLastError();
+    }
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DFA_ECUDA;
+    SyncBuffers& B = g_sync[dev];
+    std::lock_guard<std::mutex> lock(B.mu);
+    const uint8_t* use = str;
+    if (len && !on_dev) {
+        if ((rc = grow_dev(&B.str, &B.str_cap, len)) != DFA_OK) return rc;
+        if (cudaMemcpyAsync(B.str, str, len, cudaMemcpyHostToDevice, 0) != cudaSuccess)
+            return DFA_ECUDA;
+        use = B.str;
+    }
+    if ((rc = grow_dev(&B.ws, &B.ws_cap, s.ws.total + 256)) != DFA_OK) return rc;
+    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(B.ws + s.ws.total);
+    s.lp.test1.str = use;
+    bind(s.lp, B.ws, s.ws);
+    s.lp.results = dres;
+    rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr,
+                     opts ? opts->match_begin_event : nullptr, opts ? opts->match_end_event : nullptr);
+    if (rc == DFA_OK && cudaMemcpy(out, dres, sizeof *out, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = DFA_ECUDA;
+    if (rc == DFA_OK && out->status != DFA_OK) rc = out->status;
+    return rc;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct dfa_batch_s {
+    Prepared p;
+    uint8_t* ws = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    dfa_result_t* graph_out = nullptr;
+    void* ev_begin = nullptr;
+    void* ev_end = nullptr;
+};
+
+extern "C" {
+
+int dfa_batch_prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
+                      const uint64_t* lens, const dfa_match_opts_t* opts, dfa_batch_t** out) {
+    if (!out) return DFA_EINVAL;
+    *out = nullptr;
+    dfa_batch_t* b = new (std::nothrow) dfa_batch_t();
+    if (!b) return DFA_ENOMEM;
+    int rc = prepare(count, dfas, strs, lens, opts, true, &b->p);
+    if (rc != DFA_OK) {
+        delete b;
+        return rc;
+    }
+    if (cudaMalloc(&b->ws, b->p.ws.total) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return DFA_ENOMEM;
+    }
+    rc = upload_desc(b->p, b->ws);
+    if (rc != DFA_OK) {
+        cudaFree(b->ws);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return DFA_OK;
+}
+
+int dfa_batch_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) {
+    if (!b || !dev_out) return DFA_EINVAL;
+    LaunchPlan lp;
+    fill_plan(b->p, lp, b->ws, dev_out);
+    return launch_plan(lp, b->p.kmax, b->p.smem, static_cast<cudaStream_t>(stream), nullptr,
+                       b->ev_begin, b->ev_end);
+}
+
+int dfa_batch_set_events(dfa_batch_t* b, void* ev_begin, void* ev_end) {
+    if (!b) return DFA_EINVAL;
+    b->ev_begin = ev_begin;
+    b->ev_end = ev_end;
+    return DFA_OK;
+}
+
+int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) {
+    if (!b || !dev_out) return DFA_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!b->exec || b->graph_out != dev_out) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        cudaStream_t cap = st;
+        bool own = false;
+        if (!cap) {  // the legacy default stream cannot be captured
+            if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return DFA_ECUDA;
+            own = true;
+        }
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            if (own) cudaStreamDestroy(cap);
+            return DFA_ECUDA;
+        }
+        LaunchPlan lp;
+        fill_plan(b->p, lp, b->ws, dev_out);
+        int rc = launch_plan(lp, b->p.kmax, b->p.smem, cap, nullptr);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap, &g);
+        if (own) cudaStreamDestroy(cap);
+        if (rc != DFA_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return DFA_ECUDA;
+        }
+        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return DFA_ECUDA;
+        }
+        b->graph = g;
+        b->graph_out = dev_out;
+    }
+    return cudaGraphLaunch(b->exec, st) == cudaSuccess ? DFA_OK : DFA_ECUDA;
+}
+
+int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
+    if (!b || !n) return DFA_EINVAL;
+    *n = 6;
+    return DFA_OK;
+}
+
+void dfa_batch_destroy(dfa_batch_t* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ws) cudaFree(b->ws);
+    delete b;
+}
+
+int dfa_match_batch(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
+                    const uint64_t* lens, const dfa_match_opts_t* opts, dfa_result_t* dev_out,
+                    void* stream) {
+    dfa_batch_t* b = nullptr;
+    int rc = dfa_batch_prepare(count, dfas, strs, lens, opts, &b);
+    if (rc != DFA_OK) return rc;
+    rc = dfa_batch_launch(b, dev_out, stream);
+    if (rc == DFA_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        rc = DFA_ECUDA;
+    dfa_batch_destroy(b);
+    return rc;
+}
+
+const char* dfa_strerror(int s) {
+    switch (s) {
+        case DFA_OK: return "ok";
+        case DFA_EINVAL: return "invalid argument";
+        case DFA_ESYMBOL: return "input byte not in the alphabet";
+        case DFA_ENOMEM: return "out of memory";
+        case DFA_ECUDA: return "CUDA error";
+        case DFA_ETIMEOUT: return "timed out";
+        case DFA_EBUDGET: return "request exceeds the memory budget";
+        case DFA_EAGAIN: return "try again";
+        case DFA_ENOSPACE: return "workspace too small";
+        case DFA_EHOSTONLY: return "DFA has no device image";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Internal structures of libdfamatch: the compiled DFA (host and device
+// images), per-launch plans and the kernel launchers.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dfamatch.h"
+
+namespace dfam {
+
+// ------------------------------------------------------------------ tuning
+constexpr int kThreads = 512;            // threads per CTA of the match kernel
+constexpr int kMaxChunksPerTile = kThreads / 2;  // every chunk is charged >= 2 thread slots
+constexpr int kStageBytes = 16384;       // one staging buffer of class-row offsets
+constexpr int kMaxSegLen = 1024;         // longest staged segment per chunk (positions)
+constexpr uint16_t kNone16 = 0xFFFF;     // "not a member" in pos tables / invalid byte
+constexpr uint32_t kNone32 = 0xFFFFFFFFu;
+constexpr uint32_t kSmemTableMax = 112 * 1024;  // tables larger than this are read through L2
+constexpr uint32_t kMaxStates = 4095;    // |Q| limit: a chunk's chains (|I| <= |Q|+1) fit one tile at K=16
+
+enum Placement : uint32_t { kSmem = 0, kGlobal = 1 };
+
+// ------------------------------------------------------- device DFA image
+// Everything the kernels read about one DFA.  Pointers are device pointers.
+struct DevDfa {
+    const uint8_t* table;        // (C+1) rows x qpad entries of sb bytes; entry = next_state*sb;
+                                 // row C is the identity row used to pad chunk tails
+    const uint16_t* byte_off16;  // [256] byte -> row byte offset c*qpad*sb (kNone16: not in Sigma)
+    const uint32_t* byte_off32;  // [256] same, 32-bit (global placement)
+    const uint16_t* byte_class;  // [256] byte -> class (kNone16: not in Sigma)
+    const uint32_t* iset_off;    // [C+3] CSR offsets; set C = start set {q0}, set C+1 = all of Q
+    const uint16_t* iset;        // CSR members (ascending)
+    const uint16_t* pos;         // [(C+2)*qe] index of state s in set c, kNone16 if absent
+    const uint8_t* accept;       // [qe] 1 iff accepting
+    uint32_t qe;                 // states incl. q_e
+    uint32_t qpad;               // row stride (entries)
+    uint32_t C;                  // classes (without the start set)
+    uint32_t sb;                 // bytes per table entry (1 or 2)
+    uint32_t placement;          // Placement
+    uint32_t table_bytes;        // (C+1)*qpad*sb
+    uint32_t q0;
+    uint32_t imax;               // Eq. (12) over real classes
+    uint32_t K;                  // states per thread
+    uint32_t cost_max;           // max thread slots one chunk can need: max(ceil(|I|/K), 2)
+    uint32_t vcap;               // largest set size (incl. start set) = capacity of a state map
+    uint32_t pad_;
+};
+
+// One membership test of a launch.
+struct DevTest {
+    const uint8_t* str;
+    uint64_t n;
+    uint32_t dfa;         // index into the launch's DevDfa array
+    uint32_t P;           // chunks
+    uint32_t m;           // multiplicity of Eq. (10) used in the partition
+    uint32_t chunk_base;  // global index of its chunk 0
+    uint32_t group;       // run of consecutive tests sharing one DFA
+    uint32_t lookahead;   // 1: Algorithm 3, 0: Algorithm 2 (all states)
+    uint32_t out;         // index of its result in the caller's output array
+    uint32_t pad_;
+};
+static_assert(sizeof(DevTest) == 48, "DevTest layout");
+
+struct DevGroup {
+    uint32_t first_chunk, end_chunk, dfa, first_test;
+};
+
+// Device-side result (layout identical to dfa_result_t).
+static_assert(sizeof(dfa_result_t) == 12, "dfa_result_t layout");
+
+// Per-launch device workspace (all pointers into one caller-provided block).
+struct LaunchPlan {
+    const DevDfa* dfas;
+    const DevTest* tests;
+    const DevGroup* groups;
+    uint32_t ntests, ngroups, ptot, nblk;
+    uint32_t grid;              // CTAs of the match kernel
+    uint32_t seg_stride;        // entries per segment map
+    uint32_t smem_table_cap;    // bytes reserved for a shared-memory table
+    uint32_t vcap;              // entries reserved for the running map
+    uint32_t* chunk_test;       // [ptot]
+    uint16_t* chunk_cls;        // [ptot]
+    uint32_t* cost;             // [ptot] thread slots charged to the chunk
+    uint32_t* off;              // [ptot+1] exclusive prefix of cost (within the launch)
+    uint32_t* bsum;             // [nblk+1]
+    uint32_t* tile_first;       // [ptot+1]
+    uint32_t* tile_base;        // [ngroups+1]
+    uint32_t* num_tiles;        // [1]
+    uint32_t* test_err;         // [ntests]
+    uint32_t* arrived;          // [ntests]
+    uint32_t* first_cta;        // [ntests]
+    uint32_t* last_cta;         // [ntests]
+    uint32_t* seg_hdr;          // [(grid+ntests)*4]: first chunk, nchunks, class, size
+    uint16_t* seg_vals;         // [(grid+ntests)*seg_stride]
+    dfa_result_t* results;      // [ntests] in the caller's order (DevTest::out)
+    // single-test launches carry their descriptors by value (tests/groups == nullptr)
+    DevTest test1;
+    DevGroup group1;
+};
+
+// Workspace carve-up of one launch (byte offsets into the device workspace).
+struct WsLayout {
+    uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, bsum, tile_first, tile_base,
+        num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, total;
+};
+
+// A batch planned on the host: descriptors, sizes and the workspace layout.
+struct Prepared {
+    std::vector<DevDfa> dfas;
+    std::vector<DevTest> tests;
+    std::vector<DevGroup> groups;
+    uint32_t ptot = 0, nblk = 0, grid = 0, kmax = 2, vcap = 1, table_cap = 0, smem = 0;
+    WsLayout ws{};
+};
+
+// ------------------------------------------------------------ host image
+struct HostDfa {
+    uint32_t Q = 0, S = 0, qe = 0, q0 = 0, C = 0, qpad = 0, sb = 0;
+    uint32_t imax = 0, num_excluded = 0, placement = kSmem, K = 4;
+    double gamma = 0, mean_iset = 0;
+    std::vector<uint16_t> byte_class;   // 256, kNone16 = not in Sigma
+    std::vector<uint8_t> accept;        // qe
+    std::vector<uint8_t> excluded;      // qe
+    std::vector<uint32_t> iset_off;     // C+3
+    std::vector<uint16_t> iset;
+    std::vector<uint16_t> pos;          // (C+2)*qe
+    std::vector<uint8_t> table;         // (C+1)*qpad*sb
+    std::vector<uint16_t> byte_off16;   // 256
+    std::vector<uint32_t> byte_off32;   // 256
+};
+
+// Compile (validation, classes, excluded states, I sets, table image).
+int compile_dfa(uint32_t num_states, uint32_t num_symbols, const int32_t* delta, uint32_t q0,
+                const uint32_t* finals, uint32_t num_finals, const uint8_t* byte_to_symbol,
+                HostDfa* out);
+
+uint64_t chunk_start(uint64_t n, uint32_t P, uint32_t m, uint32_t k);
+
+}  // namespace dfam
+
+struct dfa_s;
+namespace dfam {
+// Batch planning and launching (dfa_api.cu), shared with the serving loop.
+int prepare(uint32_t count, const dfa_s* const* dfas, const uint8_t* const* strs,
+            const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out);
+void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out);
+int upload_desc_async(const Prepared& p, uint8_t* ws, uint8_t* pinned, void* stream);
+uint64_t desc_span(const Prepared& p);
+int launch_prepared(const Prepared& p, uint8_t* ws, dfa_result_t* out, void* stream);
+}  // namespace dfam
+
+// The opaque handle of the C ABI.
+struct dfa_s {
+    dfam::HostDfa h;
+    bool on_device = false;
+    int device = -1;
+    void* dev_block = nullptr;       // one allocation holding every device array
+    uint64_t dev_bytes = 0;
+    dfam::DevDfa dev;                // pointers into dev_block
+    dfam::DevDfa* dev_desc = nullptr;  // device copies of `dev` for launches with lookahead 1 and 0
+    const dfam::DevDfa* dev_desc_for(uint32_t lookahead) const;
+    uint32_t tuned_chunk_len = 0;    // preferred chunk length (0 = planner default)
+};

@@ -1,0 +1,681 @@
+// Device side of the speculative chunked DFA membership test (sm_103a).
+//
+// A launch covers `ntests` independent membership tests.  Work flows through
+// five planning kernels and one persistent match kernel, all on one stream:
+//
+//   k_count        per chunk: test, reverse-lookahead class, thread slots  (Alg. 3 l.16, Eq. 11)
+//   k_scan_blocks  exclusive scan of the per-block slot sums
+//   k_offsets      per-chunk slot offsets
+//   k_group_tiles  tiles per DFA group, tile bases
+//   k_tiles        first chunk of every tile
+//   k_match        persistent: stage chunks, advance every (chunk, state) chain,
+//                  compose the chunk maps, combine per test             (Alg. 3 l.8-20, Eqs. 8-9)
+//
+// Layout of the work: chunk k of a test is matched from every state of its
+// initial-state set I_k (the image of its reverse-lookahead symbol's class).
+// Each thread advances K of those chains together (one "lane task" per
+// (chunk, state) pair, K per thread so the class stream is read once for K
+// lookups).  A tile is a run of consecutive chunks whose threads fit one CTA;
+// each CTA owns a contiguous range of tiles and composes the maps of its
+// chunks in order (Eq. 9) into one running map per test; tests that span
+// several CTAs are finished by the CTA that completes last.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "dfa_internal.h"
+
+namespace dfam {
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t sa(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint4 lds_v4(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_v4(uint32_t a, uint4 v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                 :: "r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+__device__ __forceinline__ uint32_t ldg_u8(const uint8_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u8 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ldg_u16(const uint8_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u16 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Eq. (6) with unit weights and m states per later chunk (see chunk_start on the host).
+__device__ __forceinline__ uint64_t dstart(uint64_t n, uint32_t P, uint32_t m, uint32_t k) {
+    if (k == 0) return 0;
+    if (k >= P) return n;
+    unsigned __int128 num = (unsigned __int128)n * (uint64_t)(m + k - 1);
+    return (uint64_t)(num / (uint64_t)(m + P - 1));
+}
+
+template <int NTH>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, uint32_t* total) {
+    // tmp: NTH/32 + 1 words of shared memory
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NTH / 32 ? tmp[lane] : 0, z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < NTH / 32) tmp[lane] = z - w;
+        if (lane == NTH / 32 - 1) tmp[NTH / 32] = z;
+    }
+    __syncthreads();
+    uint32_t r = tmp[warp] + x - v;
+    if (total) *total = tmp[NTH / 32];
+    __syncthreads();
+    return r;
+}
+
+constexpr int kPlanThreads = 1024;
+
+__device__ __forceinline__ DevTest test_at(const LaunchPlan& lp, uint32_t i) {
+    return lp.tests ? lp.tests[i] : lp.test1;
+}
+__device__ __forceinline__ DevGroup group_at(const LaunchPlan& lp, uint32_t i) {
+    return lp.groups ? lp.groups[i] : lp.group1;
+}
+
+// ------------------------------------------------------------ planning
+
+// Per chunk: owning test, reverse-lookahead class (Algorithm 3 line 16) and
+// the thread slots it is charged: ceil(|I_k| / K), at least 2.
+__global__ void __launch_bounds__(kPlanThreads) k_count(LaunchPlan lp) {
+    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
+    uint32_t cost = 0;
+    if (g < lp.ptot) {
+        uint32_t lo = 0, hi = lp.ntests - 1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (test_at(lp, mid).chunk_base <= g) lo = mid; else hi = mid - 1;
+        }
+        const DevTest t = test_at(lp, lo);
+        const DevDfa& d = lp.dfas[t.dfa];
+        const uint32_t k = g - t.chunk_base;
+        const uint64_t st = dstart(t.n, t.P, t.m, k);
+        uint32_t cls;
+        if (st == 0) {
+            cls = d.C;  // chunk 0, or a chunk preceded only by empty chunks: start set {q0}
+        } else if (!t.lookahead) {
+            cls = d.C + 1;  // Algorithm 2: all of Q
+        } else {
+            uint32_t c = d.byte_class[t.str[st - 1]];
+            if (c == kNone16) {
+                atomicOr(&lp.test_err[lo], 1u);
+                c = d.C;
+            }
+            cls = c;
+        }
+        const uint32_t size = d.iset_off[cls + 1] - d.iset_off[cls];
+        const uint32_t cnt = (size + d.K - 1) / d.K;
+        cost = cnt < 2 ? 2 : cnt;
+        lp.chunk_test[g] = lo;
+        lp.chunk_cls[g] = (uint16_t)cls;
+        lp.cost[g] = cost;
+    }
+    uint32_t total;
+    block_excl_scan<kPlanThreads>(cost, tmp, &total);
+    if (threadIdx.x == 0) lp.bsum[blockIdx.x] = total;
+}
+
+// Exclusive scan of the block sums (one CTA).  bsum[nblk] = total.
+__global__ void __launch_bounds__(kPlanThreads) k_scan_blocks(LaunchPlan lp) {
+    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < lp.nblk; base += kPlanThreads) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t v = i < lp.nblk ? lp.bsum[i] : 0;
+        uint32_t total;
+        uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
+        if (i < lp.nblk) lp.bsum[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) lp.bsum[lp.nblk] = carry;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_offsets(LaunchPlan lp) {
+    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
+    uint32_t v = g < lp.ptot ? lp.cost[g] : 0;
+    uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, nullptr);
+    if (g < lp.ptot) lp.off[g] = lp.bsum[blockIdx.x] + ex;
+    if (g == 0) lp.off[lp.ptot] = lp.bsum[lp.nblk];
+}
+
+__device__ __forceinline__ uint32_t group_nt_eff(const DevDfa& d) {
+    return (uint32_t)kThreads - (d.cost_max - 1);
+}
+
+// Tiles per group: a tile holds the chunks whose slot offset (relative to the
+// group's first chunk) falls in one window of nt_eff slots, so a tile never
+// needs more than kThreads threads.
+__global__ void __launch_bounds__(kPlanThreads) k_group_tiles(LaunchPlan lp) {
+    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < lp.ngroups; base += kPlanThreads) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t nt = 0;
+        if (i < lp.ngroups) {
+            const DevGroup gr = group_at(lp, i);
+            const uint32_t eff = group_nt_eff(lp.dfas[gr.dfa]);
+            nt = (lp.off[gr.end_chunk - 1] - lp.off[gr.first_chunk]) / eff + 1;
+        }
+        uint32_t total;
+        uint32_t ex = block_excl_scan<kPlanThreads>(nt, tmp, &total);
+        if (i < lp.ngroups) lp.tile_base[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        lp.tile_base[lp.ngroups] = carry;
+        *lp.num_tiles = carry;
+        lp.tile_first[carry] = lp.ptot;
+    }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_tiles(LaunchPlan lp) {
+    const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
+    if (g >= lp.ptot) return;
+    const uint32_t grp = test_at(lp, lp.chunk_test[g]).group;
+    const DevGroup gr = group_at(lp, grp);
+    const uint32_t eff = group_nt_eff(lp.dfas[gr.dfa]);
+    const uint32_t base = lp.off[gr.first_chunk];
+    const uint32_t lt = (lp.off[g] - base) / eff;
+    const bool first = g == gr.first_chunk || (lp.off[g - 1] - base) / eff != lt;
+    if (first) lp.tile_first[lp.tile_base[grp] + lt] = g;
+}
+
+// ------------------------------------------------------------ matching
+
+struct ChunkMeta {
+    const uint8_t* ptr;  // first byte of the chunk
+    uint32_t len;        // bytes
+    uint32_t test;
+    uint16_t toff;       // first thread (tile-local) of the chunk
+    uint16_t cls;        // set index (class, start set, or all of Q)
+    uint16_t cnt;        // threads actually used: ceil(|I|/K)
+    uint8_t lo_slack;    // min(bytes of the string before the chunk, 255)
+    uint8_t hi_slack;    // min(bytes of the string after the chunk, 255)
+};
+static_assert(sizeof(ChunkMeta) == 24, "ChunkMeta layout");
+
+// Shared-memory carve-up of k_match (byte offsets, all 16-byte aligned).
+struct SmemLayout {
+    uint32_t table, boff, stage, lmap, vmap, meta, misc, desc, total;
+};
+
+__host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline SmemLayout smem_layout(uint32_t table_cap, uint32_t kmax, uint32_t vcap) {
+    SmemLayout L;
+    L.table = 0;
+    L.boff = align16(table_cap);
+    L.stage = L.boff + 1024;
+    L.lmap = L.stage + 2 * kStageBytes;
+    L.vmap = L.lmap + align16(kThreads * kmax * 2);
+    L.meta = L.vmap + align16(vcap * 2);
+    L.misc = L.meta + kMaxChunksPerTile * sizeof(ChunkMeta);
+    L.desc = L.misc + 64;
+    L.total = L.desc + align16(sizeof(DevDfa));
+    return L;
+}
+
+// misc words
+enum { M_MAXLEN = 0, M_LAST = 1, M_DFA = 2 };
+
+// Advance K chains of one chunk over one staged segment of S positions.
+// Shared-memory table, 16-bit row offsets, StBytes-sized entries.
+template <int K, int SB>
+__device__ __forceinline__ void run_smem(uint32_t (&s)[K], uint32_t tb, uint32_t stage_addr, int S) {
+    for (int j = 0; j < S; j += 8) {
+        const uint4 w = lds_v4(stage_addr + 2 * j);
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const uint32_t row = tb + (half ? (words[h] >> 16) : (words[h] & 0xFFFFu));
+#pragma unroll
+                for (int u = 0; u < K; ++u) s[u] = SB == 1 ? lds_u8(row + s[u]) : lds_u16(row + s[u]);
+            }
+        }
+    }
+}
+
+// Same with the table read through L2 (32-bit row offsets, 4 per 16 bytes).
+template <int K, int SB>
+__device__ __forceinline__ void run_global(uint32_t (&s)[K], const uint8_t* tbl, uint32_t stage_addr,
+                                           int S) {
+    for (int j = 0; j < S; j += 4) {
+        const uint4 w = lds_v4(stage_addr + 4 * j);
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint8_t* row = tbl + words[h];
+#pragma unroll
+            for (int u = 0; u < K; ++u) s[u] = SB == 1 ? ldg_u8(row + s[u]) : ldg_u16(row + s[u]);
+        }
+    }
+}
+
+// One tile's chains for a given K: load initial states, run all segments
+// (staging is done by the caller through `stage_fn`), store the final states
+// into the tile-local map (plain state ids).
+struct TileCtx {
+    uint32_t tb;          // shared address of the table (smem placement)
+    const uint8_t* gtbl;  // global table (L2 placement)
+    uint32_t stage0;      // shared address of stage buffer 0
+    uint32_t lmap;        // shared address of the tile map
+    int sb, placement;
+    int ci, r, active;    // my chunk, rank within chunk, has work
+    int S;                // staged positions per chunk per segment
+};
+
+// ------------------------------------------------------------ staging
+
+// Convert bytes [pos, pos+8) of chunk ci to 8 row offsets and store them
+// at stage[ci*S + pos_in_seg].  Positions past the chunk end get the
+// identity row; bytes outside Sigma flag the test and also get the identity row.
+template <bool OFF32>
+__device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, uint32_t dst,
+                                            uint32_t boff, uint32_t id_off, uint32_t* test_err) {
+    uint32_t o[8];
+    if (pos >= m.len) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = id_off;
+    } else {
+        const uint32_t nvalid = min(8u, m.len - pos);
+        const uint8_t* a = m.ptr + pos;
+        const uint32_t d = (uint32_t)((uintptr_t)a & 7u);
+        uint64_t v = 0;
+        // fast path: the two aligned 8-byte words around [a, a+8) lie inside the string
+        const bool fast = (pos + m.lo_slack >= d) && (pos + 16u <= m.len + m.hi_slack + d);
+        if (fast) {
+            const uint64_t* al = reinterpret_cast<const uint64_t*>(a - d);
+            const uint64_t w0 = __ldg(al), w1 = __ldg(al + 1);
+            v = d ? ((w0 >> (8 * d)) | (w1 << (64 - 8 * d))) : w0;
+        } else {
+            for (uint32_t j = 0; j < nvalid; ++j) v |= (uint64_t)__ldg(a + j) << (8 * j);
+        }
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t b = (uint32_t)(v >> (8 * j)) & 0xFFu;
+            uint32_t x = OFF32 ? 0u : 0u;
+            if (OFF32) {
+                uint32_t t;
+                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(boff + 4 * b));
+                x = t;
+                if ((uint32_t)j < nvalid && x == kNone32) { bad = true; x = id_off; }
+            } else {
+                x = lds_u16(boff + 2 * b);
+                if ((uint32_t)j < nvalid && x == kNone16) { bad = true; x = id_off; }
+            }
+            o[j] = (uint32_t)j < nvalid ? x : id_off;
+        }
+        if (bad) atomicOr(test_err + m.test, 1u);
+    }
+    if (OFF32) {
+        sts_v4(dst, make_uint4(o[0], o[1], o[2], o[3]));
+        sts_v4(dst + 16, make_uint4(o[4], o[5], o[6], o[7]));
+    } else {
+        sts_v4(dst, make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
+                               o[6] | (o[7] << 16)));
+    }
+}
+
+template <bool OFF32>
+__device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, uint32_t stage,
+                              uint32_t boff, uint32_t id_off, uint32_t* test_err) {
+    const int groups = S / 8;
+    const int items = nch * groups;
+    for (int it = threadIdx.x; it < items; it += kThreads) {
+        const int ci = it / groups, q = it - ci * groups;
+        const ChunkMeta m = meta[ci];
+        const uint32_t pos = (uint32_t)seg * (uint32_t)S + 8u * (uint32_t)q;
+        const uint32_t dst = stage + (uint32_t)(ci * S + 8 * q) * (OFF32 ? 4u : 2u);
+        stage_group<OFF32>(m, pos, dst, boff, id_off, test_err);
+    }
+}
+
+template <int K>
+__device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uint32_t maxlen,
+                            const TileCtx& c, uint32_t boff, uint32_t* test_err) {
+    uint32_t s[K];
+    const bool off32 = d.placement == kGlobal;
+    const uint32_t sh = d.sb == 2 ? 1 : 0;
+    if (c.active) {
+        const ChunkMeta m = meta[c.ci];
+        const uint32_t base = d.iset_off[m.cls], size = d.iset_off[m.cls + 1] - base;
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            uint32_t slot = (uint32_t)c.r * K + u;
+            if (slot >= size) slot = (uint32_t)c.r * K;  // padding chain: repeat the first
+            s[u] = (uint32_t)d.iset[base + slot] << sh;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < K; ++u) s[u] = 0;
+    }
+    const uint32_t id_off = d.C * d.qpad * d.sb;
+    const int nseg = (int)((maxlen + c.S - 1) / c.S);
+    const uint32_t esz = off32 ? 4u : 2u;
+    for (int seg = 0; seg < nseg; ++seg) {
+        const uint32_t stage = c.stage0 + (uint32_t)(seg & 1) * kStageBytes;
+        if (off32) stage_segment<true>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
+        else stage_segment<false>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
+        __syncthreads();
+        if (c.active) {
+            const uint32_t my = stage + (uint32_t)(c.ci * c.S) * esz;
+            if (!off32) {
+                if (d.sb == 1) run_smem<K, 1>(s, c.tb, my, c.S);
+                else run_smem<K, 2>(s, c.tb, my, c.S);
+            } else {
+                if (d.sb == 1) run_global<K, 1>(s, c.gtbl, my, c.S);
+                else run_global<K, 2>(s, c.gtbl, my, c.S);
+            }
+        }
+        // the next segment stages into the other buffer, so one barrier per segment suffices
+    }
+    if (c.active) {
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            uint32_t v = s[u] >> sh;
+            asm volatile("st.shared.u16 [%0], %1;" :: "r"(c.lmap + 2u * ((uint32_t)(threadIdx.x) * K + u)),
+                         "h"((uint16_t)v) : "memory");
+        }
+    }
+}
+
+// Final state of test t from its segment maps (slots b + t for b in
+// [first_cta, last_cta]), composed in order by one thread: Eq. (8) applied
+// segment by segment.
+__device__ void combine_test(const LaunchPlan& lp, uint32_t t) {
+    const DevTest tt = test_at(lp, t);
+    const DevDfa& d = lp.dfas[tt.dfa];
+    const uint32_t b0 = __ldcg(lp.first_cta + t), b1 = __ldcg(lp.last_cta + t);
+    uint32_t s = __ldcg(lp.seg_vals + (size_t)(b0 + t) * lp.seg_stride);
+    for (uint32_t b = b0 + 1; b <= b1; ++b) {
+        const size_t slot = b + t;
+        const uint32_t cls = __ldcg(lp.seg_hdr + slot * 4 + 2);
+        const uint32_t p = d.pos[(size_t)cls * d.qe + s];
+        if (p != kNone16) s = __ldcg(lp.seg_vals + slot * lp.seg_stride + p);
+    }
+    dfa_result_t r;
+    const uint32_t err = atomicOr(lp.test_err + t, 0u);
+    r.final_state = err ? 0u : s;
+    r.accept = err ? 0 : d.accept[s];
+    r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
+    r.status = err ? DFA_ESYMBOL : DFA_OK;
+    lp.results[tt.out] = r;
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t kmax) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const SmemLayout L = smem_layout(lp.smem_table_cap, kmax, lp.vcap);
+    ChunkMeta* meta = reinterpret_cast<ChunkMeta*>(sm + L.meta);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(sm + L.misc);
+    uint16_t* vmap = reinterpret_cast<uint16_t*>(sm + L.vmap);
+    const uint16_t* lmap = reinterpret_cast<const uint16_t*>(sm + L.lmap);
+    const int tid = threadIdx.x;
+
+    const uint32_t T = *lp.num_tiles;
+    const uint32_t G = gridDim.x, b = blockIdx.x;
+    // CTA b owns tiles [t0, t1); the CTAs that own tiles are 0, 1, 2, ... without gaps
+    uint32_t t0, t1;
+    if (T >= G) {
+        t0 = (uint32_t)((uint64_t)b * T / G);
+        t1 = (uint32_t)((uint64_t)(b + 1) * T / G);
+    } else {
+        t0 = b < T ? b : T;
+        t1 = b + 1 < T ? b + 1 : T;
+    }
+    if (t0 >= t1) return;
+    const uint32_t c_lo = lp.tile_first[t0], c_hi = lp.tile_first[t1];
+
+    int cur_dfa = -1;
+    DevDfa& d = *reinterpret_cast<DevDfa*>(sm + L.desc);  // the current tile's DFA
+    // running segment (CTA-uniform)
+    int cur_test = -1;
+    uint32_t seg_first = 0, seg_n = 0, seg_cls = 0, nD = 0;
+
+    auto end_segment = [&]() {
+        const DevTest tt = test_at(lp, (uint32_t)cur_test);
+        const bool covered = tt.chunk_base >= c_lo && tt.chunk_base + tt.P <= c_hi;
+        if (covered) {
+            // the segment is the whole test, started at chunk 0 from {q0}: V[0] is the answer
+            if (tid == 0) {
+                const uint32_t s = vmap[0];
+                const uint32_t err = atomicOr(lp.test_err + cur_test, 0u);
+                dfa_result_t r;
+                r.final_state = err ? 0u : s;
+                r.accept = err ? 0 : d.accept[s];
+                r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
+                r.status = err ? DFA_ESYMBOL : DFA_OK;
+                lp.results[tt.out] = r;
+            }
+            return;
+        }
+        const size_t slot = (size_t)b + (size_t)cur_test;
+        for (uint32_t x = tid; x < nD; x += kThreads) lp.seg_vals[slot * lp.seg_stride + x] = vmap[x];
+        if (tid == 0) {
+            lp.seg_hdr[slot * 4 + 0] = seg_first;
+            lp.seg_hdr[slot * 4 + 1] = seg_n;
+            lp.seg_hdr[slot * 4 + 2] = seg_cls;
+            lp.seg_hdr[slot * 4 + 3] = nD;
+            if (seg_first == tt.chunk_base) lp.first_cta[cur_test] = b;
+            if (seg_first + seg_n == tt.chunk_base + tt.P) lp.last_cta[cur_test] = b;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const uint32_t old = atomicAdd(lp.arrived + cur_test, seg_n);
+            misc[M_LAST] = (old + seg_n == tt.P) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (misc[M_LAST]) {
+            if (tid == 0) {
+                __threadfence();
+                combine_test(lp, (uint32_t)cur_test);
+            }
+        }
+        __syncthreads();
+    };
+
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t gA = lp.tile_first[t], gB = lp.tile_first[t + 1];
+        const int nch = (int)(gB - gA);
+        const uint32_t test0 = lp.chunk_test[gA];
+        const int di = (int)test_at(lp, test0).dfa;
+        if (di != cur_dfa) {
+            __syncthreads();
+            if (tid < (int)(sizeof(DevDfa) / 4))
+                reinterpret_cast<uint32_t*>(&d)[tid] = reinterpret_cast<const uint32_t*>(lp.dfas + di)[tid];
+            __syncthreads();
+            if (d.placement == kSmem) {
+                const uint4* src = reinterpret_cast<const uint4*>(d.table);
+                uint4* dst = reinterpret_cast<uint4*>(sm + L.table);
+                const uint32_t n16 = (d.table_bytes + 15) / 16;
+                for (uint32_t i = tid; i < n16; i += kThreads) dst[i] = __ldg(src + i);
+                uint16_t* bo = reinterpret_cast<uint16_t*>(sm + L.boff);
+                for (int i = tid; i < 256; i += kThreads) bo[i] = __ldg(d.byte_off16 + i);
+            } else {
+                uint32_t* bo = reinterpret_cast<uint32_t*>(sm + L.boff);
+                for (int i = tid; i < 256; i += kThreads) bo[i] = __ldg(d.byte_off32 + i);
+            }
+            cur_dfa = di;
+        }
+        // chunk metadata
+        if (tid == 0) misc[M_MAXLEN] = 0;
+        __syncthreads();
+        const uint32_t off0 = lp.off[gA];
+        for (int i = tid; i < nch; i += kThreads) {
+            const uint32_t g = gA + (uint32_t)i;
+            const uint32_t te = lp.chunk_test[g];
+            const DevTest tt = test_at(lp, te);
+            const uint32_t k = g - tt.chunk_base;
+            const uint64_t st = dstart(tt.n, tt.P, tt.m, k), en = dstart(tt.n, tt.P, tt.m, k + 1);
+            const uint32_t cls = lp.chunk_cls[g];
+            const uint32_t size = d.iset_off[cls + 1] - d.iset_off[cls];
+            ChunkMeta m;
+            m.ptr = tt.str + st;
+            m.len = (uint32_t)(en - st);
+            m.test = te;
+            m.toff = (uint16_t)(lp.off[g] - off0);
+            m.cls = (uint16_t)cls;
+            m.cnt = (uint16_t)((size + d.K - 1) / d.K);
+            m.lo_slack = (uint8_t)(st < 255 ? st : 255);
+            m.hi_slack = (uint8_t)(tt.n - en < 255 ? tt.n - en : 255);
+            meta[i] = m;
+            atomicMax(misc + M_MAXLEN, m.len);
+        }
+        __syncthreads();
+        const uint32_t maxlen = misc[M_MAXLEN];
+
+        // my chunk: last ci with toff <= tid
+        TileCtx c;
+        {
+            int lo = 0, hi = nch - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (meta[mid].toff <= tid) lo = mid; else hi = mid - 1;
+            }
+            c.ci = lo;
+            c.r = tid - meta[lo].toff;
+            c.active = c.r < (int)meta[lo].cnt;
+        }
+        const uint32_t esz = d.placement == kGlobal ? 4u : 2u;
+        int S = (int)(kStageBytes / ((uint32_t)nch * esz)) & ~7;
+        S = S < 8 ? 8 : (S > kMaxSegLen ? kMaxSegLen : S);
+        c.S = S;
+        c.tb = sa(sm + L.table);
+        c.gtbl = d.table;
+        c.stage0 = sa(sm + L.stage);
+        c.lmap = sa(sm + L.lmap);
+        c.sb = (int)d.sb;
+        c.placement = (int)d.placement;
+        const uint32_t boff = sa(sm + L.boff);
+        switch (d.K) {
+            case 2: tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
+            case 4: tile_chains<4>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
+            case 8: tile_chains<8>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
+            default: tile_chains<KMAX>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
+        }
+        __syncthreads();
+
+        // Compose the tile's chunk maps, in order, into the running map of each
+        // test (Eq. 9).  Thread x owns entries x, x+kThreads, ... of the running map.
+        for (int i = 0; i < nch; ++i) {
+            const ChunkMeta m = meta[i];
+            const uint32_t base = (uint32_t)m.toff * d.K;
+            if ((int)m.test != cur_test) {
+                if (cur_test >= 0) end_segment();
+                cur_test = (int)m.test;
+                seg_first = gA + (uint32_t)i;
+                seg_n = 0;
+                seg_cls = m.cls;
+                nD = d.iset_off[m.cls + 1] - d.iset_off[m.cls];
+                for (uint32_t x = tid; x < nD; x += kThreads) vmap[x] = lmap[base + x];
+            } else {
+                const uint16_t* pos = d.pos + (size_t)m.cls * d.qe;
+                for (uint32_t x = tid; x < nD; x += kThreads) {
+                    const uint32_t v = vmap[x];
+                    const uint32_t p = __ldg(pos + v);
+                    if (p != kNone16) vmap[x] = lmap[base + p];
+                }
+            }
+            ++seg_n;
+        }
+        __syncthreads();
+    }
+    if (cur_test >= 0) end_segment();
+}
+
+// ------------------------------------------------------------ host side
+
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap) {
+    return smem_layout(table_cap, kmax, vcap).total;
+}
+
+static int g_sm_count = -1, g_dev = -1;
+
+template <int KMAX>
+static int grid_for(uint32_t smem, uint32_t* grid) {
+    if (cudaFuncSetAttribute(k_match<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return DFA_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<KMAX>, kThreads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return DFA_ECUDA;
+    *grid = (uint32_t)(g_sm_count * per_sm);
+    return DFA_OK;
+}
+
+int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DFA_ECUDA;
+    if (g_dev != dev) {
+        if (cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return DFA_ECUDA;
+        g_dev = dev;
+    }
+    return kmax > 8 ? grid_for<16>(smem, grid) : grid_for<8>(smem, grid);
+}
+
+// Issue the whole launch on `st`: memsets of the per-test counters, five
+// planning kernels and the match kernel.  Returns the number of kernels.
+int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
+                uint32_t* kernels, void* ev_begin, void* ev_end) {
+    if (cudaMemsetAsync(lp.test_err, 0, sizeof(uint32_t) * lp.ntests * 2, st) != cudaSuccess)
+        return DFA_ECUDA;  // test_err and arrived are adjacent
+    const uint32_t nb = lp.nblk;
+    k_count<<<nb, kPlanThreads, 0, st>>>(lp);
+    k_scan_blocks<<<1, kPlanThreads, 0, st>>>(lp);
+    k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
+    k_group_tiles<<<1, kPlanThreads, 0, st>>>(lp);
+    k_tiles<<<nb, kPlanThreads, 0, st>>>(lp);
+    if (ev_begin) cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), st);
+    if (kmax > 8) k_match<16><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
+    else k_match<8><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
+    if (ev_end) cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st);
+    if (kernels) *kernels = 6;
+    return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
+}
+
+}  // namespace dfam

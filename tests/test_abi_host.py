@@ -1,0 +1,141 @@
+"""CPU checks of the C ABI: the library loads, exports exactly what
+include/dfamatch.h declares, and its host-side steps (DFA compilation, Eq. 11/12
+initial-state sets, alphabet classes, the Eq. 6-7 partition) agree with the
+oracle.  No CUDA call is made here (dfa_create_host does none)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dm():
+    from paper_1210_5093_gb300 import build
+    build.build()
+    import paper_1210_5093_gb300 as dm
+    dm.lib()
+    return dm
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "dfamatch.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dfa_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(dm):
+    names = _header_functions()
+    assert len(names) >= 20
+    L = ctypes.CDLL(dm.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(dm.SIGNATURES) == names
+
+
+def test_strerror(dm):
+    assert dm.strerror(0) == "ok"
+    assert "alphabet" in dm.strerror(dm.ESYMBOL)
+
+
+def _compare_isets(dm, spec):
+    d = dm.Dfa.from_spec(spec, host_only=True)
+    o = oracle.Dfa.from_spec(spec)
+    flags, imax = o.isets()
+    info = d.info()
+    assert info.i_max == imax
+    assert info.num_states_ext == spec.num_states + 1
+    assert abs(info.gamma - imax / spec.num_states) < 1e-12
+    cls = d.class_of_bytes()
+    sym = spec.symbol_of_byte()
+    for b in range(256):
+        if sym[b] < 0:
+            assert cls[b] == 0xFFFF
+            continue
+        want = np.nonzero(flags[sym[b]])[0].tolist()
+        assert d.iset(int(cls[b])) == want, b
+    # bytes share a class exactly when their symbols have identical columns
+    ext = np.vstack([np.where(spec.delta < 0, spec.num_states, spec.delta),
+                     np.full((1, spec.num_symbols), spec.num_states)])
+    valid = [b for b in range(256) if sym[b] >= 0]
+    for i, b1 in enumerate(valid[:40]):
+        for b2 in valid[i + 1:i + 40]:
+            same = np.array_equal(ext[:, sym[b1]], ext[:, sym[b2]])
+            assert (cls[b1] == cls[b2]) == same
+    assert d.iset(info.num_classes) == [spec.q0]                       # start set
+    assert d.iset(info.num_classes + 1) == list(range(spec.num_states + 1))  # all of Q
+    excluded = o.excluded()
+    assert info.num_excluded == int(excluded.sum())
+    return d, info
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_compile_random_small(dm, seed):
+    spec = gen.random_dfa(40 + seed, 3 + 2 * seed, 2 + seed, num_finals=2, missing=0.3 * (seed % 2))
+    m = np.full(256, 0xFF, dtype=np.uint8)
+    m[97:97 + spec.num_symbols] = np.arange(spec.num_symbols)
+    spec.byte_to_symbol = m
+    _compare_isets(dm, spec)
+
+
+def test_compile_256_distinct_classes(dm):
+    spec = gen.random_dfa(77, 60, 256, num_finals=3)
+    d, info = _compare_isets(dm, spec)
+    assert info.num_classes == 256
+    assert sorted(set(d.class_of_bytes().tolist())) == list(range(256))
+
+
+def test_compile_workload_dfas(dm):
+    d, info = _compare_isets(dm, gen.plain_dfa(1))
+    assert info.state_bytes == 1 and info.placement == 0
+    spec = gen.regex_dfa(2)
+    d, info = _compare_isets(dm, spec)
+    assert info.num_classes == 32 and info.state_bytes == 2 and info.i_max == 241
+    spec = gen.protein_dfa(3)
+    d, info = _compare_isets(dm, spec)
+    assert info.num_classes == 20 and info.i_max == int(np.ceil(0.35 * 1288 - 1e-9))
+
+
+def test_compile_paper_examples(dm):
+    from tests._golden import dfa_from, load, symbol_map
+    for name in ("w1_fig1.txt", "w2_fig6.txt"):
+        f = load(name)
+        Q, syms, delta, q0, finals = dfa_from(f)
+        spec = gen.DfaSpec(Q, len(syms), delta, q0, np.array(finals, dtype=np.uint32),
+                           symbol_map(syms))
+        d, info = _compare_isets(dm, spec)
+        assert info.i_max == int(f["imax"][0][0])
+
+
+def test_compile_rejects_bad_input(dm):
+    good = np.zeros((2, 2), dtype=np.int32)
+    with pytest.raises(dm.DfaError):
+        dm.Dfa(2, 2, np.array([[0, 5], [0, 0]]), 0, [1], np.zeros(256, np.uint8), host_only=True)
+    with pytest.raises(dm.DfaError):
+        dm.Dfa(2, 2, good, 3, [1], np.zeros(256, np.uint8), host_only=True)   # q0 out of range
+    with pytest.raises(dm.DfaError):
+        dm.Dfa(2, 2, good, 0, [7], np.zeros(256, np.uint8), host_only=True)   # final out of range
+    with pytest.raises(dm.DfaError):
+        dm.Dfa(2, 2, good, 0, [1], None, host_only=True)                    # identity needs 256
+    bad_map = np.zeros(256, np.uint8)
+    bad_map[5] = 9
+    with pytest.raises(dm.DfaError):
+        dm.Dfa(2, 2, good, 0, [1], bad_map, host_only=True)
+    d = dm.Dfa(2, 2, good, 0, [1], np.zeros(256, np.uint8), host_only=True)
+    with pytest.raises(dm.DfaError) as e:
+        d.match(b"ab")
+    assert e.value.status == dm.EHOSTONLY
+
+
+@pytest.mark.parametrize("n", [0, 1, 36, 12345, 4 << 20, 10**10 + 7])
+@pytest.mark.parametrize("P", [1, 2, 3, 1000])
+@pytest.mark.parametrize("m", [1, 2, 241])
+def test_partition_matches_oracle(dm, n, P, m):
+    got = dm.partition(n, P, m).tolist()
+    assert got == oracle.chunk_starts(n, P, m)

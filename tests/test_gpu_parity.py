@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit-exact
+(final state and accept bit; the answer of a membership test is unique, so the
+tolerance is zero).  Covers the paper's examples, random and closed-form DFAs,
+every workload DFA, empty/ragged inputs, bytes outside Sigma, Algorithm 2
+(lookahead 0), the multiplicity of Eq. (10), the async and batched entry
+points, and the full-size regex- and protein-shaped workloads."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dm():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1210_5093_gb300 import build
+    build.build()
+    import paper_1210_5093_gb300 as dm
+    return dm
+
+
+def _expect(spec, data):
+    st, fs, acc = oracle.Dfa.from_spec(spec).run(data)
+    return st, fs, acc
+
+
+def _check(dm, d, spec, data, **kw):
+    st, fs, acc = d.match(data, **kw)
+    est, efs, eacc = _expect(spec, data)
+    assert st == est, (st, est, kw)
+    if st == 0:
+        assert (fs, acc) == (efs, eacc), kw
+
+
+def test_paper_examples(dm):
+    from tests._golden import dfa_from, load, symbol_map
+    for name in ("w1_fig1.txt", "w2_fig6.txt"):
+        f = load(name)
+        Q, syms, delta, q0, finals = dfa_from(f)
+        spec = gen.DfaSpec(Q, len(syms), delta, q0, np.array(finals, np.uint32), symbol_map(syms))
+        d = dm.Dfa.from_spec(spec)
+        text = f["input"][0][0].encode()
+        for P in (1, 2, 3, 5, 12, 36, 100):
+            for m in (1, 2, 4):
+                _check(dm, d, spec, text, num_chunks=P, multiplicity=m)
+        for n in range(len(text) + 1):
+            _check(dm, d, spec, text[:n], num_chunks=3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_dfas_many_chunkings(dm, seed):
+    Q = [2, 5, 17, 60, 255, 300][seed]
+    S = [2, 3, 7, 256, 20, 64][seed]
+    spec = gen.random_dfa(3000 + seed, Q, S, num_finals=max(1, Q // 5),
+                          missing=0.02 if seed % 2 else 0.0)
+    if S != 256:
+        m = np.full(256, 0xFF, dtype=np.uint8)
+        m[:S] = np.arange(S)
+        spec.byte_to_symbol = m
+    d = dm.Dfa.from_spec(spec)
+    data = gen.uniform_bytes(4000 + seed, 300_000)
+    if S != 256:
+        data = (data % S).astype(np.uint8)
+    for n in (0, 1, 7, 8, 9, 15, 16, 17, 100, 1000, 4097, 65537, 300_000):
+        for P in (0, 1, 2, 3, 17, 1024):
+            _check(dm, d, spec, data[:n], num_chunks=P)
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_mod_counter_gamma_one(dm, k):
+    spec = gen.mod_counter_dfa(k, 3)
+    m = np.full(256, 0xFF, dtype=np.uint8)
+    m[:3] = np.arange(3)
+    spec.byte_to_symbol = m
+    d = dm.Dfa.from_spec(spec)
+    assert d.info().i_max == k
+    data = (gen.uniform_bytes(77, 1 << 20) % 3).astype(np.uint8)
+    for n in (0, 5, 1000, 1 << 20):
+        _check(dm, d, spec, data[:n])
+        _check(dm, d, spec, data[:n], num_chunks=999)
+
+
+def test_suffix_automaton(dm):
+    word = [1, 0, 2, 2, 1]
+    spec = gen.suffix_dfa(word, 3)
+    m = np.full(256, 0xFF, dtype=np.uint8)
+    m[:3] = np.arange(3)
+    spec.byte_to_symbol = m
+    d = dm.Dfa.from_spec(spec)
+    data = (gen.uniform_bytes(78, 1 << 20) % 3).astype(np.uint8)
+    data[-5:] = word
+    for n in (5, 4096, 1 << 20):
+        st, fs, acc = d.match(data[:n])
+        assert acc == bytes(data[:n]).endswith(bytes(word))
+        _check(dm, d, spec, data[:n], num_chunks=333)
+
+
+def test_plain_workload_full_size(dm):
+    w = gen.plain_workload(1)
+    d = dm.Dfa.from_spec(w.spec)
+    _check(dm, d, w.spec, w.data, num_chunks=w.num_chunks)
+    _check(dm, d, w.spec, w.data)
+    for seed in range(2, 6):
+        data = gen.uniform_bytes(seed, (4 << 20) - seed * 1111)
+        _check(dm, d, w.spec, data, num_chunks=1024)
+
+
+@pytest.mark.parametrize("maker,n", [("regex", 16 << 20), ("protein", 16 << 20)])
+def test_shaped_workloads_reduced(dm, maker, n):
+    w = gen.regex_workload(2, n) if maker == "regex" else gen.protein_workload(3, n)
+    d = dm.Dfa.from_spec(w.spec)
+    _check(dm, d, w.spec, w.data)
+    for P in (1, 7, 4096, 100_000):
+        _check(dm, d, w.spec, w.data, num_chunks=P)
+    # ragged lengths and an accepted ending (a planted word drives every state into F)
+    word = np.frombuffer(w.spec.meta["planted_words"][0], dtype=np.uint8)
+    data = w.data[: n - 12345].copy()
+    data[-len(word):] = word
+    st, fs, acc = d.match(data)
+    assert st == 0 and acc
+    _check(dm, d, w.spec, data)
+
+
+def test_symbols_outside_sigma(dm):
+    spec = gen.protein_dfa(3)
+    d = dm.Dfa.from_spec(spec)
+    data = gen.protein_text(3, 1 << 20)
+    for pos in (0, 1, 4095, 4096, 500_000, (1 << 20) - 1):
+        bad = data.copy()
+        bad[pos] = ord("B")
+        for P in (0, 1, 2, 1000):
+            st, fs, acc = d.match(bad, num_chunks=P)
+            assert st == dm.ESYMBOL, (pos, P)
+    st, _, _ = d.match(data)
+    assert st == 0
+
+
+def test_empty_and_tiny_inputs(dm):
+    spec = gen.regex_dfa(2)
+    d = dm.Dfa.from_spec(spec)
+    st, fs, acc = d.match(b"")
+    assert (st, fs) == (0, spec.q0)
+    for n in range(1, 40):
+        _check(dm, d, spec, gen.zipf_text(5, n))
+        _check(dm, d, spec, gen.zipf_text(5, n), num_chunks=n + 3)
+
+
+def test_algorithm2_and_multiplicity(dm):
+    for spec, data in ((gen.regex_dfa(2), gen.zipf_text(2, 3 << 20)),
+                       (gen.plain_dfa(1), gen.uniform_bytes(1, 3 << 20))):
+        d = dm.Dfa.from_spec(spec)
+        for la in (0, 1):
+            for m in (1, 3, 241):
+                _check(dm, d, spec, data, lookahead=la, multiplicity=m)
+                _check(dm, d, spec, data, lookahead=la, multiplicity=m, num_chunks=5000)
+
+
+def test_async_with_torch_buffers(dm):
+    import torch
+    w = gen.regex_workload(2, 8 << 20)
+    d = dm.Dfa.from_spec(w.spec)
+    dev = torch.from_numpy(w.data).cuda()
+    ws = torch.empty(d.workspace_size(dev.numel()), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(12, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            d.match_async(dev, out, ws, stream=s)
+    s.synchronize()
+    (fs, acc, st), = dm.results_from(out)
+    est, efs, eacc = _expect(w.spec, w.data)
+    assert (st, fs, acc) == (0, efs, eacc)
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dm.DfaError):
+        d.match_async(dev, out, small)
+
+
+def _batch_mix(seed, count, max_len):
+    specs = gen.batch_dfas(seed, 8)
+    lens = gen.batch_lengths(seed, count, 1, max_len)
+    lens[:3] = [0, 1, 2]
+    picks = gen.batch_picks(seed, count, len(specs))
+    datas = [gen.batch_text(seed * 7919 + i, specs[picks[i]], int(lens[i])) for i in range(count)]
+    return specs, picks, datas
+
+
+def test_batch_matches_oracle_and_graph_replay(dm):
+    import torch
+    specs, picks, datas = _batch_mix(11, 300, 1 << 20)
+    dfas = [dm.Dfa.from_spec(s) for s in specs]
+    tens = [torch.from_numpy(x).cuda() for x in datas]
+    expect = [_expect(specs[picks[i]], datas[i]) for i in range(len(datas))]
+    res = dm.match_batch([dfas[p] for p in picks], tens)
+    for (fs, acc, st), (est, efs, eacc) in zip(res, expect):
+        assert st == est and (st != 0 or (fs, acc) == (efs, eacc))
+    b = dm.Batch([dfas[p] for p in picks], tens)
+    out = torch.zeros(12 * len(tens), dtype=torch.uint8, device="cuda")
+    for graph in (False, True, True):
+        out.zero_()
+        b.launch(out, graph=graph)
+        torch.cuda.synchronize()
+        assert dm.results_from(out) == res
+    # the same tests one at a time give the same answers
+    for i in range(0, len(tens), 37):
+        st, fs, acc = dfas[picks[i]].match(tens[i])
+        assert (fs, acc) == res[i][:2] or st != 0
+
+
+@pytest.mark.slow
+def test_regex_full_size_1GiB(dm):
+    import torch
+    w = gen.regex_workload(2, 1 << 30)
+    d = dm.Dfa.from_spec(w.spec)
+    dev = torch.from_numpy(w.data).cuda()
+    ws = torch.empty(d.workspace_size(dev.numel()), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(12, dtype=torch.uint8, device="cuda")
+    d.match_async(dev, out, ws)
+    torch.cuda.synchronize()
+    (fs, acc, st), = dm.results_from(out)
+    est, efs, eacc = _expect(w.spec, w.data)
+    assert (st, fs, acc) == (0, efs, eacc)
+
+
+@pytest.mark.slow
+def test_protein_full_size_10GB(dm):
+    import torch
+    w = gen.protein_workload(3, 10 * 10**9)
+    d = dm.Dfa.from_spec(w.spec)
+    dev = torch.from_numpy(w.data).cuda()
+    ws = torch.empty(d.workspace_size(dev.numel()), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(12, dtype=torch.uint8, device="cuda")
+    d.match_async(dev, out, ws)
+    torch.cuda.synchronize()
+    (fs, acc, st), = dm.results_from(out)
+    est, efs, eacc = _expect(w.spec, w.data)
+    assert (st, fs, acc) == (0, efs, eacc)
