@@ -172,6 +172,31 @@ int dfa_match_async(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
                     uint64_t workspace_bytes, void *stream);
 
 /*
+ * Allocation-free variant of dfa_match_async, for callers that cannot call
+ * cudaMalloc at all and have no workspace to hand over (for example a loop
+ * that gave all device memory to its own pool, or code that must not enter
+ * the CUDA allocator while serving).  The paper has no counterpart: this is
+ * a property of the library, not of the method.
+ * The scratch space is a fixed 16 MiB device array inside the library
+ * (dfa_noalloc_scratch_bytes()), held by every GPU that loads the library
+ * until the process exits.  The caller still passes the input (device,
+ * len bytes) and dev_out (one device dfa_result_t).  A call whose plan needs
+ * more scratch than that returns DFA_ENOSPACE before launching anything;
+ * lower opts->num_chunks or use dfa_match_async.  No call allocates memory
+ * (no cudaMalloc, cudaFree or allocating library routine); the parts of the
+ * scratch that must start at zero are cleared on the stream by each call.
+ * All calls on a device share the one array, which keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, or another
+ * host thread) race and give wrong results; order them on one stream.  The
+ * first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ */
+int dfa_match_noalloc(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
+                      const dfa_match_opts_t *opts, dfa_result_t *dev_out, void *stream);
+/* Size in bytes of the scratch array dfa_match_noalloc uses. */
+uint64_t dfa_noalloc_scratch_bytes(void);
+
+/*
  * Batched membership tests: count independent tests (dfas[i], strs[i],
  * lens[i]) run in one persistent launch (plus four small planning launches).
  * dfas may repeat (tests are grouped by DFA); strs are device pointers;

@@ -77,6 +77,8 @@ SIGNATURES = {
     "dfa_plan_chunks": (_I, [_P, _U64, _P, _P]),
     "dfa_match_workspace_size": (_I, [_P, _U64, _P, _P]),
     "dfa_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
+    "dfa_match_noalloc": (_I, [_P, _P, _U64, _P, _P, _P]),
+    "dfa_noalloc_scratch_bytes": (_U64, []),
     "dfa_match_batch": (_I, [_U32, _P, _P, _P, _P, _P, _P]),
     "dfa_batch_prepare": (_I, [_U32, _P, _P, _P, _P, _P]),
     "dfa_batch_launch": (_I, [_P, _P, _P]),
@@ -261,6 +263,20 @@ class Dfa:
                                    dev_out.data_ptr(), workspace.data_ptr(), workspace.numel(),
                                    _stream_ptr(stream))
         _check(rc, "dfa_match_async")
+
+    def match_noalloc(self, dev_data, dev_out, stream=None, num_chunks: int = 0,
+                      multiplicity: int = 0, lookahead: int = 1):
+        """Enqueue a test that uses the library's fixed scratch array instead of a
+        workspace (see dfa_match_noalloc: calls sharing a device must not overlap)."""
+        o = _opts(num_chunks, multiplicity, lookahead)
+        n = dev_data.numel()
+        rc = lib().dfa_match_noalloc(self._h, dev_data.data_ptr() if n else None, n,
+                                     ctypes.byref(o), dev_out.data_ptr(), _stream_ptr(stream))
+        _check(rc, "dfa_match_noalloc")
+
+
+def noalloc_scratch_bytes() -> int:
+    return int(lib().dfa_noalloc_scratch_bytes())
 
 
 def _ptr_array(vals):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdfamatch.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["dfa_kernels.cu", "dfa_api.cu", "dfa_server.cu", "dfa_compile.cpp"]
+SOURCES = ["dfa_kernels.cu", "dfa_api.cu", "dfa_server.cu", "dfa_noalloc.cu", "dfa_compile.cpp"]
 
 
 def _nvcc() -> str:

@@ -222,15 +222,12 @@ int launch_prepared(const Prepared& p, uint8_t* ws, dfa_result_t* out, void* str
     return launch_plan(lp, p.kmax, p.smem, static_cast<cudaStream_t>(stream), nullptr);
 }
 
-namespace {
+int launch_single(const Single& s, void* stream, void* ev_begin, void* ev_end) {
+    return launch_plan(s.lp, s.kmax, s.smem, static_cast<cudaStream_t>(stream), nullptr, ev_begin,
+                       ev_end);
+}
 
 // Single-test plan with descriptors carried by value (no upload needed).
-struct Single {
-    LaunchPlan lp;
-    WsLayout ws;
-    uint32_t smem, kmax;
-};
-
 int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Single* s) {
     if (!d) return DFA_EINVAL;
     if (!d->on_device) return DFA_EHOSTONLY;
@@ -275,7 +272,6 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     return DFA_OK;
 }
 
-}  // namespace
 }  // namespace dfam
 
 using namespace dfam;

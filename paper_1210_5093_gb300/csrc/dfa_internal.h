@@ -150,6 +150,16 @@ void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out
 int upload_desc_async(const Prepared& p, uint8_t* ws, uint8_t* pinned, void* stream);
 uint64_t desc_span(const Prepared& p);
 int launch_prepared(const Prepared& p, uint8_t* ws, dfa_result_t* out, void* stream);
+
+// Single-test launch: plan (descriptors by value), workspace layout, binding.
+struct Single {
+    LaunchPlan lp;
+    WsLayout ws;
+    uint32_t smem, kmax;
+};
+int plan_single(const dfa_s* d, uint64_t len, const dfa_match_opts_t* opts, Single* s);
+void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w);
+int launch_single(const Single& s, void* stream, void* ev_begin, void* ev_end);
 }  // namespace dfam
 
 // The opaque handle of the C ABI.

@@ -1,0 +1,67 @@
+// dfa_match_noalloc: the single-test membership test without any device
+// allocation by the caller or by the library at call time.
+//
+// The planning and match kernels need scratch memory (per-chunk classes and
+// offsets, tile boundaries, per-test counters and the state maps of the CTAs
+// that share a test).  dfa_match_async takes that scratch from the caller and
+// dfa_match allocates it; some callers can do neither - for example a host
+// loop that has handed all device memory to its own pool, or code that must
+// not enter the CUDA allocator while it serves requests.  For them the scratch
+// lives in the fixed array below, which every GPU that loads this library
+// holds until the process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "dfa_internal.h"
+
+namespace {
+
+constexpr uint64_t kScratchBytes = 16ull << 20;  // 16 MiB per device
+
+// Shared by every call on a device; only host code needs its address, which
+// is looked up once per device (the array's host-side name is not a device
+// address and must never be passed to a kernel).
+static __device__ __align__(256) uint8_t g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+uint8_t* g_ptr[kMaxDevices] = {};
+
+int scratch_ptr(uint8_t** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DFA_ECUDA;
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DFA_ECUDA;
+        }
+        g_ptr[dev] = static_cast<uint8_t*>(p);
+    }
+    *out = g_ptr[dev];
+    return DFA_OK;
+}
+
+}  // namespace
+
+extern "C" int dfa_match_noalloc(const dfa_t* dfa, const uint8_t* dev_str, uint64_t len,
+                                 const dfa_match_opts_t* opts, dfa_result_t* dev_out,
+                                 void* stream) {
+    if (!dfa || !dev_out || (len && !dev_str)) return DFA_EINVAL;
+    dfam::Single s;
+    int rc = dfam::plan_single(dfa, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    if (s.ws.total > kScratchBytes) return DFA_ENOSPACE;
+    uint8_t* base = nullptr;
+    if ((rc = scratch_ptr(&base)) != DFA_OK) return rc;
+    s.lp.test1.str = dev_str;
+    dfam::bind(s.lp, base, s.ws);
+    s.lp.results = dev_out;
+    // the per-test counters that must start at zero are cleared by the launch itself
+    return dfam::launch_single(s, stream, opts ? opts->match_begin_event : nullptr,
+                               opts ? opts->match_end_event : nullptr);
+}
+
+extern "C" uint64_t dfa_noalloc_scratch_bytes(void) { return kScratchBytes; }
