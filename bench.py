@@ -184,6 +184,99 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def _mixed_strings(spec, seed: int, count: int, lo: int, hi: int):
+    """Strings for the batched/serving legs: lengths log-uniform in [lo, hi]."""
+    import gen
+    lens = gen.batch_lengths(seed, count, lo, hi)
+    return [gen.batch_text(seed * 1000003 + i, spec, int(n)) for i, n in enumerate(lens)]
+
+
+def batched_leg(dm, dfas, datas, reps: int = 5):
+    """One persistent graph-replayed launch over all tests vs the plain path
+    (one dfa_match_async per string, back to back on one stream).  Device-resident."""
+    import torch
+    tens = [torch.from_numpy(x).cuda() for x in datas]
+    total = sum(len(x) for x in datas)
+    stream = torch.cuda.Stream()
+    out = torch.zeros(12 * len(tens), dtype=torch.uint8, device="cuda")
+    b = dm.Batch(dfas, tens)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            b.launch(out, stream=stream, graph=True)
+    torch.cuda.synchronize()
+    res_b = dm.results_from(out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            b.launch(out, stream=stream, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    # plain path: per-string launches with one reusable workspace
+    wsz = max(d.workspace_size(t.numel()) for d, t in zip(dfas, tens))
+    ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+    outs = torch.zeros(12 * len(tens), dtype=torch.uint8, device="cuda")
+
+    def plain():
+        for i, (d, t) in enumerate(zip(dfas, tens)):
+            d.match_async(t, outs[12 * i:12 * i + 12], ws, stream=stream)
+    with torch.cuda.stream(stream):
+        plain()
+    torch.cuda.synchronize()
+    assert dm.results_from(outs) == res_b, "batched and plain results differ"
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, reps // 2)):
+            plain()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3 / max(1, reps // 2)
+    kernels = b.num_kernels()
+    b.close()
+    return {"tests": len(tens), "bytes": total, "gbs": round(total / t_batch / 1e9, 3),
+            "ms": round(t_batch * 1e3, 3), "plain_gbs": round(total / t_plain / 1e9, 3),
+            "plain_ms": round(t_plain * 1e3, 3), "speedup_vs_plain": round(t_plain / t_batch, 3),
+            "launches": kernels, "plain_launches": 6 * len(tens)}, res_b
+
+
+def serving_leg(dm, dfas, datas, rate_gbs: float, seconds: float = 2.0, budget: int = 2 << 30,
+                inflight: int = 4, seed: int = 5):
+    """Poisson arrivals at `rate_gbs` of offered load drawn from the given tests
+    (pinned host buffers); reports achieved GB/s and arrival->result latency."""
+    import torch
+
+    import gen
+    pinned = [torch.from_numpy(x).pin_memory() for x in datas]
+    mean_bytes = sum(len(x) for x in datas) / len(datas)
+    lam = rate_gbs * 1e9 / mean_bytes                       # requests per second
+    n = max(20, int(lam * seconds))
+    gaps = -np.log(1.0 - gen.unit(gen.draws(gen.key(seed, 99), n))) / lam
+    picks = gen.below(gen.draws(gen.key(seed, 98), n), len(datas)).astype(np.int64)
+    srv = dm.Server(budget, max_inflight=inflight)
+    t0 = time.perf_counter()
+    t_next = t0
+    sub = {}
+    for i in range(n):
+        t_next += gaps[i]
+        while time.perf_counter() < t_next:
+            pass
+        sub[srv.submit(dfas[picks[i]], pinned[picks[i]])] = picks[i]
+    srv.drain(600.0)
+    done = srv.poll(n + 16)
+    st = srv.stats()
+    srv.close()
+    lat = sorted((c[5] - c[4]) * 1e3 for c in done)
+    t_first = min(c[4] for c in done)
+    t_last = max(c[5] for c in done)
+    nbytes = sum(len(datas[sub[c[0]]]) for c in done)
+    return {"requests": len(done), "offered_gbs": round(rate_gbs, 3),
+            "offered_req_s": round(lam, 1), "achieved_gbs": round(nbytes / (t_last - t_first) / 1e9, 3),
+            "p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+            "launches": int(st.launches), "max_concurrent_batches": int(st.max_concurrent),
+            "budget_bytes": budget}, done, sub
+
+
 def _dtype(spec) -> str:
     return "u8" if spec.num_states + 1 <= 256 else "u16"
 
@@ -198,6 +291,7 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--bytes", type=int, default=0, help="input size override (small profiling cases)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-mix", action="store_true", help="skip the batched and serving legs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -327,6 +421,14 @@ def main():
                        "reasons": clk["reasons"], "samples": clk["samples"]},
             "result": {"final_state": fs, "accept": acc, "status": st},
         }
+        if not args.no_mix and args.workload == "regex":
+            mix = _mixed_strings(w.spec, 11, 384, 256, 8 << 20)
+            bl, res_b = batched_leg(dm, [d] * len(mix), mix)
+            line["batched"] = dict(bl, workload="regex512 DFA, 384 strings, lengths log-uniform 256 B - 8 MiB")
+            sv, done, sub = serving_leg(dm, [d] * len(mix), mix, 0.5 * bl["gbs"])
+            for c in done:          # every served result equals the same test in the batch
+                assert (c[1], c[2], c[3]) == res_b[sub[c[0]]], "served result differs"
+            line["serving"] = dict(sv, workload="same 384 strings, Poisson arrivals at half the batched rate")
         if not args.no_cpu:
             v, nbytes, reps = cpu_oracle_gbs(w.spec, w.data)
             line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1,

@@ -243,6 +243,7 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, rejected, launches, bytes_matched;
     uint64_t bytes_in_flight, max_bytes_in_flight;
+    uint64_t max_concurrent;  /* most batches that were on the device at once */
 } dfa_server_stats_t;
 
 /*

@@ -60,7 +60,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("rejected", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("bytes_matched", ctypes.c_uint64), ("bytes_in_flight", ctypes.c_uint64),
-                ("max_bytes_in_flight", ctypes.c_uint64)]
+                ("max_bytes_in_flight", ctypes.c_uint64), ("max_concurrent", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes); the complete exported surface of include/dfamatch.h

@@ -219,6 +219,9 @@ bool dfa_server_s::launch_one() {
     {
         std::lock_guard<std::mutex> g(mu);
         st.launches++;
+        uint64_t busy = 0;
+        for (const Slot& x : slots) busy += x.busy ? 1 : 0;
+        if (busy > st.max_concurrent) st.max_concurrent = busy;
     }
     if (rc != DFA_OK) {
         cudaGetLastError();

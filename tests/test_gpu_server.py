@@ -1,0 +1,92 @@
+"""The serving loop (dfa_server_*): continuous batching of requests that
+arrive while earlier batches run.  Each result must equal the result of the
+same test run alone (and the oracle's), bit-exactly; admission respects the
+memory budget; batches overlap on the device."""
+import time
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dm():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1210_5093_gb300 import build
+    build.build()
+    import paper_1210_5093_gb300 as dm
+    return dm
+
+
+def test_served_results_equal_alone(dm):
+    specs = [gen.plain_dfa(1), gen.regex_dfa(2), gen.protein_dfa(3)] + gen.batch_dfas(5, 4)
+    dfas = [dm.Dfa.from_spec(s) for s in specs]
+    n_req = 240
+    lens = gen.batch_lengths(21, n_req, 1, 2 << 20)
+    picks = gen.batch_picks(21, n_req, len(specs))
+    datas = []
+    for i in range(n_req):
+        spec = specs[picks[i]]
+        if spec.name == "plain16":
+            x = gen.uniform_bytes(100 + i, int(lens[i]))
+        else:
+            x = gen.batch_text(100 + i, spec, int(lens[i]))
+        datas.append(x)
+    # one request carries a byte outside a protein DFA's alphabet
+    bad = next(i for i in range(n_req) if specs[picks[i]].byte_to_symbol is not None and lens[i] > 10)
+    datas[bad] = datas[bad].copy()
+    datas[bad][5] = ord("Z") if ord("Z") not in gen.AMINO else ord("#")
+    srv = dm.Server(64 << 20, max_inflight=4)
+    tickets = {}
+    done = {}
+    for i in range(n_req):
+        tickets[srv.submit(dfas[picks[i]], datas[i])] = i
+        if i % 16 == 15:
+            time.sleep(0.002)           # requests keep arriving while batches run
+            for c in srv.poll():
+                done[c[0]] = c
+    srv.drain(120.0)
+    for c in srv.poll(4096):
+        done[c[0]] = c
+    assert len(done) == n_req
+    st = srv.stats()
+    assert st.completed == n_req and st.submitted == n_req
+    assert st.launches >= 2
+    assert st.max_bytes_in_flight <= 64 << 20
+    for t, (ticket, fs, acc, status, t_sub, t_done) in done.items():
+        i = tickets[ticket]
+        assert t_done >= t_sub
+        est, efs, eacc = oracle.Dfa.from_spec(specs[picks[i]]).run(datas[i])
+        if i == bad:
+            assert status == dm.ESYMBOL and est == oracle.ESYMBOL
+            continue
+        assert (status, fs, acc) == (0, efs, eacc), i
+        alone = dfas[picks[i]].match(datas[i])
+        assert alone == (0, fs, acc)
+    with pytest.raises(dm.DfaError) as e:
+        srv.submit(dfas[0], np.zeros((64 << 20) + 1, dtype=np.uint8))
+    assert e.value.status == dm.EBUDGET
+    srv.close()
+
+
+def test_batches_overlap_under_continuous_arrivals(dm):
+    spec = gen.regex_dfa(2)
+    d = dm.Dfa.from_spec(spec)
+    x = gen.zipf_text(7, 24 << 20)
+    srv = dm.Server(1 << 30, max_inflight=3)
+    for k in range(12):
+        srv.submit(d, x)
+        time.sleep(0.001)
+    srv.drain(120.0)
+    res = srv.poll(64)
+    assert len(res) == 12
+    st = srv.stats()
+    assert st.max_concurrent >= 2
+    _, efs, eacc = oracle.Dfa.from_spec(spec).run(x)
+    assert all((r[1], r[2], r[3]) == (efs, eacc, 0) for r in res)
+    srv.close()
