@@ -292,6 +292,7 @@ def main():
     ap.add_argument("--bytes", type=int, default=0, help="input size override (small profiling cases)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-mix", action="store_true", help="skip the batched and serving legs")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -321,6 +322,10 @@ def main():
     d = dm.Dfa.from_spec(w.spec)
     n = len(w.data)
     dev = torch.from_numpy(w.data).cuda()
+    tuning = None
+    if not w.num_chunks and not args.no_tune:
+        t, _ = d.autotune(dev)          # the library's per-DFA tuner, before any timing
+        tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta}
     P = d.plan_chunks(n, num_chunks=w.num_chunks)
     ws = torch.empty(d.workspace_size(n, num_chunks=w.num_chunks), dtype=torch.uint8, device="cuda")
     out = torch.zeros(12, dtype=torch.uint8, device="cuda")
@@ -398,6 +403,7 @@ def main():
             "config": {"workload": w.name, "states": w.spec.num_states,
                        "classes": int(info.num_classes), "input_bytes": n, "chunks": int(P),
                        "lookahead": 1, "i_max": int(info.i_max), "gamma": round(info.gamma, 4),
+                       "tuning": tuning,
                        "l2": "input (%d MiB) larger than L2 (129 MB); no flush needed" % (n >> 20)
                        if n > (129 << 20) else "input smaller than L2",
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -73,6 +73,17 @@ typedef struct {
     double mean_iset;        /* mean |I_c| over the classes                        */
 } dfa_info_t;
 
+/* Per-DFA tuning record (the GPU counterpart of the paper's per-processor
+ * profiling, Sec. 4.1): how many chains one thread advances and how long the
+ * chunks are.  Zero fields mean "library default". */
+typedef struct {
+    uint32_t states_per_thread; /* K in {2, 4, 8, 16}; ceil(I_max/K) must be <= 256
+                                   (Algorithm 2 launches raise K as needed)         */
+    uint32_t tiles_per_cta;     /* single tests: aim for this many tiles per CTA (default 8) */
+    uint32_t min_chunk_bytes;   /* single tests: shortest chunk (default 512)          */
+    uint32_t batch_chunk_bytes; /* batched and served tests: chunk length (default 8192) */
+} dfa_tuning_t;
+
 /* Optional per-call planning overrides; pass NULL for the defaults. */
 typedef struct {
     uint32_t num_chunks;   /* P; 0 = chosen by the planner                         */
@@ -118,6 +129,24 @@ int dfa_create_host(uint32_t num_states, uint32_t num_symbols, const int32_t *de
 void dfa_destroy(dfa_t *dfa);
 
 int dfa_info(const dfa_t *dfa, dfa_info_t *out);
+
+/* Read / replace the tuning record.  dfa_set_tuning re-uploads the DFA's
+ * device descriptor (synchronous); no launch may use the DFA meanwhile.
+ * Errors: DFA_EINVAL (K not allowed), DFA_ECUDA. */
+int dfa_get_tuning(const dfa_t *dfa, dfa_tuning_t *out);
+int dfa_set_tuning(dfa_t *dfa, const dfa_tuning_t *tuning);
+
+/*
+ * Autotuner: times single-test launches of the device string dev_sample
+ * (len bytes) for every allowed K in {2, 4, 8, 16} and tiles-per-CTA in
+ * {4, 8, 16} (median of 3 timed launches each, CUDA events on `stream`),
+ * keeps the fastest as the DFA's tuning record and returns it in *chosen and
+ * its time in *best_ms (either may be NULL).  The batched chunk length is set
+ * to the chosen single-test chunk length, clamped to [2 KiB, 64 KiB].
+ * Allocates a temporary workspace; synchronises the stream.
+ */
+int dfa_autotune(dfa_t *dfa, const uint8_t *dev_sample, uint64_t len, void *stream,
+                 dfa_tuning_t *chosen, double *best_ms);
 
 /* out[256]: alphabet class of every byte, 0xFFFF for bytes not in Sigma. */
 int dfa_class_of_bytes(const dfa_t *dfa, uint16_t *out);

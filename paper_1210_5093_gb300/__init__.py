@@ -45,6 +45,11 @@ class Info(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("mean_iset", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("states_per_thread", ctypes.c_uint32), ("tiles_per_cta", ctypes.c_uint32),
+                ("min_chunk_bytes", ctypes.c_uint32), ("batch_chunk_bytes", ctypes.c_uint32)]
+
+
 class MatchOpts(ctypes.Structure):
     _fields_ = [("num_chunks", ctypes.c_uint32), ("multiplicity", ctypes.c_uint32),
                 ("lookahead", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
@@ -71,6 +76,9 @@ SIGNATURES = {
     "dfa_destroy": (None, [_P]),
     "dfa_info": (_I, [_P, _P]),
     "dfa_class_of_bytes": (_I, [_P, _P]),
+    "dfa_get_tuning": (_I, [_P, _P]),
+    "dfa_set_tuning": (_I, [_P, _P]),
+    "dfa_autotune": (_I, [_P, _P, _U64, _P, _P, _P]),
     "dfa_iset": (_I, [_P, _U32, _P, _U32, _P]),
     "dfa_partition": (_I, [_U64, _U32, _U32, _P]),
     "dfa_match": (_I, [_P, _P, _U64, _P, _P]),
@@ -200,6 +208,27 @@ class Dfa:
         out = Info()
         _check(lib().dfa_info(self._h, ctypes.byref(out)), "dfa_info")
         return out
+
+    def tuning(self) -> Tuning:
+        t = Tuning()
+        _check(lib().dfa_get_tuning(self._h, ctypes.byref(t)), "dfa_get_tuning")
+        return t
+
+    def set_tuning(self, states_per_thread: int = 0, tiles_per_cta: int = 0,
+                   min_chunk_bytes: int = 0, batch_chunk_bytes: int = 0):
+        t = Tuning(states_per_thread, tiles_per_cta, min_chunk_bytes, batch_chunk_bytes)
+        _check(lib().dfa_set_tuning(self._h, ctypes.byref(t)), "dfa_set_tuning")
+
+    def autotune(self, dev_sample, stream=None):
+        """Time the candidate tunings on a device sample and keep the fastest.
+        Returns (Tuning, best_ms)."""
+        t = Tuning()
+        ms = ctypes.c_double()
+        n = dev_sample.numel()
+        _check(lib().dfa_autotune(self._h, dev_sample.data_ptr() if n else None, n,
+                                  _stream_ptr(stream), ctypes.byref(t), ctypes.byref(ms)),
+               "dfa_autotune")
+        return t, float(ms.value)
 
     def class_of_bytes(self) -> np.ndarray:
         out = np.zeros(256, dtype=np.uint16)

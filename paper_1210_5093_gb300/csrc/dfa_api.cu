@@ -14,7 +14,7 @@
 #include "dfa_internal.h"
 
 namespace dfam {
-uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap);
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes);
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
                 uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr);
@@ -68,10 +68,12 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
     lp.seg_vals = reinterpret_cast<uint16_t*>(base + w.seg_vals);
 }
 
-// Launch-specific copy of a DFA's device descriptor.
+// Launch-specific copy of a DFA's device descriptor.  K is raised when the
+// largest set the launch matches would not fit one tile.
 DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
     DevDfa x = d->dev;
     const uint32_t vmax = lookahead ? std::max(d->h.imax, 1u) : d->h.qe;
+    while ((vmax + x.K - 1) / x.K > (uint32_t)kThreads / 2 && x.K < 16) x.K *= 2;
     x.cost_max = std::max((vmax + x.K - 1) / x.K, 2u);
     x.vcap = vmax;
     return x;
@@ -84,7 +86,7 @@ uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_
     if (o && o->num_chunks) {
         P = o->num_chunks;
     } else if (batched) {
-        uint64_t L = d->tuned_chunk_len ? d->tuned_chunk_len : kBatchChunk;
+        uint64_t L = d->tuning.batch_chunk_bytes ? d->tuning.batch_chunk_bytes : kBatchChunk;
         P = (n + L - 1) / L;
     } else {
         // enough lane tasks for kTilesPerCta tiles on every CTA, chunks >= kMinChunk
@@ -95,8 +97,9 @@ uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_
             mean_cost += std::max((sz + h.K - 1) / h.K, 2u);
         }
         mean_cost = h.C ? mean_cost / h.C : 2.0;
-        double want = (double)grid * kThreads * kTilesPerCta * 0.9 / mean_cost;
-        uint64_t by_len = n / (d->tuned_chunk_len ? d->tuned_chunk_len : kMinChunk);
+        const uint32_t tpc = d->tuning.tiles_per_cta ? d->tuning.tiles_per_cta : kTilesPerCta;
+        double want = (double)grid * kThreads * tpc * 0.9 / mean_cost;
+        uint64_t by_len = n / (d->tuning.min_chunk_bytes ? d->tuning.min_chunk_bytes : kMinChunk);
         P = std::min<uint64_t>((uint64_t)want, by_len);
     }
     P = std::max<uint64_t>(P, (n + kMaxChunk - 1) / kMaxChunk);
@@ -132,7 +135,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         p.vcap = std::max(p.vcap, x.vcap);
         if (x.placement == kSmem) p.table_cap = std::max(p.table_cap, (uint32_t)up(x.table_bytes, 16));
     }
-    p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap);
+    p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap, &p.stage);
     int rc = match_grid(p.smem, p.kmax, &p.grid);
     if (rc != DFA_OK) return rc;
     std::vector<uint32_t> order(count);
@@ -183,6 +186,7 @@ void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out
     lp.seg_stride = p.vcap;
     lp.smem_table_cap = p.table_cap;
     lp.vcap = p.vcap;
+    lp.stage_bytes = p.stage;
     lp.dfas = reinterpret_cast<const DevDfa*>(ws + p.ws.dfas);
     lp.tests = reinterpret_cast<const DevTest*>(ws + p.ws.tests);
     lp.groups = reinterpret_cast<const DevGroup*>(ws + p.ws.groups);
@@ -237,7 +241,8 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     DevDfa x = launch_desc(d, lookahead);
     const uint32_t tcap = x.placement == kSmem ? (uint32_t)up(x.table_bytes, 16) : 0u;
     s->kmax = x.K;
-    s->smem = match_smem_bytes(tcap, x.K, x.vcap);
+    uint32_t stage = 0;
+    s->smem = match_smem_bytes(tcap, x.K, x.vcap, &stage);
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
@@ -252,6 +257,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.seg_stride = x.vcap;
     lp.smem_table_cap = tcap;
     lp.vcap = x.vcap;
+    lp.stage_bytes = stage;
     lp.dfas = d->dev_desc_for(lookahead);
     lp.tests = nullptr;
     lp.groups = nullptr;
@@ -394,6 +400,109 @@ int dfa_info(const dfa_t* d, dfa_info_t* o) {
     o->gamma = h.gamma;
     o->mean_iset = h.mean_iset;
     return DFA_OK;
+}
+
+int dfa_get_tuning(const dfa_t* d, dfa_tuning_t* out) {
+    if (!d || !out) return DFA_EINVAL;
+    *out = d->tuning;
+    out->states_per_thread = d->h.K;
+    return DFA_OK;
+}
+
+int dfa_set_tuning(dfa_t* d, const dfa_tuning_t* t) {
+    if (!d || !t) return DFA_EINVAL;
+    uint32_t K = t->states_per_thread ? t->states_per_thread : d->h.K;
+    if (K != 2 && K != 4 && K != 8 && K != 16) return DFA_EINVAL;
+    if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) return DFA_EINVAL;
+    d->tuning = *t;
+    d->tuning.states_per_thread = K;
+    d->h.K = K;
+    d->dev.K = K;
+    if (d->on_device) {
+        DevDfa descs[2] = {launch_desc(d, 1), launch_desc(d, 0)};
+        if (cudaMemcpy(d->dev_desc, descs, sizeof descs, cudaMemcpyHostToDevice) != cudaSuccess)
+            return DFA_ECUDA;
+    }
+    return DFA_OK;
+}
+
+int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream,
+                 dfa_tuning_t* chosen, double* best_ms) {
+    if (!d || (len && !dev_sample)) return DFA_EINVAL;
+    if (!d->on_device) return DFA_EHOSTONLY;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const dfa_tuning_t saved = d->tuning;
+    const uint32_t savedK = d->h.K;
+    std::vector<dfa_tuning_t> cands;
+    for (uint32_t K : {2u, 4u, 8u, 16u}) {
+        if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) continue;
+        for (uint32_t tpc : {4u, 8u, 16u}) {
+            dfa_tuning_t t = saved;
+            t.states_per_thread = K;
+            t.tiles_per_cta = tpc;
+            cands.push_back(t);
+        }
+    }
+    // workspace for the largest plan
+    uint64_t ws_need = 0;
+    for (const dfa_tuning_t& t : cands) {
+        if (dfa_set_tuning(d, &t) != DFA_OK) continue;
+        Single s;
+        if (plan_single(d, len, nullptr, &s) == DFA_OK) ws_need = std::max(ws_need, s.ws.total);
+    }
+    uint8_t* ws = nullptr;
+    if (cudaMalloc(&ws, ws_need + 256) != cudaSuccess) {
+        cudaGetLastError();
+        dfa_tuning_t t = saved;
+        t.states_per_thread = savedK;
+        dfa_set_tuning(d, &t);
+        return DFA_ENOMEM;
+    }
+    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(ws + ws_need);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    dfa_tuning_t best_t = saved;
+    best_t.states_per_thread = savedK;
+    uint32_t best_P = 1;
+    int rc = DFA_OK;
+    for (const dfa_tuning_t& t : cands) {
+        if (dfa_set_tuning(d, &t) != DFA_OK) continue;
+        Single s;
+        if (plan_single(d, len, nullptr, &s) != DFA_OK) continue;
+        s.lp.test1.str = dev_sample;
+        bind(s.lp, ws, s.ws);
+        s.lp.results = dres;
+        std::vector<float> ms;
+        for (int r = 0; r < 4 && rc == DFA_OK; ++r) {
+            cudaEventRecord(e0, st);
+            rc = launch_plan(s.lp, s.kmax, s.smem, st, nullptr);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = DFA_ECUDA;
+            float x = 0;
+            cudaEventElapsedTime(&x, e0, e1);
+            if (r > 0) ms.push_back(x);  // the first launch is a warm-up
+        }
+        if (rc != DFA_OK) break;
+        std::sort(ms.begin(), ms.end());
+        const double med = ms[ms.size() / 2];
+        if (med < best) {
+            best = med;
+            best_t = t;
+            best_P = s.lp.ptot;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ws);
+    uint64_t clen = best_P ? len / best_P : kBatchChunk;
+    best_t.batch_chunk_bytes = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(clen, 2048), 65536);
+    int rc2 = dfa_set_tuning(d, &best_t);
+    if (rc == DFA_OK) rc = rc2;
+    if (chosen) *chosen = d->tuning;
+    if (best_ms) *best_ms = best;
+    return rc;
 }
 
 int dfa_class_of_bytes(const dfa_t* d, uint16_t* out) {

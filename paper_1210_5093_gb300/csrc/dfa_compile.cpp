@@ -153,10 +153,10 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
     // enough that the padding of the last thread of a chunk stays small.
     double mean = std::max(1.0, h.mean_iset);
     h.K = mean >= 48 ? 8 : (mean >= 12 ? 4 : 2);
-    // a chunk's chains must fit in one tile: ceil(|set|/K) <= kThreads/2 for
-    // every set, including all of Q (Algorithm 2)
-    while ((qe + h.K - 1) / h.K > (uint32_t)kThreads / 2 && h.K < 16) h.K *= 2;
-    if ((qe + h.K - 1) / h.K > (uint32_t)kThreads / 2) return DFA_EINVAL;
+    // a chunk's chains must fit in one tile: ceil(I_max/K) <= kThreads/2
+    // (launches of Algorithm 2, which match all of Q, raise K further)
+    while ((std::max(h.imax, 1u) + h.K - 1) / h.K > (uint32_t)kThreads / 2 && h.K < 16) h.K *= 2;
+    if ((qe + 15) / 16 > (uint32_t)kThreads / 2) return DFA_EINVAL;
     *out = std::move(h);
     return DFA_OK;
 }

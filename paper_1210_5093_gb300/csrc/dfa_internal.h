@@ -81,6 +81,7 @@ struct LaunchPlan {
     uint32_t seg_stride;        // entries per segment map
     uint32_t smem_table_cap;    // bytes reserved for a shared-memory table
     uint32_t vcap;              // entries reserved for the running map
+    uint32_t stage_bytes;       // bytes of one of the two stage buffers
     uint32_t* chunk_test;       // [ptot]
     uint16_t* chunk_cls;        // [ptot]
     uint32_t* cost;             // [ptot] thread slots charged to the chunk
@@ -112,7 +113,7 @@ struct Prepared {
     std::vector<DevDfa> dfas;
     std::vector<DevTest> tests;
     std::vector<DevGroup> groups;
-    uint32_t ptot = 0, nblk = 0, grid = 0, kmax = 2, vcap = 1, table_cap = 0, smem = 0;
+    uint32_t ptot = 0, nblk = 0, grid = 0, kmax = 2, vcap = 1, table_cap = 0, smem = 0, stage = 0;
     WsLayout ws{};
 };
 
@@ -172,5 +173,5 @@ struct dfa_s {
     dfam::DevDfa dev;                // pointers into dev_block
     dfam::DevDfa* dev_desc = nullptr;  // device copies of `dev` for launches with lookahead 1 and 0
     const dfam::DevDfa* dev_desc_for(uint32_t lookahead) const;
-    uint32_t tuned_chunk_len = 0;    // preferred chunk length (0 = planner default)
+    dfa_tuning_t tuning{};           // per-DFA tuning record (dfa_set_tuning / dfa_autotune)
 };

@@ -239,12 +239,13 @@ struct SmemLayout {
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-__host__ __device__ inline SmemLayout smem_layout(uint32_t table_cap, uint32_t kmax, uint32_t vcap) {
+__host__ __device__ inline SmemLayout smem_layout(uint32_t table_cap, uint32_t kmax, uint32_t vcap,
+                                                  uint32_t stage_bytes) {
     SmemLayout L;
     L.table = 0;
     L.boff = align16(table_cap);
     L.stage = L.boff + 1024;
-    L.lmap = L.stage + 2 * kStageBytes;
+    L.lmap = L.stage + 2 * stage_bytes;
     L.vmap = L.lmap + align16(kThreads * kmax * 2);
     L.meta = L.vmap + align16(vcap * 2);
     L.misc = L.meta + kMaxChunksPerTile * sizeof(ChunkMeta);
@@ -302,6 +303,7 @@ struct TileCtx {
     int sb, placement;
     int ci, r, active;    // my chunk, rank within chunk, has work
     int S;                // staged positions per chunk per segment
+    uint32_t stage_bytes; // bytes of one stage buffer
 };
 
 // ------------------------------------------------------------ staging
@@ -394,7 +396,7 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
     const int nseg = (int)((maxlen + c.S - 1) / c.S);
     const uint32_t esz = off32 ? 4u : 2u;
     for (int seg = 0; seg < nseg; ++seg) {
-        const uint32_t stage = c.stage0 + (uint32_t)(seg & 1) * kStageBytes;
+        const uint32_t stage = c.stage0 + (uint32_t)(seg & 1) * c.stage_bytes;
         if (off32) stage_segment<true>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
         else stage_segment<false>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
         __syncthreads();
@@ -446,7 +448,7 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t) {
 template <int KMAX>
 __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t kmax) {
     extern __shared__ __align__(16) uint8_t sm[];
-    const SmemLayout L = smem_layout(lp.smem_table_cap, kmax, lp.vcap);
+    const SmemLayout L = smem_layout(lp.smem_table_cap, kmax, lp.vcap, lp.stage_bytes);
     ChunkMeta* meta = reinterpret_cast<ChunkMeta*>(sm + L.meta);
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + L.misc);
     uint16_t* vmap = reinterpret_cast<uint16_t*>(sm + L.vmap);
@@ -579,9 +581,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
             c.active = c.r < (int)meta[lo].cnt;
         }
         const uint32_t esz = d.placement == kGlobal ? 4u : 2u;
-        int S = (int)(kStageBytes / ((uint32_t)nch * esz)) & ~7;
+        int S = (int)(lp.stage_bytes / ((uint32_t)nch * esz)) & ~7;
         S = S < 8 ? 8 : (S > kMaxSegLen ? kMaxSegLen : S);
         c.S = S;
+        c.stage_bytes = lp.stage_bytes;
         c.tb = sa(sm + L.table);
         c.gtbl = d.table;
         c.stage0 = sa(sm + L.stage);
@@ -627,8 +630,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
 
 // ------------------------------------------------------------ host side
 
-uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap) {
-    return smem_layout(table_cap, kmax, vcap).total;
+// Shared memory of k_match and the stage-buffer size: the largest stage (up to
+// 64 KB per buffer) that still lets two CTAs share an SM.
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes) {
+    const uint32_t per_sm = 228u * 1024u, reserved = 1024u;
+    uint32_t best = kStageBytes;
+    for (uint32_t sb = 64u * 1024u; sb > kStageBytes; sb -= 2048u) {
+        if (2u * (smem_layout(table_cap, kmax, vcap, sb).total + reserved) <= per_sm) {
+            best = sb;
+            break;
+        }
+    }
+    *stage_bytes = best;
+    return smem_layout(table_cap, kmax, vcap, best).total;
 }
 
 static int g_sm_count = -1, g_dev = -1;
