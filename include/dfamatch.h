@@ -89,8 +89,11 @@ typedef struct {
     uint32_t num_chunks;   /* P; 0 = chosen by the planner                         */
     uint32_t multiplicity; /* the per-chunk state count m in Eqs. (5)-(7)/(10);
                               0 = 1 (a chunk's states run on parallel lanes)      */
-    uint32_t lookahead;    /* reverse-lookahead symbols r: 1 = Algorithm 3 (default),
-                              0 = Algorithm 2 (every chunk matched from all of Q)  */
+    uint32_t lookahead;    /* reverse-lookahead symbols r: 1 = Algorithm 3 (the
+                              default; pass 1 explicitly when using this struct),
+                              0 = Algorithm 2 (every chunk matched from all of Q),
+                              2..8 = the r-symbol sets of Eq. (13), computed per
+                              chunk on the device                                 */
     uint32_t reserved;
     void *match_begin_event; /* optional cudaEvent_t recorded on the stream right before  */
     void *match_end_event;   /* ... and right after the match kernel (for timing it alone) */
@@ -182,6 +185,16 @@ int dfa_match(const dfa_t *dfa, const uint8_t *str, uint64_t len, const dfa_matc
 /* Number of chunks P the planner uses for a single test of len bytes
  * (opts->num_chunks when given); the partition is then dfa_partition(len, P, m). */
 int dfa_plan_chunks(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts, uint32_t *P);
+
+/*
+ * Inspection: run only the planning kernels of a single test on dev_str and
+ * return, for each of its P chunks, the size of the initial-state set it is
+ * matched from (sizes[k] = |I_k|; chunk 0 and chunks preceded only by empty
+ * chunks have 1).  *P receives the chunk count; at most cap sizes are
+ * written.  Allocates a temporary workspace and synchronises the device.
+ */
+int dfa_plan_sets(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
+                  const dfa_match_opts_t *opts, uint32_t *sizes, uint32_t cap, uint32_t *P);
 
 /* Device workspace needed by dfa_match_async for (dfa, len, opts). */
 int dfa_match_workspace_size(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts,

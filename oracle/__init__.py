@@ -11,8 +11,9 @@ It shares no code with ``paper_1210_5093_gb300`` and does not import it.
 * ``compose``    - Eq. (9).
 * ``partition``  - Eqs. (4)-(7) and (10) in exact rational arithmetic.
 * ``weights``    - Eq. (1).
-* ``isets_r``    - Eq. (13) (r reverse-lookahead symbols), by enumerating all
-                   words of length r (exponential; small DFAs only).
+* ``iset_word``  - Eq. (13) for one word of r reverse-lookahead symbols, in C.
+* ``isets_r``    - Eq. (13) for every word of length r, by enumeration
+                   (exponential; small DFAs only).
 
 Parity is pinned for every function here by tests/test_oracle_*.py (worked
 examples printed in the paper, closed-form languages, brute force over all
@@ -61,6 +62,8 @@ def _L():
         lib.oracle_chunked.restype = ctypes.c_int
         lib.oracle_chunked.argtypes = [u32, u32, p, u32, p, p, p, u64, u32, p, p, p, p]
         lib.oracle_compose.argtypes = [u32, p, p, p]
+        lib.oracle_iset_word.restype = u32
+        lib.oracle_iset_word.argtypes = [u32, u32, p, p, p, u32, p]
         lib.oracle_delta_star.restype = u32
         lib.oracle_delta_star.argtypes = [u32, u32, p, u32, p, u32]
         _lib = lib
@@ -146,6 +149,23 @@ class Dfa:
                                           w.ctypes.data if len(w) else None, len(w)))
 
     # ---------------------------------------------------------- Eq. 13
+    def iset_word(self, word: Sequence[int]) -> list:
+        """I_{sigma_1..sigma_r} of Eq. (13) for one symbol word, ascending."""
+        w = np.ascontiguousarray(np.asarray(word, dtype=np.uint32))
+        out = np.zeros(self.Q + 1, dtype=np.uint8)
+        _L().oracle_iset_word(self.Q, self.S, self.delta.ctypes.data, self.final_flags.ctypes.data,
+                              w.ctypes.data if len(w) else None, len(w), out.ctypes.data)
+        return [int(s) for s in np.nonzero(out)[0]]
+
+    def symbols(self, data) -> np.ndarray:
+        """Symbol index of every byte (-1 outside Sigma)."""
+        b = _as_u8(data).astype(np.int64)
+        if self.map is None:
+            return b
+        m = self.map.astype(np.int64)
+        m[m == 0xFF] = -1
+        return m[b]
+
     def isets_r(self, r: int) -> dict:
         """{word: set of states} for every word of r symbols (Eq. 13 with the
         same exclusion as Algorithm 3/4).  Exponential in r."""

@@ -169,6 +169,27 @@ void oracle_compose(uint32_t m, const uint32_t *Li, const uint32_t *Lj, uint32_t
     for (uint32_t k = 0; k < m; ++k) out[k] = Lj[Li[k]];
 }
 
+/*
+ * Eq. (13): I_{sigma_1..sigma_r} = { delta*(x, sigma_1..sigma_r) : x in Q },
+ * minus the excluded states (the same exclusion as Algorithm 3 and 4).
+ * out has Q+1 flags; returns the set's cardinality.
+ */
+uint32_t oracle_iset_word(uint32_t Q, uint32_t S, const int32_t *delta, const uint8_t *final_flags,
+                          const uint32_t *word, uint32_t len, uint8_t *out) {
+    uint8_t *excl = (uint8_t *)malloc(Q + 1);
+    oracle_excluded(Q, S, delta, final_flags, excl);
+    memset(out, 0, Q + 1);
+    for (uint32_t x = 0; x <= Q; ++x) {
+        uint32_t s = x;
+        for (uint32_t i = 0; i < len; ++i) s = step(Q, S, delta, s, word[i]);
+        if (!excl[s]) out[s] = 1;
+    }
+    uint32_t card = 0;
+    for (uint32_t s = 0; s <= Q; ++s) card += out[s];
+    free(excl);
+    return card;
+}
+
 /* delta*(q, w) over a symbol word (Sec. 2.1), used for the r-symbol sets of Eq. (13). */
 uint32_t oracle_delta_star(uint32_t Q, uint32_t S, const int32_t *delta, uint32_t q,
                            const uint32_t *word, uint32_t len) {

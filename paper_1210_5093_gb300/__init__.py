@@ -83,6 +83,7 @@ SIGNATURES = {
     "dfa_partition": (_I, [_U64, _U32, _U32, _P]),
     "dfa_match": (_I, [_P, _P, _U64, _P, _P]),
     "dfa_plan_chunks": (_I, [_P, _U64, _P, _P]),
+    "dfa_plan_sets": (_I, [_P, _P, _U64, _P, _P, _U32, _P]),
     "dfa_match_workspace_size": (_I, [_P, _U64, _P, _P]),
     "dfa_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
     "dfa_match_noalloc": (_I, [_P, _P, _U64, _P, _P, _P]),
@@ -271,6 +272,19 @@ class Dfa:
         _check(lib().dfa_plan_chunks(self._h, n, ctypes.byref(o), ctypes.byref(out)),
                "dfa_plan_chunks")
         return int(out.value)
+
+    def plan_sets(self, dev_data, num_chunks: int = 0, multiplicity: int = 0,
+                  lookahead: int = 1) -> np.ndarray:
+        """|I_k| of every chunk of a single test on dev_data (planning kernels only)."""
+        o = _opts(num_chunks, multiplicity, lookahead)
+        n = dev_data.numel()
+        P = ctypes.c_uint32()
+        _check(lib().dfa_plan_sets(self._h, dev_data.data_ptr() if n else None, n, ctypes.byref(o),
+                                   None, 0, ctypes.byref(P)), "dfa_plan_sets")
+        out = np.zeros(max(1, P.value), dtype=np.uint32)
+        _check(lib().dfa_plan_sets(self._h, dev_data.data_ptr() if n else None, n, ctypes.byref(o),
+                                   out.ctypes.data, P.value, ctypes.byref(P)), "dfa_plan_sets")
+        return out[: P.value]
 
     def workspace_size(self, n: int, num_chunks: int = 0, multiplicity: int = 0,
                        lookahead: int = 1) -> int:

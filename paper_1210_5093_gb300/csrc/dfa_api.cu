@@ -17,7 +17,8 @@ namespace dfam {
 uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes);
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
-                uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr);
+                uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr,
+                bool plan_only = false);
 
 constexpr uint32_t kTilesPerCta = 8;       // persistent CTAs each get about this many tiles
 constexpr uint64_t kMinChunk = 512;        // bytes; shorter chunks cost more in tile overhead
@@ -27,7 +28,8 @@ constexpr uint64_t kMaxChunk = 1ull << 31; // chunk lengths are 32-bit on the de
 inline uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
 WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t ptot, uint32_t nblk,
-                   uint32_t grid, uint32_t stride, bool inline_desc) {
+                   uint32_t grid, uint32_t stride, bool inline_desc, bool dyn = false,
+                   uint64_t set_entries = 0) {
     WsLayout w;
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) { uint64_t r = o; o = up(o + bytes, 256); return r; };
@@ -47,6 +49,8 @@ WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t pt
     w.last_cta = take(4ull * ntests);
     w.seg_hdr = take(16ull * (grid + ntests));
     w.seg_vals = take(2ull * stride * (grid + ntests));
+    w.set_size = take(dyn ? 4ull * ptot : 0);
+    w.sets = take(dyn ? 2ull * set_entries : 0);
     w.total = o;
     return w;
 }
@@ -66,7 +70,15 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
     lp.last_cta = reinterpret_cast<uint32_t*>(base + w.last_cta);
     lp.seg_hdr = reinterpret_cast<uint32_t*>(base + w.seg_hdr);
     lp.seg_vals = reinterpret_cast<uint16_t*>(base + w.seg_vals);
+    lp.set_size = reinterpret_cast<uint32_t*>(base + w.set_size);
+    lp.sets = reinterpret_cast<uint16_t*>(base + w.sets);
 }
+
+// Reverse-lookahead symbols requested by opts: 1 (Algorithm 3) by default,
+// 0 for Algorithm 2, up to kMaxLookahead for Eq. (13).
+constexpr uint32_t kMaxLookahead = 8;
+inline uint32_t opts_lookahead(const dfa_match_opts_t* o) { return o ? o->lookahead : 1u; }
+inline uint32_t seg_stride_for(uint32_t qe_max) { return (qe_max + 1) & ~1u; }
 
 // Launch-specific copy of a DFA's device descriptor.  K is raised when the
 // largest set the launch matches would not fit one tile.
@@ -111,7 +123,8 @@ uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_
 int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
             const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out) {
     if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
-    const uint32_t lookahead = opts ? (opts->lookahead == 0 ? 0u : 1u) : 1u;
+    const uint32_t lookahead = opts_lookahead(opts);
+    if (lookahead > kMaxLookahead) return DFA_EINVAL;
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     Prepared p;
     // group tests by DFA (stable), unique DFAs in first-seen order
@@ -133,6 +146,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         p.dfas.push_back(x);
         p.kmax = std::max(p.kmax, x.K);
         p.vcap = std::max(p.vcap, x.vcap);
+        p.qe_max = std::max(p.qe_max, x.qe);
         if (x.placement == kSmem) p.table_cap = std::max(p.table_cap, (uint32_t)up(x.table_bytes, 16));
     }
     p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap, &p.stage);
@@ -156,10 +170,16 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         t.lookahead = lookahead;
         t.out = i;
         if (p.groups.empty() || p.groups.back().dfa != t.dfa) {
+            if (!p.groups.empty()) {
+                const DevGroup& pg = p.groups.back();
+                p.set_entries += (uint64_t)(pg.end_chunk - pg.first_chunk) * pg.set_stride;
+            }
             DevGroup g{};
             g.first_chunk = (uint32_t)chunks;
             g.dfa = t.dfa;
             g.first_test = j;
+            g.set_stride = std::max(d->h.imax, 1u);
+            g.set_base = p.set_entries;
             p.groups.push_back(g);
         }
         t.group = (uint32_t)p.groups.size() - 1;
@@ -170,8 +190,13 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
     }
     p.ptot = (uint32_t)chunks;
     p.nblk = (p.ptot + 1023) / 1024;
+    {
+        const DevGroup& pg = p.groups.back();
+        p.set_entries += (uint64_t)(pg.end_chunk - pg.first_chunk) * pg.set_stride;
+    }
+    p.dyn = lookahead >= 2 ? 1u : 0u;
     p.ws = ws_layout((uint32_t)p.dfas.size(), count, (uint32_t)p.groups.size(), p.ptot, p.nblk,
-                     p.grid, p.vcap, false);
+                     p.grid, seg_stride_for(p.qe_max), false, p.dyn != 0, p.set_entries);
     *out = std::move(p);
     return DFA_OK;
 }
@@ -183,9 +208,11 @@ void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out
     lp.ptot = p.ptot;
     lp.nblk = p.nblk;
     lp.grid = p.grid;
-    lp.seg_stride = p.vcap;
+    lp.seg_stride = seg_stride_for(p.qe_max);
     lp.smem_table_cap = p.table_cap;
     lp.vcap = p.vcap;
+    lp.qe_max = p.qe_max;
+    lp.dyn = p.dyn;
     lp.stage_bytes = p.stage;
     lp.dfas = reinterpret_cast<const DevDfa*>(ws + p.ws.dfas);
     lp.tests = reinterpret_cast<const DevTest*>(ws + p.ws.tests);
@@ -235,8 +262,8 @@ int launch_single(const Single& s, void* stream, void* ev_begin, void* ev_end) {
 int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Single* s) {
     if (!d) return DFA_EINVAL;
     if (!d->on_device) return DFA_EHOSTONLY;
-    const uint32_t lookahead = opts ? (opts->lookahead == 0 ? 0u : 1u) : 1u;
-    if (!lookahead && d->h.qe > 4096) return DFA_EINVAL;
+    const uint32_t lookahead = opts_lookahead(opts);
+    if (lookahead > kMaxLookahead) return DFA_EINVAL;
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     DevDfa x = launch_desc(d, lookahead);
     const uint32_t tcap = x.placement == kSmem ? (uint32_t)up(x.table_bytes, 16) : 0u;
@@ -254,10 +281,12 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.ptot = P;
     lp.nblk = (P + 1023) / 1024;
     lp.grid = grid;
-    lp.seg_stride = x.vcap;
+    lp.seg_stride = seg_stride_for(x.qe);
     lp.smem_table_cap = tcap;
     lp.vcap = x.vcap;
     lp.stage_bytes = stage;
+    lp.qe_max = x.qe;
+    lp.dyn = lookahead >= 2 ? 1u : 0u;
     lp.dfas = d->dev_desc_for(lookahead);
     lp.tests = nullptr;
     lp.groups = nullptr;
@@ -274,7 +303,10 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.group1.end_chunk = P;
     lp.group1.dfa = 0;
     lp.group1.first_test = 0;
-    s->ws = ws_layout(1, 1, 1, P, lp.nblk, grid, x.vcap, true);
+    lp.group1.set_stride = std::max(d->h.imax, 1u);
+    lp.group1.set_base = 0;
+    s->ws = ws_layout(1, 1, 1, P, lp.nblk, grid, lp.seg_stride, true, lp.dyn != 0,
+                      (uint64_t)P * lp.group1.set_stride);
     return DFA_OK;
 }
 
@@ -325,6 +357,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         const uint64_t o_b16 = take(512), o_b32 = take(1024), o_bc = take(512);
         const uint64_t o_ioff = take(4 * h.iset_off.size()), o_iset = take(2 * h.iset.size());
         const uint64_t o_pos = take(2 * h.pos.size()), o_acc = take(h.accept.size());
+        const uint64_t o_exc = take(h.excluded.size());
         uint8_t* blk = nullptr;
         if (cudaMalloc(&blk, o) != cudaSuccess) {
             cudaGetLastError();
@@ -341,6 +374,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         x.iset = reinterpret_cast<const uint16_t*>(blk + o_iset);
         x.pos = reinterpret_cast<const uint16_t*>(blk + o_pos);
         x.accept = blk + o_acc;
+        x.excluded = blk + o_exc;
         d->dev_desc = reinterpret_cast<DevDfa*>(blk + o_desc);
         DevDfa descs[2] = {launch_desc(d, 1), launch_desc(d, 0)};
         bool ok = cudaMemcpy(blk + o_desc, descs, sizeof descs, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -351,7 +385,8 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
                   cudaMemcpy(blk + o_ioff, h.iset_off.data(), 4 * h.iset_off.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_iset, h.iset.data(), 2 * h.iset.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_pos, h.pos.data(), 2 * h.pos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(blk + o_acc, h.accept.data(), h.accept.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+                  cudaMemcpy(blk + o_acc, h.accept.data(), h.accept.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_exc, h.excluded.data(), h.excluded.size(), cudaMemcpyHostToDevice) == cudaSuccess;
         if (!ok) {
             cudaFree(blk);
             delete d;
@@ -523,6 +558,38 @@ int dfa_iset(const dfa_t* d, uint32_t c, uint32_t* states, uint32_t cap, uint32_
 int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t* starts) {
     if (P == 0 || m == 0 || !starts) return DFA_EINVAL;
     for (uint32_t k = 0; k <= P; ++k) starts[k] = chunk_start(n, P, m, k);
+    return DFA_OK;
+}
+
+int dfa_plan_sets(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
+                  const dfa_match_opts_t* opts, uint32_t* sizes, uint32_t cap, uint32_t* P) {
+    if (!P || (len && !dev_str)) return DFA_EINVAL;
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    *P = s.lp.ptot;
+    uint8_t* ws = nullptr;
+    if (cudaMalloc(&ws, s.ws.total) != cudaSuccess) { cudaGetLastError(); return DFA_ENOMEM; }
+    s.lp.test1.str = dev_str;
+    bind(s.lp, ws, s.ws);
+    s.lp.results = nullptr;
+    rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr, nullptr, nullptr, true);
+    const uint32_t n = std::min(cap, s.lp.ptot);
+    std::vector<uint16_t> cls(n);
+    std::vector<uint32_t> dyn(n);
+    if (rc == DFA_OK && n) {
+        if (cudaMemcpy(cls.data(), s.lp.chunk_cls, 2ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = DFA_ECUDA;
+        if (rc == DFA_OK && s.lp.dyn &&
+            cudaMemcpy(dyn.data(), s.lp.set_size, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = DFA_ECUDA;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = DFA_ECUDA;
+    cudaFree(ws);
+    if (rc != DFA_OK) return rc;
+    const HostDfa& h = d->h;
+    for (uint32_t k = 0; k < n; ++k)
+        sizes[k] = cls[k] == dyn_set(h.C) ? dyn[k] : h.iset_off[cls[k] + 1] - h.iset_off[cls[k]];
     return DFA_OK;
 }
 
@@ -719,7 +786,7 @@ int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) 
 
 int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
     if (!b || !n) return DFA_EINVAL;
-    *n = 6;
+    *n = b->p.dyn ? 7 : 6;
     return DFA_OK;
 }
 

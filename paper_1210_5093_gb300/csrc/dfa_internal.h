@@ -35,6 +35,7 @@ struct DevDfa {
     const uint16_t* iset;        // CSR members (ascending)
     const uint16_t* pos;         // [(C+2)*qe] index of state s in set c, kNone16 if absent
     const uint8_t* accept;       // [qe] 1 iff accepting
+    const uint8_t* excluded;     // [qe] 1 iff left out of every initial-state set
     uint32_t qe;                 // states incl. q_e
     uint32_t qpad;               // row stride (entries)
     uint32_t C;                  // classes (without the start set)
@@ -66,7 +67,18 @@ static_assert(sizeof(DevTest) == 48, "DevTest layout");
 
 struct DevGroup {
     uint32_t first_chunk, end_chunk, dfa, first_test;
+    uint32_t set_stride;  // entries per chunk in the lookahead-set arena (r >= 2)
+    uint32_t pad_;
+    uint64_t set_base;    // offset (entries) of the group's first chunk in that arena
 };
+static_assert(sizeof(DevGroup) == 32, "DevGroup layout");
+
+// Set index of a chunk whose initial-state set was computed from r >= 2
+// lookahead symbols (Eq. 13) and stored in the launch's set arena.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t dyn_set(uint32_t C) { return C + 2; }
 
 // Device-side result (layout identical to dfa_result_t).
 static_assert(sizeof(dfa_result_t) == 12, "dfa_result_t layout");
@@ -94,8 +106,12 @@ struct LaunchPlan {
     uint32_t* arrived;          // [ntests]
     uint32_t* first_cta;        // [ntests]
     uint32_t* last_cta;         // [ntests]
-    uint32_t* seg_hdr;          // [(grid+ntests)*4]: first chunk, nchunks, class, size
-    uint16_t* seg_vals;         // [(grid+ntests)*seg_stride]
+    uint32_t* seg_hdr;          // [(grid+ntests)*4]: first chunk, nchunks, -, -
+    uint16_t* seg_vals;         // [(grid+ntests)*seg_stride]: dense maps over Q
+    uint16_t* sets;             // lookahead-set arena (r >= 2), see DevGroup
+    uint32_t* set_size;         // [ptot] |I| of each chunk computed by k_lookahead
+    uint32_t dyn;               // 1 if some test uses r >= 2 lookahead symbols
+    uint32_t qe_max;            // largest |Q|+1 of the launch's DFAs
     dfa_result_t* results;      // [ntests] in the caller's order (DevTest::out)
     // single-test launches carry their descriptors by value (tests/groups == nullptr)
     DevTest test1;
@@ -105,7 +121,7 @@ struct LaunchPlan {
 // Workspace carve-up of one launch (byte offsets into the device workspace).
 struct WsLayout {
     uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, bsum, tile_first, tile_base,
-        num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, total;
+        num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
 };
 
 // A batch planned on the host: descriptors, sizes and the workspace layout.
@@ -114,6 +130,8 @@ struct Prepared {
     std::vector<DevTest> tests;
     std::vector<DevGroup> groups;
     uint32_t ptot = 0, nblk = 0, grid = 0, kmax = 2, vcap = 1, table_cap = 0, smem = 0, stage = 0;
+    uint32_t qe_max = 1, dyn = 0;
+    uint64_t set_entries = 0;
     WsLayout ws{};
 };
 

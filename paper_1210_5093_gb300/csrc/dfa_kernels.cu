@@ -111,6 +111,99 @@ __device__ __forceinline__ DevGroup group_at(const LaunchPlan& lp, uint32_t i) {
 
 // ------------------------------------------------------------ planning
 
+__device__ __forceinline__ uint32_t find_test(const LaunchPlan& lp, uint32_t g) {
+    uint32_t lo = 0, hi = lp.ntests - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (test_at(lp, mid).chunk_base <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kLaWarps = 8;
+
+// r-symbol reverse lookahead (Eq. 13), one warp per chunk: with sigma_1..sigma_j
+// the j = min(r, Start(k)) bytes before the chunk, I = delta*(Q, sigma_1..sigma_j)
+// minus the excluded states, computed as I_{sigma_1} pushed through
+// sigma_2..sigma_j (excluded states are absorbing, so dropping them at every
+// step is exact).  A bitmap over Q removes duplicates and yields the set in
+// ascending order.  Chunks with j < 2 are left to k_count (start set or one
+// symbol).  Shared memory per warp: qe_words bitmap words + vcap set entries.
+__global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint32_t qe_words,
+                                                          uint32_t set_words) {
+    extern __shared__ uint32_t la_sm[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* bm = la_sm + (size_t)w * (qe_words + set_words);
+    uint16_t* buf = reinterpret_cast<uint16_t*>(bm + qe_words);
+    const uint32_t g = blockIdx.x * kLaWarps + (uint32_t)w;
+    if (g >= lp.ptot) return;  // warp-uniform
+    const uint32_t ti = find_test(lp, g);
+    const DevTest t = test_at(lp, ti);
+    if (t.lookahead < 2) return;
+    const DevDfa& d = lp.dfas[t.dfa];
+    const uint64_t st = dstart(t.n, t.P, t.m, g - t.chunk_base);
+    const uint32_t j = (uint32_t)(st < t.lookahead ? st : t.lookahead);
+    if (j < 2) return;
+    const DevGroup gr = group_at(lp, t.group);
+    uint16_t* out = lp.sets + gr.set_base + (uint64_t)(g - gr.first_chunk) * gr.set_stride;
+    const uint8_t* p = t.str + (st - j);
+    uint32_t c = d.byte_class[p[0]];
+    if (c == kNone16) {
+        if (lane == 0) { atomicOr(lp.test_err + ti, 1u); lp.set_size[g] = 0; }
+        return;
+    }
+    uint32_t n = d.iset_off[c + 1] - d.iset_off[c];
+    for (uint32_t x = lane; x < n; x += 32) buf[x] = d.iset[d.iset_off[c] + x];
+    __syncwarp();
+    const uint32_t words = (d.qe + 31) / 32;
+    const uint32_t wpl = (words + 31) / 32;  // bitmap words per lane
+    for (uint32_t i = 1; i < j; ++i) {
+        c = d.byte_class[p[i]];
+        if (c == kNone16) {
+            if (lane == 0) { atomicOr(lp.test_err + ti, 1u); lp.set_size[g] = 0; }
+            return;
+        }
+        for (uint32_t x = lane; x < words; x += 32) bm[x] = 0;
+        __syncwarp();
+        const uint8_t* row = d.table + (size_t)c * d.qpad * d.sb;
+        for (uint32_t x = lane; x < n; x += 32) {
+            const uint32_t s = buf[x];
+            const uint32_t nx = d.sb == 1 ? row[s] : (uint32_t)(reinterpret_cast<const uint16_t*>(row)[s] >> 1);
+            if (!d.excluded[nx]) atomicOr(bm + (nx >> 5), 1u << (nx & 31));
+        }
+        __syncwarp();
+        // ascending compaction: lane L owns bitmap words [L*wpl, (L+1)*wpl)
+        uint32_t cnt = 0;
+        for (uint32_t k = 0; k < wpl; ++k) {
+            const uint32_t wi = lane * wpl + k;
+            if (wi < words) cnt += __popc(bm[wi]);
+        }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t pos = incl - cnt;
+        __syncwarp();
+        for (uint32_t k = 0; k < wpl; ++k) {
+            const uint32_t wi = lane * wpl + k;
+            if (wi >= words) break;
+            uint32_t bits = bm[wi];
+            while (bits) {
+                const uint32_t b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                buf[pos++] = (uint16_t)(wi * 32 + b);
+            }
+        }
+        n = total;
+        __syncwarp();
+    }
+    for (uint32_t x = lane; x < n; x += 32) out[x] = buf[x];
+    if (lane == 0) lp.set_size[g] = n;
+}
+
 // Per chunk: owning test, reverse-lookahead class (Algorithm 3 line 16) and
 // the thread slots it is charged: ceil(|I_k| / K), at least 2.
 __global__ void __launch_bounds__(kPlanThreads) k_count(LaunchPlan lp) {
@@ -118,11 +211,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_count(LaunchPlan lp) {
     const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
     uint32_t cost = 0;
     if (g < lp.ptot) {
-        uint32_t lo = 0, hi = lp.ntests - 1;
-        while (lo < hi) {
-            uint32_t mid = (lo + hi + 1) >> 1;
-            if (test_at(lp, mid).chunk_base <= g) lo = mid; else hi = mid - 1;
-        }
+        const uint32_t lo = find_test(lp, g);
         const DevTest t = test_at(lp, lo);
         const DevDfa& d = lp.dfas[t.dfa];
         const uint32_t k = g - t.chunk_base;
@@ -139,8 +228,9 @@ __global__ void __launch_bounds__(kPlanThreads) k_count(LaunchPlan lp) {
                 c = d.C;
             }
             cls = c;
+            if (t.lookahead >= 2 && st >= 2 && c != d.C) cls = dyn_set(d.C);  // Eq. 13 set from k_lookahead
         }
-        const uint32_t size = d.iset_off[cls + 1] - d.iset_off[cls];
+        const uint32_t size = cls == dyn_set(d.C) ? lp.set_size[g] : d.iset_off[cls + 1] - d.iset_off[cls];
         const uint32_t cnt = (size + d.K - 1) / d.K;
         cost = cnt < 2 ? 2 : cnt;
         lp.chunk_test[g] = lo;
@@ -221,20 +311,23 @@ __global__ void __launch_bounds__(kPlanThreads) k_tiles(LaunchPlan lp) {
 // ------------------------------------------------------------ matching
 
 struct ChunkMeta {
-    const uint8_t* ptr;  // first byte of the chunk
-    uint32_t len;        // bytes
+    const uint8_t* ptr;     // first byte of the chunk
+    const uint16_t* init;   // its initial-state set (ascending)
+    uint32_t len;           // bytes
     uint32_t test;
-    uint16_t toff;       // first thread (tile-local) of the chunk
-    uint16_t cls;        // set index (class, start set, or all of Q)
-    uint16_t cnt;        // threads actually used: ceil(|I|/K)
-    uint8_t lo_slack;    // min(bytes of the string before the chunk, 255)
-    uint8_t hi_slack;    // min(bytes of the string after the chunk, 255)
+    uint16_t toff;          // first thread (tile-local) of the chunk
+    uint16_t cls;           // set index (class, start set, all of Q, or dyn_set)
+    uint16_t cnt;           // threads actually used: ceil(|I|/K)
+    uint16_t size;          // |I|
+    uint8_t lo_slack;       // min(bytes of the string before the chunk, 255)
+    uint8_t hi_slack;       // min(bytes of the string after the chunk, 255)
+    uint8_t pad_[6];
 };
-static_assert(sizeof(ChunkMeta) == 24, "ChunkMeta layout");
+static_assert(sizeof(ChunkMeta) == 40, "ChunkMeta layout");
 
 // Shared-memory carve-up of k_match (byte offsets, all 16-byte aligned).
 struct SmemLayout {
-    uint32_t table, boff, stage, lmap, vmap, meta, misc, desc, total;
+    uint32_t table, boff, stage, lmap, linit, vmap, vdom, meta, misc, desc, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -246,8 +339,10 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t table_cap, uint32_t k
     L.boff = align16(table_cap);
     L.stage = L.boff + 1024;
     L.lmap = L.stage + 2 * stage_bytes;
-    L.vmap = L.lmap + align16(kThreads * kmax * 2);
-    L.meta = L.vmap + align16(vcap * 2);
+    L.linit = L.lmap + align16(kThreads * kmax * 2);
+    L.vmap = L.linit + align16(kThreads * kmax * 2);
+    L.vdom = L.vmap + align16(vcap * 2);
+    L.meta = L.vdom + align16(vcap * 2);
     L.misc = L.meta + kMaxChunksPerTile * sizeof(ChunkMeta);
     L.desc = L.misc + 64;
     L.total = L.desc + align16(sizeof(DevDfa));
@@ -255,7 +350,7 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t table_cap, uint32_t k
 }
 
 // misc words
-enum { M_MAXLEN = 0, M_LAST = 1, M_DFA = 2 };
+enum { M_MAXLEN = 0, M_LAST = 1, M_DFA = 2, M_CELL = 3 };
 
 // Advance K chains of one chunk over one staged segment of S positions.
 // Shared-memory table, 16-bit row offsets, StBytes-sized entries.
@@ -299,7 +394,8 @@ struct TileCtx {
     uint32_t tb;          // shared address of the table (smem placement)
     const uint8_t* gtbl;  // global table (L2 placement)
     uint32_t stage0;      // shared address of stage buffer 0
-    uint32_t lmap;        // shared address of the tile map
+    uint32_t lmap;        // shared address of the tile map (final states per chain)
+    uint32_t linit;       // shared address of the chains' initial states
     int sb, placement;
     int ci, r, active;    // my chunk, rank within chunk, has work
     int S;                // staged positions per chunk per segment
@@ -381,12 +477,15 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
     const uint32_t sh = d.sb == 2 ? 1 : 0;
     if (c.active) {
         const ChunkMeta m = meta[c.ci];
-        const uint32_t base = d.iset_off[m.cls], size = d.iset_off[m.cls + 1] - base;
+        const uint32_t size = m.size;
 #pragma unroll
         for (int u = 0; u < K; ++u) {
             uint32_t slot = (uint32_t)c.r * K + u;
             if (slot >= size) slot = (uint32_t)c.r * K;  // padding chain: repeat the first
-            s[u] = (uint32_t)d.iset[base + slot] << sh;
+            const uint32_t init = m.init[slot];
+            s[u] = init << sh;
+            asm volatile("st.shared.u16 [%0], %1;" :: "r"(c.linit + 2u * ((uint32_t)(threadIdx.x) * K + u)),
+                         "h"((uint16_t)init) : "memory");
         }
     } else {
 #pragma unroll
@@ -423,26 +522,51 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
 }
 
 // Final state of test t from its segment maps (slots b + t for b in
-// [first_cta, last_cta]), composed in order by one thread: Eq. (8) applied
-// segment by segment.
-__device__ void combine_test(const LaunchPlan& lp, uint32_t t) {
+// [first_cta, last_cta]), applied in order to q0: Eq. (8) segment by segment.
+// Each segment map is dense over Q (identity outside its domain), so one
+// step is one lookup; the maps are staged through shared memory (`buf`,
+// buf_bytes) in batches so the dependent chain runs at shared-memory latency.
+// Called by all threads of the CTA.
+__device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uint32_t buf_bytes,
+                             uint32_t* cell) {
     const DevTest tt = test_at(lp, t);
     const DevDfa& d = lp.dfas[tt.dfa];
     const uint32_t b0 = __ldcg(lp.first_cta + t), b1 = __ldcg(lp.last_cta + t);
-    uint32_t s = __ldcg(lp.seg_vals + (size_t)(b0 + t) * lp.seg_stride);
-    for (uint32_t b = b0 + 1; b <= b1; ++b) {
-        const size_t slot = b + t;
-        const uint32_t cls = __ldcg(lp.seg_hdr + slot * 4 + 2);
-        const uint32_t p = d.pos[(size_t)cls * d.qe + s];
-        if (p != kNone16) s = __ldcg(lp.seg_vals + slot * lp.seg_stride + p);
+    const uint32_t nseg = b1 - b0 + 1;
+    const uint32_t qe = d.qe;
+    const uint32_t words = (qe + 1) / 2;  // u32 words per map
+    const uint32_t per = buf_bytes / (4 * words);
+    uint32_t* sm = reinterpret_cast<uint32_t*>(buf);
+    if (threadIdx.x == 0) *cell = d.q0;
+    for (uint32_t i0 = 0; i0 < nseg; i0 += per) {
+        const uint32_t nb = min(per, nseg - i0);
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < nb * words; k += kThreads) {
+            const uint32_t j = k / words, w = k - j * words;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(
+                lp.seg_vals + (size_t)(b0 + i0 + j + t) * lp.seg_stride);
+            sm[j * words + w] = __ldcg(src + w);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t s = *cell;
+            const uint16_t* m = reinterpret_cast<const uint16_t*>(sm);
+            for (uint32_t j = 0; j < nb; ++j) s = m[(size_t)j * 2 * words + s];
+            *cell = s;
+        }
     }
-    dfa_result_t r;
-    const uint32_t err = atomicOr(lp.test_err + t, 0u);
-    r.final_state = err ? 0u : s;
-    r.accept = err ? 0 : d.accept[s];
-    r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
-    r.status = err ? DFA_ESYMBOL : DFA_OK;
-    lp.results[tt.out] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t s = *cell;
+        dfa_result_t r;
+        const uint32_t err = atomicOr(lp.test_err + t, 0u);
+        r.final_state = err ? 0u : s;
+        r.accept = err ? 0 : d.accept[s];
+        r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
+        r.status = err ? DFA_ESYMBOL : DFA_OK;
+        lp.results[tt.out] = r;
+    }
+    __syncthreads();
 }
 
 template <int KMAX>
@@ -452,7 +576,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
     ChunkMeta* meta = reinterpret_cast<ChunkMeta*>(sm + L.meta);
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + L.misc);
     uint16_t* vmap = reinterpret_cast<uint16_t*>(sm + L.vmap);
+    uint16_t* vdom = reinterpret_cast<uint16_t*>(sm + L.vdom);
     const uint16_t* lmap = reinterpret_cast<const uint16_t*>(sm + L.lmap);
+    const uint16_t* linit = reinterpret_cast<const uint16_t*>(sm + L.linit);
     const int tid = threadIdx.x;
 
     const uint32_t T = *lp.num_tiles;
@@ -492,8 +618,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
             }
             return;
         }
+        // publish this CTA's part of the test as a dense map over Q: identity
+        // outside the segment's domain (those states are excluded, hence fixed)
         const size_t slot = (size_t)b + (size_t)cur_test;
-        for (uint32_t x = tid; x < nD; x += kThreads) lp.seg_vals[slot * lp.seg_stride + x] = vmap[x];
+        uint16_t* dense = lp.seg_vals + slot * lp.seg_stride;
+        for (uint32_t s = tid; s < d.qe; s += kThreads) dense[s] = (uint16_t)s;
+        __syncthreads();
+        for (uint32_t x = tid; x < nD; x += kThreads) dense[vdom[x]] = vmap[x];
         if (tid == 0) {
             lp.seg_hdr[slot * 4 + 0] = seg_first;
             lp.seg_hdr[slot * 4 + 1] = seg_n;
@@ -510,10 +641,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
         }
         __syncthreads();
         if (misc[M_LAST]) {
-            if (tid == 0) {
-                __threadfence();
-                combine_test(lp, (uint32_t)cur_test);
-            }
+            __threadfence();
+            // the stage buffers are free during the composition phase
+            combine_test(lp, (uint32_t)cur_test, sm + L.stage, 2 * lp.stage_bytes, misc + M_CELL);
         }
         __syncthreads();
     };
@@ -552,8 +682,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
             const uint32_t k = g - tt.chunk_base;
             const uint64_t st = dstart(tt.n, tt.P, tt.m, k), en = dstart(tt.n, tt.P, tt.m, k + 1);
             const uint32_t cls = lp.chunk_cls[g];
-            const uint32_t size = d.iset_off[cls + 1] - d.iset_off[cls];
             ChunkMeta m;
+            uint32_t size;
+            if (cls == dyn_set(d.C)) {
+                const DevGroup gr = group_at(lp, tt.group);
+                size = lp.set_size[g];
+                m.init = lp.sets + gr.set_base + (uint64_t)(g - gr.first_chunk) * gr.set_stride;
+            } else {
+                size = d.iset_off[cls + 1] - d.iset_off[cls];
+                m.init = d.iset + d.iset_off[cls];
+            }
+            m.size = (uint16_t)size;
             m.ptr = tt.str + st;
             m.len = (uint32_t)(en - st);
             m.test = te;
@@ -589,6 +728,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
         c.gtbl = d.table;
         c.stage0 = sa(sm + L.stage);
         c.lmap = sa(sm + L.lmap);
+        c.linit = sa(sm + L.linit);
         c.sb = (int)d.sb;
         c.placement = (int)d.placement;
         const uint32_t boff = sa(sm + L.boff);
@@ -611,8 +751,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
                 seg_first = gA + (uint32_t)i;
                 seg_n = 0;
                 seg_cls = m.cls;
-                nD = d.iset_off[m.cls + 1] - d.iset_off[m.cls];
-                for (uint32_t x = tid; x < nD; x += kThreads) vmap[x] = lmap[base + x];
+                nD = m.size;
+                for (uint32_t x = tid; x < nD; x += kThreads) {
+                    vmap[x] = lmap[base + x];
+                    vdom[x] = linit[base + x];
+                }
+            } else if (m.cls == dyn_set(d.C)) {
+                // the chunk's set came from r >= 2 lookahead symbols: find the
+                // entering state's slot by binary search in its initial states
+                const uint16_t* keys = linit + base;
+                for (uint32_t x = tid; x < nD; x += kThreads) {
+                    const uint32_t v = vmap[x];
+                    uint32_t lo = 0, hi = m.size;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (keys[mid] < v) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < m.size && keys[lo] == v) vmap[x] = lmap[base + lo];
+                }
             } else {
                 const uint16_t* pos = d.pos + (size_t)m.cls * d.qe;
                 for (uint32_t x = tid; x < nD; x += kThreads) {
@@ -672,23 +828,36 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
     return kmax > 8 ? grid_for<16>(smem, grid) : grid_for<8>(smem, grid);
 }
 
-// Issue the whole launch on `st`: memsets of the per-test counters, five
-// planning kernels and the match kernel.  Returns the number of kernels.
+// Issue the whole launch on `st`: memsets of the per-test counters, the
+// planning kernels (k_lookahead only for r >= 2) and the match kernel.
+// With plan_only the match kernel is skipped.
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
-                uint32_t* kernels, void* ev_begin, void* ev_end) {
+                uint32_t* kernels, void* ev_begin, void* ev_end, bool plan_only) {
     if (cudaMemsetAsync(lp.test_err, 0, sizeof(uint32_t) * lp.ntests * 2, st) != cudaSuccess)
         return DFA_ECUDA;  // test_err and arrived are adjacent
     const uint32_t nb = lp.nblk;
+    uint32_t nk = 6;
+    if (lp.dyn) {
+        const uint32_t qe_words = (lp.qe_max + 31) / 32, set_words = (lp.vcap + 1) / 2;
+        const uint32_t smem = kLaWarps * (qe_words + set_words) * 4;
+        k_lookahead<<<(lp.ptot + kLaWarps - 1) / kLaWarps, kLaWarps * 32, smem, st>>>(lp, qe_words,
+                                                                                   set_words);
+        ++nk;
+    }
     k_count<<<nb, kPlanThreads, 0, st>>>(lp);
     k_scan_blocks<<<1, kPlanThreads, 0, st>>>(lp);
     k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
     k_group_tiles<<<1, kPlanThreads, 0, st>>>(lp);
     k_tiles<<<nb, kPlanThreads, 0, st>>>(lp);
+    if (plan_only) {
+        if (kernels) *kernels = nk - 1;
+        return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
+    }
     if (ev_begin) cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), st);
     if (kmax > 8) k_match<16><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
     else k_match<8><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
     if (ev_end) cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st);
-    if (kernels) *kernels = 6;
+    if (kernels) *kernels = nk;
     return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
 }
 

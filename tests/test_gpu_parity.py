@@ -238,3 +238,74 @@ def test_protein_full_size_10GB(dm):
     (fs, acc, st), = dm.results_from(out)
     est, efs, eacc = _expect(w.spec, w.data)
     assert (st, fs, acc) == (0, efs, eacc)
+
+
+def _expected_set_sizes(spec, data, P, r):
+    """|I_k| per chunk from the oracle: Eq. (13) on the min(r, Start(k)) symbols
+    before chunk k (Eq. 11 when that is one symbol); 1 for the start set."""
+    od = oracle.Dfa.from_spec(spec)
+    starts = oracle.chunk_starts(len(data), P, 1)
+    sym = od.symbols(data)
+    out = []
+    for k in range(P):
+        st = starts[k]
+        if k == 0 or st == 0:
+            out.append(1)
+            continue
+        j = min(r, st) if r >= 1 else 0
+        out.append(len(od.iset_word(sym[st - j:st].tolist())))
+    return out
+
+
+@pytest.mark.parametrize("r", [2, 3, 4])
+def test_lookahead_r_symbols_parity(dm, r):
+    from tests._golden import dfa_from, load, symbol_map
+    for name in ("w1_fig1.txt", "w2_fig6.txt"):
+        f = load(name)
+        Q, syms, delta, q0, finals = dfa_from(f)
+        spec = gen.DfaSpec(Q, len(syms), delta, q0, np.array(finals, np.uint32), symbol_map(syms))
+        d = dm.Dfa.from_spec(spec)
+        text = f["input"][0][0].encode()
+        for P in (1, 2, 3, 7, 36):
+            _check(dm, d, spec, text, num_chunks=P, lookahead=r)
+    for seed in range(3):
+        spec = gen.random_dfa(6000 + seed, [5, 40, 300][seed], [2, 7, 20][seed], num_finals=3,
+                              missing=0.05 * seed)
+        m = np.full(256, 0xFF, dtype=np.uint8)
+        m[:spec.num_symbols] = np.arange(spec.num_symbols)
+        spec.byte_to_symbol = m
+        d = dm.Dfa.from_spec(spec)
+        data = (gen.uniform_bytes(6100 + seed, 200_000) % spec.num_symbols).astype(np.uint8)
+        for n in (0, 1, 2, 3, 5, 100, 200_000):
+            for P in (0, 2, 3, 77, 5000):
+                _check(dm, d, spec, data[:n], num_chunks=P, lookahead=r)
+    for w in (gen.regex_workload(2, 8 << 20), gen.protein_workload(3, 8 << 20)):
+        d = dm.Dfa.from_spec(w.spec)
+        for P in (0, 3000):
+            _check(dm, d, w.spec, w.data, num_chunks=P, lookahead=r)
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_lookahead_sets_equal_eq13(dm, r):
+    import torch
+    for w in (gen.regex_workload(2, 1 << 20), gen.protein_workload(3, 1 << 20)):
+        d = dm.Dfa.from_spec(w.spec)
+        dev = torch.from_numpy(w.data).cuda()
+        P = 2000
+        got = d.plan_sets(dev, num_chunks=P, lookahead=r).tolist()
+        assert got == _expected_set_sizes(w.spec, w.data, P, r)
+        if r > 1:  # the lemma of Sec. 4.3, chunk by chunk
+            one = d.plan_sets(dev, num_chunks=P, lookahead=1)
+            assert all(a <= b for a, b in zip(got, one.tolist()))
+
+
+def test_lookahead_sets_with_bad_byte(dm):
+    spec = gen.protein_dfa(3)
+    d = dm.Dfa.from_spec(spec)
+    data = gen.protein_text(3, 1 << 20)
+    for pos in (0, 2, 1000, 4096, 4097):
+        bad = data.copy()
+        bad[pos] = ord("J")
+        for r in (2, 4):
+            st, _, _ = d.match(bad, num_chunks=256, lookahead=r)
+            assert st == dm.ESYMBOL

@@ -197,6 +197,19 @@ def test_lemma_imax_nonincreasing(seed):
     assert vals[0] == imax1
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_eq13_word_sets_match_enumeration(seed):
+    spec = gen.random_dfa(950 + seed, 5 + seed, 2 + seed % 2, num_finals=1, missing=0.2 * (seed % 2))
+    d = oracle.Dfa.from_spec(spec)
+    flags, _ = d.isets()
+    for a in range(spec.num_symbols):                       # r = 1 is Eq. (11)
+        assert d.iset_word([a]) == np.nonzero(flags[a])[0].tolist()
+    for r in (2, 3):
+        for word, img in d.isets_r(r).items():             # enumeration over all x in Q
+            assert d.iset_word(list(word)) == sorted(img)
+            assert set(img) <= set(np.nonzero(flags[word[-1]])[0].tolist())   # lemma per word
+
+
 def test_composition_eq9_matches_sequential_merge():
     # each symbol permutes the states, so the chunk maps stay non-constant
     delta = np.stack([gen.permutation(gen.key(31, a), 7) for a in range(3)], axis=1)
