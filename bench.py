@@ -107,21 +107,15 @@ class Clocks:
         return out
 
 
-def lookups_per_launch(dm, d, data: np.ndarray, P: int, m: int = 1) -> tuple:
+def lookups_per_launch(dm, d, dev, n: int, num_chunks: int = 0, lookahead: int = 1) -> tuple:
     """Algorithmic work of one launch (the second term of Eq. 16):
-    W = L_0 + sum_{k>=1} L_k |I_k|, with I_k the set of chunk k's reverse
-    lookahead class (the start set for chunks preceded only by empty chunks)."""
-    starts = dm.partition(len(data), P, m).astype(np.int64)
-    lens = np.diff(starts)
-    info = d.info()
-    sizes = np.array([len(d.iset(c)) for c in range(info.num_classes)] + [1], dtype=np.int64)
-    cls = d.class_of_bytes().astype(np.int64)
-    look = np.full(P, info.num_classes, dtype=np.int64)
-    nz = starts[:-1] > 0
-    look[nz] = cls[data[starts[:-1][nz] - 1]]
-    look[0] = info.num_classes
-    W = int((lens * sizes[look]).sum())
-    return W, float(sizes[look][1:].mean()) if P > 1 else 1.0
+    W = L_0 + sum_{k>=1} L_k |I_k|.  |I_k| comes from the planning kernels
+    (dfa_plan_sets), the chunk lengths from the partition (dfa_partition)."""
+    sizes = d.plan_sets(dev, num_chunks=num_chunks, lookahead=lookahead).astype(np.int64)
+    P = len(sizes)
+    lens = np.diff(dm.partition(n, P, 1).astype(np.int64))
+    W = int((lens * sizes).sum())
+    return W, float(sizes[1:].mean()) if P > 1 else 1.0
 
 
 def _traffic_record(workload: str):
@@ -277,6 +271,89 @@ def serving_leg(dm, dfas, datas, rate_gbs: float, seconds: float = 2.0, budget: 
             "budget_bytes": budget}, done, sub
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank matches its own independent test: the work shards by test,
+    with no collective on the data path (weak scaling)."""
+    return base + rank
+
+
+def reduce_job(dist, device, bytes_per_rank: int, steps: int, elapsed_ms: float, world: int):
+    """Whole-job throughput: all ranks' bytes over the slowest rank's time
+    (max over ranks of the timed region).  Returns (GB/s, max elapsed ms)."""
+    import torch
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return bytes_per_rank * world * steps / (ms_max / 1e3) / 1e9, ms_max
+
+
+def run_batch_config(args, dm, torch):
+    """Batched config: 64 DFAs (|Q| log-uniform 8-1288, byte folded/unfolded and
+    20-letter alphabets, gamma_max 0.02-0.47), 4096 tests with lengths
+    log-uniform 256 B - 64 MiB, each DFA autotuned, one persistent
+    graph-replayed launch vs the plain path (one call per test)."""
+    import gen
+    t_setup = time.perf_counter()
+    ntests = args.tests
+    specs = gen.batch_dfas(args.seed, 64)
+    dfas = [dm.Dfa.from_spec(s) for s in specs]
+    lens = gen.batch_lengths(args.seed, ntests, 256, args.max_len)
+    picks = gen.batch_picks(args.seed, ntests, len(specs))
+    datas = [gen.batch_text(args.seed * 1000003 + i, specs[picks[i]], int(lens[i]))
+             for i in range(ntests)]
+    if not args.no_tune:
+        for k, (s, d) in enumerate(zip(specs, dfas)):
+            sample = torch.from_numpy(gen.batch_text(7 + k, s, 16 << 20)).cuda()
+            d.autotune(sample)
+            del sample
+    bl, res = batched_leg(dm, [dfas[p] for p in picks], datas, reps=args.steps)
+    ok = True
+    if not args.no_cpu:  # spot-check against the oracle (bounded)
+        import oracle
+        for i in range(0, ntests, max(1, ntests // 64)):
+            if lens[i] <= (8 << 20):
+                st, fs, acc = oracle.Dfa.from_spec(specs[picks[i]]).run(datas[i])
+                ok &= (res[i][2], res[i][0], res[i][1]) == (st, fs, acc)
+    total = int(sum(lens))
+    line = {"metric": METRIC, "value": bl["gbs"], "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 2, "ms_per_step": bl["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": "batched_64dfa_%dtests" % ntests, "tests": ntests,
+                       "input_bytes": total, "max_len": args.max_len, "autotuned": not args.no_tune},
+            "batched": bl, "oracle_spot_check": ok,
+            "setup_s": round(time.perf_counter() - t_setup, 1)}
+    print(json.dumps(line), flush=True)
+    return specs, dfas, picks, datas, bl, res
+
+
+def run_serve_config(args, dm, torch):
+    """Serving config: Poisson arrivals drawn from the batched mix (a pool of
+    args.tests strings), tables resident, 40 GB admission budget, continuous
+    batching; 20k req/s plus a sweep at fractions of measured capacity."""
+    specs, dfas, picks, datas, bl, bl_res = run_batch_config(args, dm, torch)
+    cap = bl["gbs"]
+    dd = [dfas[p] for p in picks]
+    out = {}
+    mean = sum(len(x) for x in datas) / len(datas)
+    rates = [("20k_req_s", 20000 * mean / 1e9)] + [("%.2fx" % f, f * cap) for f in (0.25, 0.5, 0.75, 1.0)]
+    for name, gbs in rates:
+        sv, done, sub = serving_leg(dm, dd, datas, gbs, seconds=args.serve_seconds,
+                                    budget=args.budget, inflight=4, seed=len(out) + 1)
+        res_b = bl_res
+        for c in done:   # every served result equals the same test in the batched launch
+            assert (c[1], c[2], c[3]) == res_b[sub[c[0]]], "served result differs"
+        out[name] = sv
+        print(json.dumps({"serving_point": name, **sv}), flush=True)
+    line = {"metric": METRIC, "value": out["20k_req_s"]["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic",
+            "config": {"workload": "serving_batched_mix", "pool_tests": len(datas),
+                       "budget_bytes": args.budget, "mean_request_bytes": int(mean)},
+            "serving": out, "batched_capacity_gbs": cap}
+    print(json.dumps(line), flush=True)
+
+
 def _dtype(spec) -> str:
     return "u8" if spec.num_states + 1 <= 256 else "u16"
 
@@ -287,7 +364,12 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="regex", choices=["regex", "plain", "protein"])
+    ap.add_argument("--workload", default="regex",
+                    choices=["regex", "plain", "protein", "batch", "serve"])
+    ap.add_argument("--tests", type=int, default=4096, help="batch/serve: number of tests")
+    ap.add_argument("--max-len", type=int, default=64 << 20, help="batch/serve: longest test")
+    ap.add_argument("--budget", type=int, default=40 << 30, help="serve: admission budget (bytes)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--bytes", type=int, default=0, help="input size override (small profiling cases)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -318,7 +400,15 @@ def main():
         dist.barrier()
     import paper_1210_5093_gb300 as dm
 
-    w = _workload(args.workload, args.seed + rank, args.bytes)
+    if args.workload in ("batch", "serve"):
+        if rank == 0:
+            (run_batch_config if args.workload == "batch" else run_serve_config)(args, dm, torch)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    w = _workload(args.workload, rank_seed(args.seed, rank), args.bytes)
     d = dm.Dfa.from_spec(w.spec)
     n = len(w.data)
     dev = torch.from_numpy(w.data).cuda()
@@ -364,10 +454,7 @@ def main():
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
     k_ms = [a.elapsed_time(b) for a, b in zip(kb, ke)]
-    elapsed = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(elapsed, op=dist.ReduceOp.MAX)
-    ms_max = float(elapsed.item())
+    gbs, ms_max = reduce_job(dist, "cuda", len(w.data), args.steps, ms, world)
 
     # end to end through the public API with a pinned host buffer: H2D copy,
     # every kernel and the 12-byte result read back, per step
@@ -388,12 +475,11 @@ def main():
         hbm_peak, sm_max_mhz, peak_src = _peaks()
         props = torch.cuda.get_device_properties(local)
         nsm = props.multi_processor_count
-        W, mean_I = lookups_per_launch(dm, d, w.data, P)
+        W, mean_I = lookups_per_launch(dm, d, dev, n, w.num_chunks)
         k_avg_s = statistics.mean(k_ms) / 1e3
         lookup_peak = nsm * 32 * sm_max_mhz * 1e6           # 32 shared-memory lanes per clock per SM
         achieved = W / k_avg_s
         info = d.info()
-        gbs = n * world * args.steps / (ms_max / 1e3) / 1e9
         traffic = _traffic_record(w.name)
         line = {
             "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world,
@@ -427,6 +513,28 @@ def main():
                        "reasons": clk["reasons"], "samples": clk["samples"]},
             "result": {"final_state": fs, "accept": acc, "status": st},
         }
+        if not args.no_mix and args.workload in ("regex", "protein"):
+            # r-symbol reverse lookahead (Eq. 13): same input, smaller initial-state sets
+            la = {}
+            for r in (2, 4):
+                kb2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                ke2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                for e in kb2 + ke2:
+                    e.record(stream)
+                with torch.cuda.stream(stream):
+                    d.match_async(dev, out, ws2 := torch.empty(d.workspace_size(n, lookahead=r),
+                                  dtype=torch.uint8, device="cuda"), stream=stream, lookahead=r)
+                    for i in range(3):
+                        d.match_async(dev, out, ws2, stream=stream, lookahead=r, events=(kb2[i], ke2[i]))
+                torch.cuda.synchronize()
+                assert dm.results_from(out)[0] == (fs, acc, st), "lookahead changed the answer"
+                kms = statistics.median(a.elapsed_time(b) for a, b in zip(kb2, ke2))
+                Wr, _ = lookups_per_launch(dm, d, dev, n, 0, r)
+                la["r%d" % r] = {"gbs": round(n / kms / 1e6, 3), "kernel_ms": round(kms, 3),
+                                 "lookups_per_byte": round(Wr / n, 3),
+                                 "lookup_roof_frac": round(Wr / (kms / 1e3) / lookup_peak, 4)}
+                del ws2
+            line["lookahead"] = la
         if not args.no_mix and args.workload == "regex":
             mix = _mixed_strings(w.spec, 11, 384, 256, 8 << 20)
             bl, res_b = batched_leg(dm, [d] * len(mix), mix)

@@ -601,8 +601,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
     int cur_test = -1;
     uint32_t seg_first = 0, seg_n = 0, seg_cls = 0, nD = 0;
 
+    // Finishes the running segment of cur_test.  It runs when the next chunk
+    // belongs to another test, which may already be in a tile of another DFA,
+    // so it reads the test's own DFA descriptor, never the shared-memory copy.
     auto end_segment = [&]() {
         const DevTest tt = test_at(lp, (uint32_t)cur_test);
+        const DevDfa& td = lp.dfas[tt.dfa];
         const bool covered = tt.chunk_base >= c_lo && tt.chunk_base + tt.P <= c_hi;
         if (covered) {
             // the segment is the whole test, started at chunk 0 from {q0}: V[0] is the answer
@@ -611,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
                 const uint32_t err = atomicOr(lp.test_err + cur_test, 0u);
                 dfa_result_t r;
                 r.final_state = err ? 0u : s;
-                r.accept = err ? 0 : d.accept[s];
+                r.accept = err ? 0 : td.accept[s];
                 r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
                 r.status = err ? DFA_ESYMBOL : DFA_OK;
                 lp.results[tt.out] = r;
@@ -622,7 +626,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
         // outside the segment's domain (those states are excluded, hence fixed)
         const size_t slot = (size_t)b + (size_t)cur_test;
         uint16_t* dense = lp.seg_vals + slot * lp.seg_stride;
-        for (uint32_t s = tid; s < d.qe; s += kThreads) dense[s] = (uint16_t)s;
+        const uint32_t tqe = td.qe;
+        for (uint32_t s = tid; s < tqe; s += kThreads) dense[s] = (uint16_t)s;
         __syncthreads();
         for (uint32_t x = tid; x < nD; x += kThreads) dense[vdom[x]] = vmap[x];
         if (tid == 0) {

@@ -309,3 +309,42 @@ def test_lookahead_sets_with_bad_byte(dm):
         for r in (2, 4):
             st, _, _ = d.match(bad, num_chunks=256, lookahead=r)
             assert st == dm.ESYMBOL
+
+
+def test_many_dfas_on_one_input(dm):
+    """Several DFAs matched against the same input in one launch (the paper's
+    representation allows one input to be run by several DFAs, Sec. 5): each
+    result equals that DFA run alone and the oracle."""
+    import torch
+    specs = [s for s in gen.batch_dfas(21, 12) if s.byte_to_symbol is None]
+    specs.append(gen.regex_dfa(2))
+    dfas = [dm.Dfa.from_spec(s) for s in specs]
+    x = gen.zipf_text(22, 3 << 20)
+    dev = torch.from_numpy(x).cuda()
+    res = dm.match_batch(dfas, [dev] * len(dfas))
+    for (fs, acc, st), s, d in zip(res, specs, dfas):
+        est, efs, eacc = _expect(s, x)
+        assert (st, fs, acc) == (est, efs, eacc)
+        assert d.match(dev) == (st, fs, acc)
+
+
+def test_batch_dfa_switch_keeps_each_tests_own_dfa(dm):
+    """Regression: a test finished at the start of a tile of another DFA must
+    take its accept flags and state count from its own DFA.  Here DFA A
+    accepts in every state and DFA B in none, so every accept bit is
+    determined by the test's DFA; B also has more states than A."""
+    import torch
+    a = gen.random_dfa(71, 20, 256)
+    a.finals = np.arange(20, dtype=np.uint32)
+    b = gen.random_dfa(72, 300, 256, num_finals=0)
+    b.finals = np.zeros(0, dtype=np.uint32)
+    da, db = dm.Dfa.from_spec(a), dm.Dfa.from_spec(b)
+    lens = gen.batch_lengths(73, 400, 1, 200_000)
+    datas = [gen.uniform_bytes(74 + i, int(n)) for i, n in enumerate(lens)]
+    dfas = [da if i % 2 == 0 else db for i in range(len(datas))]
+    tens = [torch.from_numpy(x).cuda() for x in datas]
+    res = dm.match_batch(dfas, tens)
+    for i, (fs, acc, st) in enumerate(res):
+        spec = a if i % 2 == 0 else b
+        assert (st, fs, acc) == _expect(spec, datas[i])
+        assert acc == (i % 2 == 0)
