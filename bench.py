@@ -415,7 +415,8 @@ def main():
     tuning = None
     if not w.num_chunks and not args.no_tune:
         t, _ = d.autotune(dev)          # the library's per-DFA tuner, before any timing
-        tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta}
+        tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
+                  "ctas_per_sm": t.ctas_per_sm}
     P = d.plan_chunks(n, num_chunks=w.num_chunks)
     ws = torch.empty(d.workspace_size(n, num_chunks=w.num_chunks), dtype=torch.uint8, device="cuda")
     out = torch.zeros(12, dtype=torch.uint8, device="cuda")

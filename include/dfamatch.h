@@ -82,6 +82,8 @@ typedef struct {
     uint32_t tiles_per_cta;     /* single tests: aim for this many tiles per CTA (default 8) */
     uint32_t min_chunk_bytes;   /* single tests: shortest chunk (default 512)          */
     uint32_t batch_chunk_bytes; /* batched and served tests: chunk length (default 8192) */
+    uint32_t ctas_per_sm;       /* single tests: match-kernel CTAs per SM to aim for
+                                   (0 = 3 when K <= 4, else 2)                          */
 } dfa_tuning_t;
 
 /* Optional per-call planning overrides; pass NULL for the defaults. */
@@ -141,8 +143,9 @@ int dfa_set_tuning(dfa_t *dfa, const dfa_tuning_t *tuning);
 
 /*
  * Autotuner: times single-test launches of the device string dev_sample
- * (len bytes) for every allowed K in {2, 4, 8, 16} and tiles-per-CTA in
- * {4, 8, 16} (median of 3 timed launches each, CUDA events on `stream`),
+ * (len bytes) for every allowed K in {2, 4, 8, 16}, tiles-per-CTA in
+ * {4, 8, 16} and, for K <= 4, 2 or 3 CTAs per SM (median of 3 timed
+ * launches each, CUDA events on `stream`),
  * keeps the fastest as the DFA's tuning record and returns it in *chosen and
  * its time in *best_ms (either may be NULL).  The batched chunk length is set
  * to the chosen single-test chunk length, clamped to [2 KiB, 64 KiB].

@@ -14,7 +14,9 @@
 #include "dfa_internal.h"
 
 namespace dfam {
-uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes);
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes,
+                          uint32_t target);
+uint32_t match_target_ctas(uint32_t kmax, uint32_t want);
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
                 uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr,
@@ -149,7 +151,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         p.qe_max = std::max(p.qe_max, x.qe);
         if (x.placement == kSmem) p.table_cap = std::max(p.table_cap, (uint32_t)up(x.table_bytes, 16));
     }
-    p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap, &p.stage);
+    p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap, &p.stage, match_target_ctas(p.kmax, 0));
     int rc = match_grid(p.smem, p.kmax, &p.grid);
     if (rc != DFA_OK) return rc;
     std::vector<uint32_t> order(count);
@@ -269,7 +271,8 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     const uint32_t tcap = x.placement == kSmem ? (uint32_t)up(x.table_bytes, 16) : 0u;
     s->kmax = x.K;
     uint32_t stage = 0;
-    s->smem = match_smem_bytes(tcap, x.K, x.vcap, &stage);
+    s->smem = match_smem_bytes(tcap, x.K, x.vcap, &stage,
+                               match_target_ctas(x.K, d->tuning.ctas_per_sm));
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
@@ -472,10 +475,14 @@ int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream
     for (uint32_t K : {2u, 4u, 8u, 16u}) {
         if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) continue;
         for (uint32_t tpc : {4u, 8u, 16u}) {
-            dfa_tuning_t t = saved;
-            t.states_per_thread = K;
-            t.tiles_per_cta = tpc;
-            cands.push_back(t);
+            for (uint32_t ctas : {2u, 3u}) {
+                if (ctas == 3 && K > 4) continue;
+                dfa_tuning_t t = saved;
+                t.states_per_thread = K;
+                t.tiles_per_cta = tpc;
+                t.ctas_per_sm = ctas;
+                cands.push_back(t);
+            }
         }
     }
     // workspace for the largest plan

@@ -569,8 +569,11 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
     __syncthreads();
 }
 
-template <int KMAX>
-__global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t kmax) {
+// KMAX: largest chains-per-thread of the launch; MINB: CTAs per SM the
+// register budget is sized for (3 for K <= 4: more warps hide the shared-
+// memory load latency when each thread carries few chains).
+template <int KMAX, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_t kmax) {
     extern __shared__ __align__(16) uint8_t sm[];
     const SmemLayout L = smem_layout(lp.smem_table_cap, kmax, lp.vcap, lp.stage_bytes);
     ChunkMeta* meta = reinterpret_cast<ChunkMeta*>(sm + L.meta);
@@ -737,12 +740,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
         c.sb = (int)d.sb;
         c.placement = (int)d.placement;
         const uint32_t boff = sa(sm + L.boff);
-        switch (d.K) {
-            case 2: tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
-            case 4: tile_chains<4>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
-            case 8: tile_chains<8>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
-            default: tile_chains<KMAX>(d, meta, nch, maxlen, c, boff, lp.test_err); break;
-        }
+        if (d.K == 2) tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err);
+        else if (KMAX >= 8 && d.K == 4) tile_chains<(KMAX >= 8 ? 4 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err);
+        else if (KMAX >= 16 && d.K == 8) tile_chains<(KMAX >= 16 ? 8 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err);
+        else tile_chains<KMAX>(d, meta, nch, maxlen, c, boff, lp.test_err);
         __syncthreads();
 
         // Compose the tile's chunk maps, in order, into the running map of each
@@ -791,31 +792,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_match(LaunchPlan lp, uint32_t k
 
 // ------------------------------------------------------------ host side
 
-// Shared memory of k_match and the stage-buffer size: the largest stage (up to
-// 64 KB per buffer) that still lets two CTAs share an SM.
-uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes) {
-    const uint32_t per_sm = 228u * 1024u, reserved = 1024u;
-    uint32_t best = kStageBytes;
-    for (uint32_t sb = 64u * 1024u; sb > kStageBytes; sb -= 2048u) {
-        if (2u * (smem_layout(table_cap, kmax, vcap, sb).total + reserved) <= per_sm) {
-            best = sb;
-            break;
+// CTAs per SM the match kernel aims for: 3 when every DFA of the launch
+// uses K <= 4 (the kernel variant then fits 3 x 512 threads in registers),
+// else 2; `want` overrides it (1-3).
+uint32_t match_target_ctas(uint32_t kmax, uint32_t want) {
+    uint32_t t = kmax <= 4 ? 3u : 2u;
+    if (want >= 1 && want <= t) t = want;
+    return t;
+}
+
+// Shared memory of k_match and the stage-buffer size: the largest stage (8 to
+// 64 KB per buffer) that lets `target` CTAs share an SM, else fewer CTAs.
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes,
+                          uint32_t target) {
+    const uint32_t per_sm = 228u * 1024u, reserved = 1024u, min_stage = 8u * 1024u;
+    for (uint32_t ctas = target; ctas >= 1; --ctas) {
+        for (uint32_t sb = 64u * 1024u; sb >= min_stage; sb -= 2048u) {
+            if (ctas * (smem_layout(table_cap, kmax, vcap, sb).total + reserved) <= per_sm) {
+                *stage_bytes = sb;
+                return smem_layout(table_cap, kmax, vcap, sb).total;
+            }
         }
     }
-    *stage_bytes = best;
-    return smem_layout(table_cap, kmax, vcap, best).total;
+    *stage_bytes = min_stage;
+    return smem_layout(table_cap, kmax, vcap, min_stage).total;
 }
 
 static int g_sm_count = -1, g_dev = -1;
 
-template <int KMAX>
+template <int KMAX, int MINB>
 static int grid_for(uint32_t smem, uint32_t* grid) {
-    if (cudaFuncSetAttribute(k_match<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_match<KMAX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return DFA_ECUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<KMAX>, kThreads, smem) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<KMAX, MINB>, kThreads,
+                                                      smem) != cudaSuccess ||
         per_sm < 1)
         return DFA_ECUDA;
     *grid = (uint32_t)(g_sm_count * per_sm);
@@ -828,9 +840,16 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
     if (g_dev != dev) {
         if (cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return DFA_ECUDA;
+        // k_lookahead's per-warp bitmap and set buffer for the largest DFA (4096 states)
+        const int la_max = kLaWarps * (4096 / 32 + 4096 / 2) * 4;
+        if (cudaFuncSetAttribute(k_lookahead, cudaFuncAttributeMaxDynamicSharedMemorySize, la_max) !=
+            cudaSuccess)
+            return DFA_ECUDA;
         g_dev = dev;
     }
-    return kmax > 8 ? grid_for<16>(smem, grid) : grid_for<8>(smem, grid);
+    if (kmax > 8) return grid_for<16, 2>(smem, grid);
+    if (kmax > 4) return grid_for<8, 2>(smem, grid);
+    return grid_for<4, 3>(smem, grid);
 }
 
 // Issue the whole launch on `st`: memsets of the per-test counters, the
@@ -859,8 +878,9 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
         return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
     }
     if (ev_begin) cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), st);
-    if (kmax > 8) k_match<16><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
-    else k_match<8><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
+    if (kmax > 8) k_match<16, 2><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
+    else if (kmax > 4) k_match<8, 2><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
+    else k_match<4, 3><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
     if (ev_end) cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st);
     if (kernels) *kernels = nk;
     return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;

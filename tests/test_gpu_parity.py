@@ -348,3 +348,45 @@ def test_batch_dfa_switch_keeps_each_tests_own_dfa(dm):
         spec = a if i % 2 == 0 else b
         assert (st, fs, acc) == _expect(spec, datas[i])
         assert acc == (i % 2 == 0)
+
+
+@pytest.mark.parametrize("kind", ["u16_large", "u8_256classes"])
+def test_l2_placed_tables(dm, kind):
+    """Tables that do not fit shared memory (or whose row offsets need more
+    than 16 bits) are read through L2: 256 byte classes x 1288 states (uint16,
+    659 KB) and 256 classes x 255 states (uint8, 66 KB)."""
+    import torch
+    if kind == "u16_large":
+        spec = gen.class_dfa(81, 1288, 256, 0.02, 0.3, 12, "byte")
+    else:
+        spec = gen.random_dfa(82, 255, 256, num_finals=20, missing=0.01)
+    d = dm.Dfa.from_spec(spec)
+    info = d.info()
+    assert info.placement == 1 and info.num_classes == 256
+    data = gen.zipf_text(83, 6 << 20) if kind == "u16_large" else gen.uniform_bytes(83, 6 << 20)
+    for P in (0, 1, 5, 3000):
+        for r in (1, 2):
+            _check(dm, d, spec, data, num_chunks=P, lookahead=r)
+    _check(dm, d, spec, data[: 12345], num_chunks=50)
+    # batched together with a shared-memory DFA
+    small = gen.regex_dfa(2)
+    ds = dm.Dfa.from_spec(small)
+    xs = [data[: 100_000 * (i + 1)] for i in range(6)]
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    res = dm.match_batch([d, ds, d, ds, d, ds], dev)
+    for i, (fs, acc, st) in enumerate(res):
+        spec_i = spec if i % 2 == 0 else small
+        assert (st, fs, acc) == _expect(spec_i, xs[i])
+
+
+def test_largest_dfa_and_k16(dm):
+    """|Q| = 4095 (the limit), a dense 20-letter alphabet so I_max is large
+    and the planner needs K = 16 to fit a chunk into one tile."""
+    spec = gen.class_dfa(91, 4095, 20, 0.3, 0.9, 40, "protein")
+    d = dm.Dfa.from_spec(spec)
+    info = d.info()
+    assert info.i_max > 2048 and info.states_per_thread == 16
+    data = gen.protein_text(92, 2 << 20)
+    for P in (0, 1, 777):
+        _check(dm, d, spec, data, num_chunks=P)
+    _check(dm, d, spec, data, num_chunks=500, lookahead=0)   # Algorithm 2: all 4096 states
