@@ -45,6 +45,7 @@ WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t pt
     w.bsum = take(4ull * (nblk + 1));
     w.tile_first = take(4ull * (ptot + 1));
     w.tile_base = take(4ull * (ngroups + 1));
+    w.tile_eff = take(4ull * ngroups);
     w.num_tiles = take(4);
     w.test_err = take(8ull * ntests);  // test_err[ntests] then arrived[ntests]
     w.first_cta = take(4ull * ntests);
@@ -65,6 +66,7 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
     lp.bsum = reinterpret_cast<uint32_t*>(base + w.bsum);
     lp.tile_first = reinterpret_cast<uint32_t*>(base + w.tile_first);
     lp.tile_base = reinterpret_cast<uint32_t*>(base + w.tile_base);
+    lp.tile_eff = reinterpret_cast<uint32_t*>(base + w.tile_eff);
     lp.num_tiles = reinterpret_cast<uint32_t*>(base + w.num_tiles);
     lp.test_err = reinterpret_cast<uint32_t*>(base + w.test_err);
     lp.arrived = lp.test_err + lp.ntests;

@@ -101,6 +101,7 @@ struct LaunchPlan {
     uint32_t* bsum;             // [nblk+1]
     uint32_t* tile_first;       // [ptot+1]
     uint32_t* tile_base;        // [ngroups+1]
+    uint32_t* tile_eff;         // [ngroups] slot window of one tile
     uint32_t* num_tiles;        // [1]
     uint32_t* test_err;         // [ntests]
     uint32_t* arrived;          // [ntests]
@@ -121,7 +122,7 @@ struct LaunchPlan {
 // Workspace carve-up of one launch (byte offsets into the device workspace).
 struct WsLayout {
     uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, bsum, tile_first, tile_base,
-        num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
+        tile_eff, num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
 };
 
 // A batch planned on the host: descriptors, sizes and the workspace layout.

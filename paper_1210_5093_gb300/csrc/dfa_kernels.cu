@@ -271,17 +271,26 @@ __device__ __forceinline__ uint32_t group_nt_eff(const DevDfa& d) {
 }
 
 // Tiles per group: a tile holds the chunks whose slot offset (relative to the
-// group's first chunk) falls in one window of nt_eff slots, so a tile never
-// needs more than kThreads threads.
+// group's first chunk) falls in one window of `eff` slots, so a tile never
+// needs more than kThreads threads.  eff is the full window (kThreads minus
+// the largest chunk's slots, less one) unless the whole launch needs fewer
+// thread slots than the grid holds: then the windows shrink so the tiles
+// spread over all CTAs (fewer chunks per tile, longer staged segments, more
+// SMs on a latency-bound launch).  eff never drops below one chunk's slots.
 __global__ void __launch_bounds__(kPlanThreads) k_group_tiles(LaunchPlan lp) {
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
     uint32_t carry = 0;
+    const uint32_t total = lp.bsum[lp.nblk];
+    const uint32_t spread = (total + lp.grid - 1) / lp.grid;
     for (uint32_t base = 0; base < lp.ngroups; base += kPlanThreads) {
         uint32_t i = base + threadIdx.x;
         uint32_t nt = 0;
         if (i < lp.ngroups) {
             const DevGroup gr = group_at(lp, i);
-            const uint32_t eff = group_nt_eff(lp.dfas[gr.dfa]);
+            const DevDfa& dd = lp.dfas[gr.dfa];
+            uint32_t eff = group_nt_eff(dd);
+            eff = max(dd.cost_max, min(eff, spread));
+            lp.tile_eff[i] = eff;
             nt = (lp.off[gr.end_chunk - 1] - lp.off[gr.first_chunk]) / eff + 1;
         }
         uint32_t total;
@@ -301,7 +310,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_tiles(LaunchPlan lp) {
     if (g >= lp.ptot) return;
     const uint32_t grp = test_at(lp, lp.chunk_test[g]).group;
     const DevGroup gr = group_at(lp, grp);
-    const uint32_t eff = group_nt_eff(lp.dfas[gr.dfa]);
+    const uint32_t eff = lp.tile_eff[grp];
     const uint32_t base = lp.off[gr.first_chunk];
     const uint32_t lt = (lp.off[g] - base) / eff;
     const bool first = g == gr.first_chunk || (lp.off[g - 1] - base) / eff != lt;
