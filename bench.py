@@ -509,7 +509,7 @@ def main():
             "e2e": {"value": round(n * world / e2e_s / 1e9, 3), "unit": "GB/s",
                     "h2d_bytes_per_step": n, "d2h_bytes_per_step": 12,
                     "api": "dfa_match (pinned host buffer)"},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": d.num_kernels(n, num_chunks=w.num_chunks) * args.steps,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"]},
             "result": {"final_state": fs, "accept": acc, "status": st},

@@ -84,6 +84,7 @@ SIGNATURES = {
     "dfa_partition": (_I, [_U64, _U32, _U32, _P]),
     "dfa_match": (_I, [_P, _P, _U64, _P, _P]),
     "dfa_plan_chunks": (_I, [_P, _U64, _P, _P]),
+    "dfa_match_num_kernels": (_I, [_P, _U64, _P, _P]),
     "dfa_plan_sets": (_I, [_P, _P, _U64, _P, _P, _U32, _P]),
     "dfa_match_workspace_size": (_I, [_P, _U64, _P, _P]),
     "dfa_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
@@ -272,6 +273,13 @@ class Dfa:
         o = _opts(num_chunks, multiplicity, lookahead)
         _check(lib().dfa_plan_chunks(self._h, n, ctypes.byref(o), ctypes.byref(out)),
                "dfa_plan_chunks")
+        return int(out.value)
+
+    def num_kernels(self, n: int, num_chunks: int = 0, lookahead: int = 1) -> int:
+        out = ctypes.c_uint32()
+        o = _opts(num_chunks, 0, lookahead)
+        _check(lib().dfa_match_num_kernels(self._h, n, ctypes.byref(o), ctypes.byref(out)),
+               "dfa_match_num_kernels")
         return int(out.value)
 
     def plan_sets(self, dev_data, num_chunks: int = 0, multiplicity: int = 0,

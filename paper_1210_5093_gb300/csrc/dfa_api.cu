@@ -570,6 +570,15 @@ int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t* starts) {
     return DFA_OK;
 }
 
+int dfa_match_num_kernels(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, uint32_t* n) {
+    if (!n) return DFA_EINVAL;
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    *n = (s.lp.ptot <= 16384 ? 2u : 6u) + (s.lp.dyn ? 1u : 0u);
+    return DFA_OK;
+}
+
 int dfa_plan_sets(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
                   const dfa_match_opts_t* opts, uint32_t* sizes, uint32_t cap, uint32_t* P) {
     if (!P || (len && !dev_str)) return DFA_EINVAL;
@@ -795,7 +804,7 @@ int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) 
 
 int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
     if (!b || !n) return DFA_EINVAL;
-    *n = b->p.dyn ? 7 : 6;
+    *n = (b->p.dyn ? 7 : 6) - (b->p.ptot <= 16384 ? 4 : 0);
     return DFA_OK;
 }
 

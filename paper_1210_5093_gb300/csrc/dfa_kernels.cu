@@ -204,39 +204,42 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
     if (lane == 0) lp.set_size[g] = n;
 }
 
-// Per chunk: owning test, reverse-lookahead class (Algorithm 3 line 16) and
-// the thread slots it is charged: ceil(|I_k| / K), at least 2.
+// Per chunk g: owning test, reverse-lookahead class (Algorithm 3 line 16)
+// and the thread slots it is charged: ceil(|I_k| / K), at least 2.  Writes
+// chunk_test, chunk_cls and cost; returns the cost.
+__device__ uint32_t chunk_count(const LaunchPlan& lp, uint32_t g) {
+    const uint32_t lo = find_test(lp, g);
+    const DevTest t = test_at(lp, lo);
+    const DevDfa& d = lp.dfas[t.dfa];
+    const uint32_t k = g - t.chunk_base;
+    const uint64_t st = dstart(t.n, t.P, t.m, k);
+    uint32_t cls;
+    if (st == 0) {
+        cls = d.C;  // chunk 0, or a chunk preceded only by empty chunks: start set {q0}
+    } else if (!t.lookahead) {
+        cls = d.C + 1;  // Algorithm 2: all of Q
+    } else {
+        uint32_t c = d.byte_class[t.str[st - 1]];
+        if (c == kNone16) {
+            atomicOr(&lp.test_err[lo], 1u);
+            c = d.C;
+        }
+        cls = c;
+        if (t.lookahead >= 2 && st >= 2 && c != d.C) cls = dyn_set(d.C);  // Eq. 13 set from k_lookahead
+    }
+    const uint32_t size = cls == dyn_set(d.C) ? lp.set_size[g] : d.iset_off[cls + 1] - d.iset_off[cls];
+    const uint32_t cnt = (size + d.K - 1) / d.K;
+    const uint32_t cost = cnt < 2 ? 2 : cnt;
+    lp.chunk_test[g] = lo;
+    lp.chunk_cls[g] = (uint16_t)cls;
+    lp.cost[g] = cost;
+    return cost;
+}
+
 __global__ void __launch_bounds__(kPlanThreads) k_count(LaunchPlan lp) {
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
     const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
-    uint32_t cost = 0;
-    if (g < lp.ptot) {
-        const uint32_t lo = find_test(lp, g);
-        const DevTest t = test_at(lp, lo);
-        const DevDfa& d = lp.dfas[t.dfa];
-        const uint32_t k = g - t.chunk_base;
-        const uint64_t st = dstart(t.n, t.P, t.m, k);
-        uint32_t cls;
-        if (st == 0) {
-            cls = d.C;  // chunk 0, or a chunk preceded only by empty chunks: start set {q0}
-        } else if (!t.lookahead) {
-            cls = d.C + 1;  // Algorithm 2: all of Q
-        } else {
-            uint32_t c = d.byte_class[t.str[st - 1]];
-            if (c == kNone16) {
-                atomicOr(&lp.test_err[lo], 1u);
-                c = d.C;
-            }
-            cls = c;
-            if (t.lookahead >= 2 && st >= 2 && c != d.C) cls = dyn_set(d.C);  // Eq. 13 set from k_lookahead
-        }
-        const uint32_t size = cls == dyn_set(d.C) ? lp.set_size[g] : d.iset_off[cls + 1] - d.iset_off[cls];
-        const uint32_t cnt = (size + d.K - 1) / d.K;
-        cost = cnt < 2 ? 2 : cnt;
-        lp.chunk_test[g] = lo;
-        lp.chunk_cls[g] = (uint16_t)cls;
-        lp.cost[g] = cost;
-    }
+    const uint32_t cost = g < lp.ptot ? chunk_count(lp, g) : 0;
     uint32_t total;
     block_excl_scan<kPlanThreads>(cost, tmp, &total);
     if (threadIdx.x == 0) lp.bsum[blockIdx.x] = total;
@@ -315,6 +318,64 @@ __global__ void __launch_bounds__(kPlanThreads) k_tiles(LaunchPlan lp) {
     const uint32_t lt = (lp.off[g] - base) / eff;
     const bool first = g == gr.first_chunk || (lp.off[g - 1] - base) / eff != lt;
     if (first) lp.tile_first[lp.tile_base[grp] + lt] = g;
+}
+
+// All of k_count .. k_tiles in one CTA, for launches with at most
+// kSmallPlan chunks (saves four launches on latency-bound calls).  Same
+// results as the five kernels.
+constexpr uint32_t kSmallPlan = 16384;
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp) {
+    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    // per-chunk counts and the exclusive scan, 1024 chunks per round
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < lp.ptot; base += kPlanThreads) {
+        const uint32_t g = base + threadIdx.x;
+        const uint32_t cost = g < lp.ptot ? chunk_count(lp, g) : 0;
+        uint32_t total;
+        const uint32_t ex = block_excl_scan<kPlanThreads>(cost, tmp, &total);
+        if (g < lp.ptot) lp.off[g] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        lp.off[lp.ptot] = carry;
+        lp.bsum[lp.nblk] = carry;  // the total, read by the tile windows below
+    }
+    __syncthreads();
+    // tile windows and bases per group (as k_group_tiles)
+    const uint32_t spread = (carry + lp.grid - 1) / lp.grid;
+    uint32_t tcarry = 0;
+    for (uint32_t base = 0; base < lp.ngroups; base += kPlanThreads) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t nt = 0;
+        if (i < lp.ngroups) {
+            const DevGroup gr = group_at(lp, i);
+            const DevDfa& dd = lp.dfas[gr.dfa];
+            const uint32_t eff = max(dd.cost_max, min(group_nt_eff(dd), spread));
+            lp.tile_eff[i] = eff;
+            nt = (lp.off[gr.end_chunk - 1] - lp.off[gr.first_chunk]) / eff + 1;
+        }
+        uint32_t total;
+        const uint32_t ex = block_excl_scan<kPlanThreads>(nt, tmp, &total);
+        if (i < lp.ngroups) lp.tile_base[i] = tcarry + ex;
+        tcarry += total;
+    }
+    if (threadIdx.x == 0) {
+        lp.tile_base[lp.ngroups] = tcarry;
+        *lp.num_tiles = tcarry;
+        lp.tile_first[tcarry] = lp.ptot;
+    }
+    __syncthreads();
+    // first chunk of every tile (as k_tiles)
+    for (uint32_t g = threadIdx.x; g < lp.ptot; g += kPlanThreads) {
+        const uint32_t grp = test_at(lp, lp.chunk_test[g]).group;
+        const DevGroup gr = group_at(lp, grp);
+        const uint32_t eff = lp.tile_eff[grp];
+        const uint32_t b0 = lp.off[gr.first_chunk];
+        const uint32_t lt = (lp.off[g] - b0) / eff;
+        if (g == gr.first_chunk || (lp.off[g - 1] - b0) / eff != lt)
+            lp.tile_first[lp.tile_base[grp] + lt] = g;
+    }
 }
 
 // ------------------------------------------------------------ matching
@@ -877,11 +938,16 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
                                                                                    set_words);
         ++nk;
     }
-    k_count<<<nb, kPlanThreads, 0, st>>>(lp);
-    k_scan_blocks<<<1, kPlanThreads, 0, st>>>(lp);
-    k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
-    k_group_tiles<<<1, kPlanThreads, 0, st>>>(lp);
-    k_tiles<<<nb, kPlanThreads, 0, st>>>(lp);
+    if (lp.ptot <= kSmallPlan) {
+        k_plan_small<<<1, kPlanThreads, 0, st>>>(lp);
+        nk -= 4;
+    } else {
+        k_count<<<nb, kPlanThreads, 0, st>>>(lp);
+        k_scan_blocks<<<1, kPlanThreads, 0, st>>>(lp);
+        k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
+        k_group_tiles<<<1, kPlanThreads, 0, st>>>(lp);
+        k_tiles<<<nb, kPlanThreads, 0, st>>>(lp);
+    }
     if (plan_only) {
         if (kernels) *kernels = nk - 1;
         return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
