@@ -350,6 +350,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
     x.q0 = h.q0;
     x.imax = h.imax;
     x.K = h.K;
+    x.stage_fmt = h.placement == kGlobal ? kOff32 : (h.C + 1 <= 255 ? kCls8 : kOff16);
     if (device) {
         if (cudaGetDevice(&d->device) != cudaSuccess) {
             delete d;

@@ -15,7 +15,7 @@ namespace dfam {
 constexpr int kThreads = 512;            // threads per CTA of the match kernel
 constexpr int kMaxChunksPerTile = kThreads / 2;  // every chunk is charged >= 2 thread slots
 constexpr int kStageBytes = 16384;       // one staging buffer of class-row offsets
-constexpr int kMaxSegLen = 1024;         // longest staged segment per chunk (positions)
+constexpr int kMaxSegLen = 2048;         // longest staged segment per chunk (positions)
 constexpr uint16_t kNone16 = 0xFFFF;     // "not a member" in pos tables / invalid byte
 constexpr uint32_t kNone32 = 0xFFFFFFFFu;
 constexpr uint32_t kSmemTableMax = 112 * 1024;  // tables larger than this are read through L2
@@ -47,8 +47,14 @@ struct DevDfa {
     uint32_t K;                  // states per thread
     uint32_t cost_max;           // max thread slots one chunk can need: max(ceil(|I|/K), 2)
     uint32_t vcap;               // largest set size (incl. start set) = capacity of a state map
-    uint32_t pad_;
+    uint32_t stage_fmt;          // StageFmt of the staged input stream
 };
+
+// How a chunk's input is staged in shared memory: 8-bit class indices
+// (16 positions per 16-byte read; shared-memory tables with at most 254
+// classes), 16-bit row byte offsets (other shared-memory tables) or 32-bit
+// row byte offsets (tables read through L2).
+enum StageFmt : uint32_t { kCls8 = 0, kOff16 = 1, kOff32 = 2 };
 
 // One membership test of a launch.
 struct DevTest {

@@ -441,6 +441,26 @@ __device__ __forceinline__ void run_smem(uint32_t (&s)[K], uint32_t tb, uint32_t
     }
 }
 
+// Shared-memory table with an 8-bit class stream: one 16-byte read covers 16
+// steps; the row of class c starts at tb + c * rowbytes.
+template <int K, int SB>
+__device__ __forceinline__ void run_smem8(uint32_t (&s)[K], uint32_t tb, uint32_t rowbytes,
+                                          uint32_t stage_addr, int S) {
+    for (int j = 0; j < S; j += 16) {
+        const uint4 w = lds_v4(stage_addr + j);
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t row = tb + ((words[h] >> (8 * b)) & 0xFFu) * rowbytes;
+#pragma unroll
+                for (int u = 0; u < K; ++u) s[u] = SB == 1 ? lds_u8(row + s[u]) : lds_u16(row + s[u]);
+            }
+        }
+    }
+}
+
 // Same with the table read through L2 (32-bit row offsets, 4 per 16 bytes).
 template <int K, int SB>
 __device__ __forceinline__ void run_global(uint32_t (&s)[K], const uint8_t* tbl, uint32_t stage_addr,
@@ -477,9 +497,11 @@ struct TileCtx {
 // Convert bytes [pos, pos+8) of chunk ci to 8 row offsets and store them
 // at stage[ci*S + pos_in_seg].  Positions past the chunk end get the
 // identity row; bytes outside Sigma flag the test and also get the identity row.
-template <bool OFF32>
+template <uint32_t FMT>
 __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, uint32_t dst,
                                             uint32_t boff, uint32_t id_off, uint32_t* test_err) {
+    constexpr bool OFF32 = FMT == kOff32;
+    constexpr bool CLS8 = FMT == kCls8;
     uint32_t o[8];
     if (pos >= m.len) {
 #pragma unroll
@@ -502,12 +524,15 @@ __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, ui
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const uint32_t b = (uint32_t)(v >> (8 * j)) & 0xFFu;
-            uint32_t x = OFF32 ? 0u : 0u;
+            uint32_t x = 0u;
             if (OFF32) {
                 uint32_t t;
                 asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(boff + 4 * b));
                 x = t;
                 if ((uint32_t)j < nvalid && x == kNone32) { bad = true; x = id_off; }
+            } else if (CLS8) {
+                x = lds_u8(boff + b);
+                if ((uint32_t)j < nvalid && x == 0xFFu) { bad = true; x = id_off; }
             } else {
                 x = lds_u16(boff + 2 * b);
                 if ((uint32_t)j < nvalid && x == kNone16) { bad = true; x = id_off; }
@@ -519,13 +544,21 @@ __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, ui
     if (OFF32) {
         sts_v4(dst, make_uint4(o[0], o[1], o[2], o[3]));
         sts_v4(dst + 16, make_uint4(o[4], o[5], o[6], o[7]));
+    } else if (CLS8) {
+        const uint32_t lo = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
+        const uint32_t hi = o[4] | (o[5] << 8) | (o[6] << 16) | (o[7] << 24);
+        asm volatile("st.shared.v2.u32 [%0], {%1,%2};" :: "r"(dst), "r"(lo), "r"(hi) : "memory");
     } else {
         sts_v4(dst, make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
                                o[6] | (o[7] << 16)));
     }
 }
 
-template <bool OFF32>
+__host__ __device__ constexpr uint32_t stage_esz(uint32_t fmt) {
+    return fmt == kOff32 ? 4u : (fmt == kOff16 ? 2u : 1u);
+}
+
+template <uint32_t FMT>
 __device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, uint32_t stage,
                               uint32_t boff, uint32_t id_off, uint32_t* test_err) {
     const int groups = S / 8;
@@ -534,8 +567,8 @@ __device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, ui
         const int ci = it / groups, q = it - ci * groups;
         const ChunkMeta m = meta[ci];
         const uint32_t pos = (uint32_t)seg * (uint32_t)S + 8u * (uint32_t)q;
-        const uint32_t dst = stage + (uint32_t)(ci * S + 8 * q) * (OFF32 ? 4u : 2u);
-        stage_group<OFF32>(m, pos, dst, boff, id_off, test_err);
+        const uint32_t dst = stage + (uint32_t)(ci * S + 8 * q) * stage_esz(FMT);
+        stage_group<FMT>(m, pos, dst, boff, id_off, test_err);
     }
 }
 
@@ -543,7 +576,7 @@ template <int K>
 __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uint32_t maxlen,
                             const TileCtx& c, uint32_t boff, uint32_t* test_err) {
     uint32_t s[K];
-    const bool off32 = d.placement == kGlobal;
+    const uint32_t fmt = d.stage_fmt;
     const uint32_t sh = d.sb == 2 ? 1 : 0;
     if (c.active) {
         const ChunkMeta m = meta[c.ci];
@@ -561,17 +594,22 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
 #pragma unroll
         for (int u = 0; u < K; ++u) s[u] = 0;
     }
-    const uint32_t id_off = d.C * d.qpad * d.sb;
+    const uint32_t rowbytes = d.qpad * d.sb;
+    const uint32_t id_off = fmt == kCls8 ? d.C : d.C * rowbytes;  // the identity row
     const int nseg = (int)((maxlen + c.S - 1) / c.S);
-    const uint32_t esz = off32 ? 4u : 2u;
+    const uint32_t esz = stage_esz(fmt);
     for (int seg = 0; seg < nseg; ++seg) {
         const uint32_t stage = c.stage0 + (uint32_t)(seg & 1) * c.stage_bytes;
-        if (off32) stage_segment<true>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
-        else stage_segment<false>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
+        if (fmt == kCls8) stage_segment<kCls8>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
+        else if (fmt == kOff16) stage_segment<kOff16>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
+        else stage_segment<kOff32>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
         __syncthreads();
         if (c.active) {
             const uint32_t my = stage + (uint32_t)(c.ci * c.S) * esz;
-            if (!off32) {
+            if (fmt == kCls8) {
+                if (d.sb == 1) run_smem8<K, 1>(s, c.tb, rowbytes, my, c.S);
+                else run_smem8<K, 2>(s, c.tb, rowbytes, my, c.S);
+            } else if (fmt == kOff16) {
                 if (d.sb == 1) run_smem<K, 1>(s, c.tb, my, c.S);
                 else run_smem<K, 2>(s, c.tb, my, c.S);
             } else {
@@ -741,8 +779,16 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 uint4* dst = reinterpret_cast<uint4*>(sm + L.table);
                 const uint32_t n16 = (d.table_bytes + 15) / 16;
                 for (uint32_t i = tid; i < n16; i += kThreads) dst[i] = __ldg(src + i);
-                uint16_t* bo = reinterpret_cast<uint16_t*>(sm + L.boff);
-                for (int i = tid; i < 256; i += kThreads) bo[i] = __ldg(d.byte_off16 + i);
+                if (d.stage_fmt == kCls8) {
+                    uint8_t* bc = sm + L.boff;
+                    for (int i = tid; i < 256; i += kThreads) {
+                        const uint32_t c = __ldg(d.byte_class + i);
+                        bc[i] = c == kNone16 ? (uint8_t)0xFF : (uint8_t)c;
+                    }
+                } else {
+                    uint16_t* bo = reinterpret_cast<uint16_t*>(sm + L.boff);
+                    for (int i = tid; i < 256; i += kThreads) bo[i] = __ldg(d.byte_off16 + i);
+                }
             } else {
                 uint32_t* bo = reinterpret_cast<uint32_t*>(sm + L.boff);
                 for (int i = tid; i < 256; i += kThreads) bo[i] = __ldg(d.byte_off32 + i);
@@ -797,9 +843,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             c.r = tid - meta[lo].toff;
             c.active = c.r < (int)meta[lo].cnt;
         }
-        const uint32_t esz = d.placement == kGlobal ? 4u : 2u;
-        int S = (int)(lp.stage_bytes / ((uint32_t)nch * esz)) & ~7;
-        S = S < 8 ? 8 : (S > kMaxSegLen ? kMaxSegLen : S);
+        const uint32_t esz = stage_esz(d.stage_fmt);
+        // positions per chunk per segment: a multiple of 16 (8-bit stream) or 8,
+        // as many as the stage buffer holds for this tile's chunks
+        const int quant = d.stage_fmt == kCls8 ? 16 : 8;
+        int S = (int)(lp.stage_bytes / ((uint32_t)nch * esz)) / quant * quant;
+        S = S < quant ? quant : (S > kMaxSegLen ? kMaxSegLen : S);
         c.S = S;
         c.stage_bytes = lp.stage_bytes;
         c.tb = sa(sm + L.table);
