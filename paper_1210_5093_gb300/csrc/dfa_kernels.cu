@@ -494,64 +494,101 @@ struct TileCtx {
 
 // ------------------------------------------------------------ staging
 
-// Convert bytes [pos, pos+8) of chunk ci to 8 row offsets and store them
-// at stage[ci*S + pos_in_seg].  Positions past the chunk end get the
-// identity row; bytes outside Sigma flag the test and also get the identity row.
+// Convert bytes [pos, pos+16) of a chunk to 16 stage entries (class indices
+// or row offsets) and store them at dst.  The bytes come from two aligned
+// 16-byte loads and a funnel shift (adjacent threads take adjacent groups of
+// the same chunk, so the loads coalesce); near the ends of the string, where
+// an aligned 16-byte read could leave it, they are read one by one.  Positions
+// past the chunk end get the identity row; bytes outside Sigma flag the test
+// and also get the identity row.
+template <uint32_t FMT>
+__device__ __forceinline__ uint32_t stage_entry(uint32_t b, bool valid, uint32_t boff, uint32_t id_off,
+                                                bool& bad) {
+    uint32_t x;
+    if (FMT == kOff32) {
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(x) : "r"(boff + 4 * b));
+        if (x == kNone32) { bad |= valid; x = id_off; }
+    } else if (FMT == kCls8) {
+        x = lds_u8(boff + b);
+        if (x == 0xFFu) { bad |= valid; x = id_off; }
+    } else {
+        x = lds_u16(boff + 2 * b);
+        if (x == kNone16) { bad |= valid; x = id_off; }
+    }
+    return valid ? x : id_off;
+}
+
 template <uint32_t FMT>
 __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, uint32_t dst,
                                             uint32_t boff, uint32_t id_off, uint32_t* test_err) {
-    constexpr bool OFF32 = FMT == kOff32;
-    constexpr bool CLS8 = FMT == kCls8;
-    uint32_t o[8];
-    if (pos >= m.len) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) o[j] = id_off;
-    } else {
-        const uint32_t nvalid = min(8u, m.len - pos);
+    uint32_t v[4] = {0, 0, 0, 0};
+    uint32_t nvalid = 0;
+    if (pos < m.len) {
+        nvalid = min(16u, m.len - pos);
         const uint8_t* a = m.ptr + pos;
-        const uint32_t d = (uint32_t)((uintptr_t)a & 7u);
-        uint64_t v = 0;
-        // fast path: the two aligned 8-byte words around [a, a+8) lie inside the string
-        const bool fast = (pos + m.lo_slack >= d) && (pos + 16u <= m.len + m.hi_slack + d);
+        const uint32_t d = (uint32_t)((uintptr_t)a & 15u);
+        // fast path: the two aligned 16-byte vectors around [a, a+16) lie inside the string
+        const bool fast = (pos + m.lo_slack >= d) && (pos + 32u <= m.len + m.hi_slack + d);
         if (fast) {
-            const uint64_t* al = reinterpret_cast<const uint64_t*>(a - d);
-            const uint64_t w0 = __ldg(al), w1 = __ldg(al + 1);
-            v = d ? ((w0 >> (8 * d)) | (w1 << (64 - 8 * d))) : w0;
-        } else {
-            for (uint32_t j = 0; j < nvalid; ++j) v |= (uint64_t)__ldg(a + j) << (8 * j);
-        }
-        bool bad = false;
+            const uint4* al = reinterpret_cast<const uint4*>(a - d);
+            const uint4 x0 = __ldg(al), x1 = __ldg(al + 1);
+            const uint32_t q = d >> 2, r = (d & 3u) * 8u;
+            uint32_t sel[5];
+            sel[0] = q == 0 ? x0.x : (q == 1 ? x0.y : (q == 2 ? x0.z : x0.w));
+            sel[1] = q == 0 ? x0.y : (q == 1 ? x0.z : (q == 2 ? x0.w : x1.x));
+            sel[2] = q == 0 ? x0.z : (q == 1 ? x0.w : (q == 2 ? x1.x : x1.y));
+            sel[3] = q == 0 ? x0.w : (q == 1 ? x1.x : (q == 2 ? x1.y : x1.z));
+            sel[4] = q == 0 ? x1.x : (q == 1 ? x1.y : (q == 2 ? x1.z : x1.w));
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t b = (uint32_t)(v >> (8 * j)) & 0xFFu;
-            uint32_t x = 0u;
-            if (OFF32) {
-                uint32_t t;
-                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(t) : "r"(boff + 4 * b));
-                x = t;
-                if ((uint32_t)j < nvalid && x == kNone32) { bad = true; x = id_off; }
-            } else if (CLS8) {
-                x = lds_u8(boff + b);
-                if ((uint32_t)j < nvalid && x == 0xFFu) { bad = true; x = id_off; }
-            } else {
-                x = lds_u16(boff + 2 * b);
-                if ((uint32_t)j < nvalid && x == kNone16) { bad = true; x = id_off; }
+            for (int i = 0; i < 4; ++i) v[i] = __funnelshift_r(sel[i], sel[i + 1], r);
+        } else {
+            uint64_t lo = 0, hi = 0;
+            for (uint32_t j = 0; j < nvalid; ++j) {
+                const uint64_t byte = __ldg(a + j);
+                if (j < 8) lo |= byte << (8 * j); else hi |= byte << (8 * (j - 8));
             }
-            o[j] = (uint32_t)j < nvalid ? x : id_off;
+            v[0] = (uint32_t)lo; v[1] = (uint32_t)(lo >> 32);
+            v[2] = (uint32_t)hi; v[3] = (uint32_t)(hi >> 32);
         }
-        if (bad) atomicOr(test_err + m.test, 1u);
     }
-    if (OFF32) {
-        sts_v4(dst, make_uint4(o[0], o[1], o[2], o[3]));
-        sts_v4(dst + 16, make_uint4(o[4], o[5], o[6], o[7]));
-    } else if (CLS8) {
-        const uint32_t lo = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
-        const uint32_t hi = o[4] | (o[5] << 8) | (o[6] << 16) | (o[7] << 24);
-        asm volatile("st.shared.v2.u32 [%0], {%1,%2};" :: "r"(dst), "r"(lo), "r"(hi) : "memory");
+    bool bad = false;
+    if (FMT == kCls8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t j = 4 * i + k;
+                word |= stage_entry<FMT>((v[i] >> (8 * k)) & 0xFFu, j < nvalid, boff, id_off, bad) << (8 * k);
+            }
+            w[i] = word;
+        }
+        sts_v4(dst, make_uint4(w[0], w[1], w[2], w[3]));
+    } else if (FMT == kOff16) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t j = 8 * h + 2 * i;
+                const uint32_t src = v[j >> 2] >> (8 * (j & 3));
+                w[i] = stage_entry<FMT>(src & 0xFFu, j < nvalid, boff, id_off, bad) |
+                       (stage_entry<FMT>((src >> 8) & 0xFFu, j + 1 < nvalid, boff, id_off, bad) << 16);
+            }
+            sts_v4(dst + 16 * h, make_uint4(w[0], w[1], w[2], w[3]));
+        }
     } else {
-        sts_v4(dst, make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
-                               o[6] | (o[7] << 16)));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                w[k] = stage_entry<FMT>((v[i] >> (8 * k)) & 0xFFu, 4u * i + k < nvalid, boff, id_off, bad);
+            sts_v4(dst + 16 * i, make_uint4(w[0], w[1], w[2], w[3]));
+        }
     }
+    if (bad) atomicOr(test_err + m.test, 1u);
 }
 
 __host__ __device__ constexpr uint32_t stage_esz(uint32_t fmt) {
@@ -561,13 +598,13 @@ __host__ __device__ constexpr uint32_t stage_esz(uint32_t fmt) {
 template <uint32_t FMT>
 __device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, uint32_t stage,
                               uint32_t boff, uint32_t id_off, uint32_t* test_err) {
-    const int groups = S / 8;
+    const int groups = S / 16;
     const int items = nch * groups;
     for (int it = threadIdx.x; it < items; it += kThreads) {
         const int ci = it / groups, q = it - ci * groups;
         const ChunkMeta m = meta[ci];
-        const uint32_t pos = (uint32_t)seg * (uint32_t)S + 8u * (uint32_t)q;
-        const uint32_t dst = stage + (uint32_t)(ci * S + 8 * q) * stage_esz(FMT);
+        const uint32_t pos = (uint32_t)seg * (uint32_t)S + 16u * (uint32_t)q;
+        const uint32_t dst = stage + (uint32_t)(ci * S + 16 * q) * stage_esz(FMT);
         stage_group<FMT>(m, pos, dst, boff, id_off, test_err);
     }
 }
@@ -846,7 +883,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
         const uint32_t esz = stage_esz(d.stage_fmt);
         // positions per chunk per segment: a multiple of 16 (8-bit stream) or 8,
         // as many as the stage buffer holds for this tile's chunks
-        const int quant = d.stage_fmt == kCls8 ? 16 : 8;
+        const int quant = 16;
         int S = (int)(lp.stage_bytes / ((uint32_t)nch * esz)) / quant * quant;
         S = S < quant ? quant : (S > kMaxSegLen ? kMaxSegLen : S);
         c.S = S;
