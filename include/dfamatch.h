@@ -205,6 +205,19 @@ int dfa_plan_sets(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
 int dfa_match_num_kernels(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts,
                           uint32_t *n);
 
+/*
+ * Inspection: run a single test on dev_str and return its chunk maps, the
+ * vectors L_k of Sec. 4.1: maps[k*(num_states+1) + j] = delta*(j, chunk k)
+ * for every j in the chunk's initial-state set I_k, and j (the identity, as
+ * in Algorithm 3's initialisation) for the other states.  maps has
+ * P*(num_states+1) entries, P as returned in *P (at most cap chunks are
+ * written).  *final_state receives the test's answer.  Allocates temporary
+ * device memory and synchronises the device.
+ */
+int dfa_debug_chunk_maps(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
+                         const dfa_match_opts_t *opts, uint16_t *maps, uint32_t cap, uint32_t *P,
+                         uint32_t *final_state);
+
 /* Device workspace needed by dfa_match_async for (dfa, len, opts). */
 int dfa_match_workspace_size(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts,
                              uint64_t *bytes);
@@ -216,7 +229,9 @@ int dfa_match_workspace_size(const dfa_t *dfa, uint64_t len, const dfa_match_opt
  * must not be used by another launch until this one completes.  Launches
  * only kernels and memsets (no allocation, no host synchronisation), so it
  * can be captured in a CUDA graph.  A byte outside Sigma is reported in
- * dev_out->status.  Errors (returned): DFA_EINVAL, DFA_ENOSPACE, DFA_ECUDA.
+ * dev_out->status.  dev_out must be 4-byte aligned and dev_workspace
+ * 256-byte aligned (DFA_EINVAL otherwise).
+ * Errors (returned): DFA_EINVAL, DFA_ENOSPACE, DFA_ECUDA.
  */
 int dfa_match_async(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
                     const dfa_match_opts_t *opts, dfa_result_t *dev_out, void *dev_workspace,

@@ -86,6 +86,7 @@ SIGNATURES = {
     "dfa_plan_chunks": (_I, [_P, _U64, _P, _P]),
     "dfa_match_num_kernels": (_I, [_P, _U64, _P, _P]),
     "dfa_plan_sets": (_I, [_P, _P, _U64, _P, _P, _U32, _P]),
+    "dfa_debug_chunk_maps": (_I, [_P, _P, _U64, _P, _P, _U32, _P, _P]),
     "dfa_match_workspace_size": (_I, [_P, _U64, _P, _P]),
     "dfa_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
     "dfa_match_noalloc": (_I, [_P, _P, _U64, _P, _P, _P]),
@@ -281,6 +282,22 @@ class Dfa:
         _check(lib().dfa_match_num_kernels(self._h, n, ctypes.byref(o), ctypes.byref(out)),
                "dfa_match_num_kernels")
         return int(out.value)
+
+    def chunk_maps(self, dev_data, num_chunks: int = 0, lookahead: int = 1):
+        """(L maps [P, |Q|+1] uint16, final_state): the chunk maps of Sec. 4.1 as the
+        match kernel computed them (identity outside each chunk's I_k)."""
+        o = _opts(num_chunks, 0, lookahead)
+        n = dev_data.numel()
+        P = ctypes.c_uint32()
+        ptr = dev_data.data_ptr() if n else None
+        _check(lib().dfa_debug_chunk_maps(self._h, ptr, n, ctypes.byref(o), None, 0, ctypes.byref(P),
+                                          None), "dfa_debug_chunk_maps")
+        qe = self.num_states + 1
+        out = np.zeros((P.value, qe), dtype=np.uint16)
+        fs = ctypes.c_uint32()
+        _check(lib().dfa_debug_chunk_maps(self._h, ptr, n, ctypes.byref(o), out.ctypes.data, P.value,
+                                          ctypes.byref(P), ctypes.byref(fs)), "dfa_debug_chunk_maps")
+        return out, int(fs.value)
 
     def plan_sets(self, dev_data, num_chunks: int = 0, multiplicity: int = 0,
                   lookahead: int = 1) -> np.ndarray:

@@ -571,6 +571,48 @@ int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t* starts) {
     return DFA_OK;
 }
 
+__global__ void k_identity_maps(uint16_t* maps, uint64_t P, uint32_t qe) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < P * qe;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        maps[i] = (uint16_t)(i % qe);
+}
+
+int dfa_debug_chunk_maps(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
+                         const dfa_match_opts_t* opts, uint16_t* maps, uint32_t cap, uint32_t* P,
+                         uint32_t* final_state) {
+    if (!P || (len && !dev_str)) return DFA_EINVAL;
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    *P = s.lp.ptot;
+    if (!maps || cap == 0) return DFA_OK;
+    const uint32_t qe = s.lp.qe_max;
+    const uint64_t map_bytes = up(2ull * s.lp.ptot * qe, 256);  // keeps the result 256-byte aligned
+    uint8_t* ws = nullptr;
+    if (cudaMalloc(&ws, s.ws.total + map_bytes + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return DFA_ENOMEM;
+    }
+    uint16_t* dmaps = reinterpret_cast<uint16_t*>(ws + s.ws.total);
+    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(ws + s.ws.total + map_bytes);
+    k_identity_maps<<<1024, 256>>>(dmaps, s.lp.ptot, qe);
+    s.lp.test1.str = dev_str;
+    bind(s.lp, ws, s.ws);
+    s.lp.results = dres;
+    s.lp.dbg_maps = dmaps;
+    rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr);
+    dfa_result_t r{};
+    const uint32_t n = std::min(cap, s.lp.ptot);
+    if (rc == DFA_OK && cudaMemcpy(maps, dmaps, 2ull * n * qe, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = DFA_ECUDA;
+    if (rc == DFA_OK && cudaMemcpy(&r, dres, sizeof r, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = DFA_ECUDA;
+    cudaFree(ws);
+    if (rc == DFA_OK && final_state) *final_state = r.final_state;
+    if (rc == DFA_OK && r.status != DFA_OK) rc = r.status;
+    return rc;
+}
+
 int dfa_match_num_kernels(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, uint32_t* n) {
     if (!n) return DFA_EINVAL;
     Single s;
@@ -626,6 +668,8 @@ int dfa_match_async(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
                     const dfa_match_opts_t* opts, dfa_result_t* dev_out, void* ws,
                     uint64_t ws_bytes, void* stream) {
     if (!dev_out || (len && !dev_str) || !ws) return DFA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(dev_out) & 3u) || (reinterpret_cast<uintptr_t>(ws) & 255u))
+        return DFA_EINVAL;  // results are 4-byte aligned, the workspace 256-byte aligned
     Single s;
     int rc = plan_single(d, len, opts, &s);
     if (rc != DFA_OK) return rc;
@@ -752,7 +796,7 @@ int dfa_batch_prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* c
 }
 
 int dfa_batch_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) {
-    if (!b || !dev_out) return DFA_EINVAL;
+    if (!b || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 3u)) return DFA_EINVAL;
     LaunchPlan lp;
     fill_plan(b->p, lp, b->ws, dev_out);
     return launch_plan(lp, b->p.kmax, b->p.smem, static_cast<cudaStream_t>(stream), nullptr,
@@ -767,7 +811,7 @@ int dfa_batch_set_events(dfa_batch_t* b, void* ev_begin, void* ev_end) {
 }
 
 int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) {
-    if (!b || !dev_out) return DFA_EINVAL;
+    if (!b || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 3u)) return DFA_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!b->exec || b->graph_out != dev_out) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }

@@ -118,6 +118,7 @@ struct LaunchPlan {
     uint16_t* sets;             // lookahead-set arena (r >= 2), see DevGroup
     uint32_t* set_size;         // [ptot] |I| of each chunk computed by k_lookahead
     uint32_t dyn;               // 1 if some test uses r >= 2 lookahead symbols
+    uint16_t* dbg_maps;         // optional [ptot * qe_max]: chunk maps L_k (identity pre-filled)
     uint32_t qe_max;            // largest |Q|+1 of the launch's DFAs
     dfa_result_t* results;      // [ntests] in the caller's order (DevTest::out)
     // single-test launches carry their descriptors by value (tests/groups == nullptr)

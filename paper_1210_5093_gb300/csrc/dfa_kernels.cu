@@ -611,7 +611,8 @@ __device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, ui
 
 template <int K>
 __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uint32_t maxlen,
-                            const TileCtx& c, uint32_t boff, uint32_t* test_err) {
+                            const TileCtx& c, uint32_t boff, uint32_t* test_err,
+                            uint16_t* dbg_maps, uint32_t dbg_stride, uint32_t g0) {
     uint32_t s[K];
     const uint32_t fmt = d.stage_fmt;
     const uint32_t sh = d.sb == 2 ? 1 : 0;
@@ -657,11 +658,16 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
         // the next segment stages into the other buffer, so one barrier per segment suffices
     }
     if (c.active) {
+        const ChunkMeta m = meta[c.ci];
 #pragma unroll
         for (int u = 0; u < K; ++u) {
             uint32_t v = s[u] >> sh;
             asm volatile("st.shared.u16 [%0], %1;" :: "r"(c.lmap + 2u * ((uint32_t)(threadIdx.x) * K + u)),
                          "h"((uint16_t)v) : "memory");
+            // inspection output: L_k[j] = delta*(j, chunk k) for j in I_k (Sec. 4.1)
+            const uint32_t slot = (uint32_t)c.r * K + u;
+            if (dbg_maps && slot < m.size)
+                dbg_maps[(size_t)(g0 + c.ci) * dbg_stride + m.init[slot]] = (uint16_t)v;
         }
     }
 }
@@ -896,10 +902,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
         c.sb = (int)d.sb;
         c.placement = (int)d.placement;
         const uint32_t boff = sa(sm + L.boff);
-        if (d.K == 2) tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err);
-        else if (KMAX >= 8 && d.K == 4) tile_chains<(KMAX >= 8 ? 4 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err);
-        else if (KMAX >= 16 && d.K == 8) tile_chains<(KMAX >= 16 ? 8 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err);
-        else tile_chains<KMAX>(d, meta, nch, maxlen, c, boff, lp.test_err);
+        uint16_t* dbg = lp.dbg_maps;
+        const uint32_t dst_ = lp.qe_max;
+        if (d.K == 2) tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        else if (KMAX >= 8 && d.K == 4)
+            tile_chains<(KMAX >= 8 ? 4 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        else if (KMAX >= 16 && d.K == 8)
+            tile_chains<(KMAX >= 16 ? 8 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        else tile_chains<KMAX>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         __syncthreads();
 
         // Compose the tile's chunk maps, in order, into the running map of each

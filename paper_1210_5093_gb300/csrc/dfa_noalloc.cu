@@ -50,6 +50,7 @@ extern "C" int dfa_match_noalloc(const dfa_t* dfa, const uint8_t* dev_str, uint6
                                  const dfa_match_opts_t* opts, dfa_result_t* dev_out,
                                  void* stream) {
     if (!dfa || !dev_out || (len && !dev_str)) return DFA_EINVAL;
+    if (reinterpret_cast<uintptr_t>(dev_out) & 3u) return DFA_EINVAL;  // results are 4-byte aligned
     dfam::Single s;
     int rc = dfam::plan_single(dfa, len, opts, &s);
     if (rc != DFA_OK) return rc;

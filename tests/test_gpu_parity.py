@@ -390,3 +390,43 @@ def test_largest_dfa_and_k16(dm):
     for P in (0, 1, 777):
         _check(dm, d, spec, data, num_chunks=P)
     _check(dm, d, spec, data, num_chunks=500, lookahead=0)   # Algorithm 2: all 4096 states
+
+
+@pytest.mark.parametrize("which", ["fig6", "plain", "regex", "protein", "random_missing"])
+def test_chunk_maps_equal_algorithm3(dm, which):
+    """The chunk maps L_k the match kernel computes (Sec. 4.1: L_k[j] =
+    delta*(j, chunk k) for j in I_k, identity elsewhere) equal the oracle's
+    Algorithm 3 maps entry by entry, on the same partition."""
+    import torch
+    from tests._golden import dfa_from, load, symbol_map
+    if which == "fig6":
+        f = load("w2_fig6.txt")
+        Q, syms, delta, q0, finals = dfa_from(f)
+        spec = gen.DfaSpec(Q, len(syms), delta, q0, np.array(finals, np.uint32), symbol_map(syms))
+        data = np.frombuffer((f["input"][0][0] * 40).encode(), dtype=np.uint8).copy()
+    elif which == "plain":
+        spec, data = gen.plain_dfa(1), gen.uniform_bytes(1, 1 << 20)
+    elif which == "regex":
+        spec, data = gen.regex_dfa(2), gen.zipf_text(2, 1 << 20)
+    elif which == "protein":
+        spec, data = gen.protein_dfa(3), gen.protein_text(3, 1 << 20)
+    else:
+        spec = gen.random_dfa(99, 40, 256, num_finals=5, missing=0.05)
+        data = gen.uniform_bytes(98, 1 << 18)
+    d = dm.Dfa.from_spec(spec)
+    dev = torch.from_numpy(np.ascontiguousarray(data)).cuda()
+    od = oracle.Dfa.from_spec(spec)
+    for P in (3, 257, 2000):
+        if P > len(data):
+            continue
+        got, fs = d.chunk_maps(dev, num_chunks=P)
+        st, efs, eacc, want = od.chunked(data, oracle.chunk_starts(len(data), P, 1), want_maps=True)
+        assert st == 0 and fs == efs
+        assert got.shape == want.shape
+        assert np.array_equal(got.astype(np.uint32), want), (which, P)
+        # with r = 2 the kernel matches fewer states; those it matches agree with Algorithm 3
+        got2, fs2 = d.chunk_maps(dev, num_chunks=P, lookahead=2)
+        ident = np.arange(spec.num_states + 1, dtype=np.uint32)[None, :]
+        g2 = got2.astype(np.uint32)
+        assert fs2 == efs
+        assert np.all((g2 == want) | (g2 == ident))
