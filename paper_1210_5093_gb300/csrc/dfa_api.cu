@@ -44,8 +44,7 @@ WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t pt
     w.off = take(4ull * (ptot + 1));
     w.bsum = take(4ull * (nblk + 1));
     w.tile_first = take(4ull * (ptot + 1));
-    w.tile_base = take(4ull * (ngroups + 1));
-    w.tile_eff = take(4ull * ngroups);
+    w.wtiles = take(4ull * ((ptot + 511) / 512 + 1));
     w.num_tiles = take(4);
     w.test_err = take(8ull * ntests);  // test_err[ntests] then arrived[ntests]
     w.first_cta = take(4ull * ntests);
@@ -65,8 +64,7 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
     lp.off = reinterpret_cast<uint32_t*>(base + w.off);
     lp.bsum = reinterpret_cast<uint32_t*>(base + w.bsum);
     lp.tile_first = reinterpret_cast<uint32_t*>(base + w.tile_first);
-    lp.tile_base = reinterpret_cast<uint32_t*>(base + w.tile_base);
-    lp.tile_eff = reinterpret_cast<uint32_t*>(base + w.tile_eff);
+    lp.wtiles = reinterpret_cast<uint32_t*>(base + w.wtiles);
     lp.num_tiles = reinterpret_cast<uint32_t*>(base + w.num_tiles);
     lp.test_err = reinterpret_cast<uint32_t*>(base + w.test_err);
     lp.arrived = lp.test_err + lp.ntests;
@@ -618,7 +616,7 @@ int dfa_match_num_kernels(const dfa_t* d, uint64_t len, const dfa_match_opts_t* 
     Single s;
     int rc = plan_single(d, len, opts, &s);
     if (rc != DFA_OK) return rc;
-    *n = (s.lp.ptot <= 16384 ? 2u : 6u) + (s.lp.dyn ? 1u : 0u);
+    *n = (s.lp.ptot <= 16384 ? 2u : 7u) + (s.lp.dyn ? 1u : 0u);
     return DFA_OK;
 }
 
@@ -849,7 +847,7 @@ int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) 
 
 int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
     if (!b || !n) return DFA_EINVAL;
-    *n = (b->p.dyn ? 7 : 6) - (b->p.ptot <= 16384 ? 4 : 0);
+    *n = (b->p.ptot <= 16384 ? 2u : 7u) + (b->p.dyn ? 1u : 0u);
     return DFA_OK;
 }
 

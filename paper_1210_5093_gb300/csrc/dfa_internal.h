@@ -102,12 +102,11 @@ struct LaunchPlan {
     uint32_t stage_bytes;       // bytes of one of the two stage buffers
     uint32_t* chunk_test;       // [ptot]
     uint16_t* chunk_cls;        // [ptot]
-    uint32_t* cost;             // [ptot] thread slots charged to the chunk
+    uint32_t* cost;             // [ptot] packing word: thread slots, DFA cost_max, group start
     uint32_t* off;              // [ptot+1] exclusive prefix of cost (within the launch)
     uint32_t* bsum;             // [nblk+1]
     uint32_t* tile_first;       // [ptot+1]
-    uint32_t* tile_base;        // [ngroups+1]
-    uint32_t* tile_eff;         // [ngroups] slot window of one tile
+    uint32_t* wtiles;           // [nwin+1] tiles per packing window, then their bases
     uint32_t* num_tiles;        // [1]
     uint32_t* test_err;         // [ntests]
     uint32_t* arrived;          // [ntests]
@@ -128,8 +127,8 @@ struct LaunchPlan {
 
 // Workspace carve-up of one launch (byte offsets into the device workspace).
 struct WsLayout {
-    uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, bsum, tile_first, tile_base,
-        tile_eff, num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
+    uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, bsum, tile_first, wtiles,
+        num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
 };
 
 // A batch planned on the host: descriptors, sizes and the workspace layout.

@@ -6,8 +6,7 @@
 //   k_count        per chunk: test, reverse-lookahead class, thread slots  (Alg. 3 l.16, Eq. 11)
 //   k_scan_blocks  exclusive scan of the per-block slot sums
 //   k_offsets      per-chunk slot offsets
-//   k_group_tiles  tiles per DFA group, tile bases
-//   k_tiles        first chunk of every tile
+//   k_pack (x2), k_scan_windows   greedy packing of chunks into tiles
 //   k_match        persistent: stage chunks, advance every (chunk, state) chain,
 //                  compose the chunk maps, combine per test             (Alg. 3 l.8-20, Eqs. 8-9)
 //
@@ -204,6 +203,14 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
     if (lane == 0) lp.set_size[g] = n;
 }
 
+// Per-chunk packing word: thread slots (bits 0-9), the cost_max of the
+// chunk's DFA (bits 10-19) and a group-start flag (bit 20).  Both costs are
+// at most kThreads / 2 (the compiler keeps ceil(|I| / K) <= 256).
+__device__ __forceinline__ uint32_t pack_word(uint32_t cost, uint32_t cost_max, bool fresh) {
+    return cost | (cost_max << 10) | ((uint32_t)fresh << 20);
+}
+__device__ __forceinline__ uint32_t word_cost(uint32_t w) { return w & 0x3FFu; }
+
 // Per chunk g: owning test, reverse-lookahead class (Algorithm 3 line 16)
 // and the thread slots it is charged: ceil(|I_k| / K), at least 2.  Writes
 // chunk_test, chunk_cls and cost; returns the cost.
@@ -230,9 +237,13 @@ __device__ uint32_t chunk_count(const LaunchPlan& lp, uint32_t g) {
     const uint32_t size = cls == dyn_set(d.C) ? lp.set_size[g] : d.iset_off[cls + 1] - d.iset_off[cls];
     const uint32_t cnt = (size + d.K - 1) / d.K;
     const uint32_t cost = cnt < 2 ? 2 : cnt;
+    // a chunk opens a new DFA group when it is the first chunk of the launch,
+    // or the first of a test whose group differs from the previous chunk's
+    bool fresh = g == 0;
+    if (!fresh && k == 0) fresh = test_at(lp, find_test(lp, g - 1)).group != t.group;
     lp.chunk_test[g] = lo;
     lp.chunk_cls[g] = (uint16_t)cls;
-    lp.cost[g] = cost;
+    lp.cost[g] = pack_word(cost, d.cost_max, fresh);
     return cost;
 }
 
@@ -263,119 +274,147 @@ __global__ void __launch_bounds__(kPlanThreads) k_scan_blocks(LaunchPlan lp) {
 __global__ void __launch_bounds__(kPlanThreads) k_offsets(LaunchPlan lp) {
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
     const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
-    uint32_t v = g < lp.ptot ? lp.cost[g] : 0;
+    uint32_t v = g < lp.ptot ? word_cost(lp.cost[g]) : 0;
     uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, nullptr);
     if (g < lp.ptot) lp.off[g] = lp.bsum[blockIdx.x] + ex;
     if (g == 0) lp.off[lp.ptot] = lp.bsum[lp.nblk];
 }
 
-__device__ __forceinline__ uint32_t group_nt_eff(const DevDfa& d) {
-    return (uint32_t)kThreads - (d.cost_max - 1);
+
+// Tile packing.  A tile is a run of consecutive chunks of one DFA group whose
+// thread slots fit one CTA; chunks are packed greedily in order: a chunk
+// opens a new tile when it starts a new group or would overflow the budget.
+// The budget is kThreads, or less when the whole launch needs fewer thread
+// slots than the grid holds: then tiles shrink to about ceil(total / CTAs)
+// slots so a small launch spreads over every SM (fewer chunks per tile,
+// longer staged segments).  A greedy tile leaves fewer than cost_max slots
+// unused, so a budget of ceil(total / CTAs) + cost_max - 1 keeps the tile
+// count within the grid.  It never drops below one chunk's slots.
+//
+// The greedy pass is split into windows of kPackWin chunks, one warp each
+// (a window boundary also opens a tile, so each window packs independently):
+// pass 0 counts each window's tiles, a scan turns the counts into bases,
+// pass 1 repeats the same packing and writes each tile's first chunk.
+constexpr uint32_t kPackWin = 512;  // chunks per window of the multi-kernel path
+
+__device__ __forceinline__ uint32_t tile_budget(uint32_t cost_max, uint32_t spread) {
+    return max(cost_max, min((uint32_t)kThreads, spread + cost_max - 1));
 }
 
-// Tiles per group: a tile holds the chunks whose slot offset (relative to the
-// group's first chunk) falls in one window of `eff` slots, so a tile never
-// needs more than kThreads threads.  eff is the full window (kThreads minus
-// the largest chunk's slots, less one) unless the whole launch needs fewer
-// thread slots than the grid holds: then the windows shrink so the tiles
-// spread over all CTAs (fewer chunks per tile, longer staged segments, more
-// SMs on a latency-bound launch).  eff never drops below one chunk's slots.
-__global__ void __launch_bounds__(kPlanThreads) k_group_tiles(LaunchPlan lp) {
-    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
-    uint32_t carry = 0;
+// One warp packs chunks [w0, w1) from their packing words; returns its tile
+// count.  Every lane runs the same greedy pass (words are read 16 at a time
+// with independent loads, then scanned in registers); with out != nullptr,
+// lane 0 writes each tile's first chunk to out[0..].  `words` is global or
+// shared memory.
+__device__ uint32_t pack_window(const uint32_t* words, uint32_t w0, uint32_t w1, uint32_t spread,
+                                uint32_t* out) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t tiles = 0, cur = 0, budget = 0;
+    for (uint32_t b = w0; b < w1; b += 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (uint32_t i = 0; i < 16; ++i) v[i] = b + i < w1 ? words[b + i] : 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < 16; ++i) {
+            if (b + i >= w1) break;
+            const uint32_t c = word_cost(v[i]);
+            if ((v[i] >> 20) || b + i == w0) {
+                budget = tile_budget((v[i] >> 10) & 0x3FFu, spread);
+                cur = budget;  // force a new tile
+            }
+            if (cur + c > budget) {
+                if (out && lane == 0) out[tiles] = b + i;
+                ++tiles;
+                cur = 0;
+            }
+            cur += c;
+        }
+    }
+    return tiles;
+}
+
+constexpr int kPackWarps = 8;
+
+__global__ void __launch_bounds__(kPackWarps * 32) k_pack(LaunchPlan lp, uint32_t pass) {
+    const uint32_t w = blockIdx.x * kPackWarps + (threadIdx.x >> 5);
+    const uint32_t w0 = w * kPackWin;
+    if (w0 >= lp.ptot) return;  // warp-uniform
     const uint32_t total = lp.bsum[lp.nblk];
     const uint32_t spread = (total + lp.grid - 1) / lp.grid;
-    for (uint32_t base = 0; base < lp.ngroups; base += kPlanThreads) {
-        uint32_t i = base + threadIdx.x;
-        uint32_t nt = 0;
-        if (i < lp.ngroups) {
-            const DevGroup gr = group_at(lp, i);
-            const DevDfa& dd = lp.dfas[gr.dfa];
-            uint32_t eff = group_nt_eff(dd);
-            eff = max(dd.cost_max, min(eff, spread));
-            lp.tile_eff[i] = eff;
-            nt = (lp.off[gr.end_chunk - 1] - lp.off[gr.first_chunk]) / eff + 1;
-        }
+    const uint32_t w1 = min(w0 + kPackWin, lp.ptot);
+    if (pass == 0) {
+        const uint32_t n = pack_window(lp.cost, w0, w1, spread, nullptr);
+        if ((threadIdx.x & 31) == 0) lp.wtiles[w] = n;
+    } else {
+        pack_window(lp.cost, w0, w1, spread, lp.tile_first + lp.wtiles[w]);
+    }
+}
+
+// Exclusive scan of the per-window tile counts (one CTA); the total is the
+// number of tiles, and tile_first[T] = ptot closes the last tile.
+__global__ void __launch_bounds__(kPlanThreads) k_scan_windows(LaunchPlan lp, uint32_t nwin) {
+    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nwin; base += kPlanThreads) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nwin ? lp.wtiles[i] : 0;
         uint32_t total;
-        uint32_t ex = block_excl_scan<kPlanThreads>(nt, tmp, &total);
-        if (i < lp.ngroups) lp.tile_base[i] = carry + ex;
+        const uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
+        if (i < nwin) lp.wtiles[i] = carry + ex;
         carry += total;
     }
     if (threadIdx.x == 0) {
-        lp.tile_base[lp.ngroups] = carry;
         *lp.num_tiles = carry;
         lp.tile_first[carry] = lp.ptot;
     }
 }
 
-__global__ void __launch_bounds__(kPlanThreads) k_tiles(LaunchPlan lp) {
-    const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
-    if (g >= lp.ptot) return;
-    const uint32_t grp = test_at(lp, lp.chunk_test[g]).group;
-    const DevGroup gr = group_at(lp, grp);
-    const uint32_t eff = lp.tile_eff[grp];
-    const uint32_t base = lp.off[gr.first_chunk];
-    const uint32_t lt = (lp.off[g] - base) / eff;
-    const bool first = g == gr.first_chunk || (lp.off[g - 1] - base) / eff != lt;
-    if (first) lp.tile_first[lp.tile_base[grp] + lt] = g;
-}
-
-// All of k_count .. k_tiles in one CTA, for launches with at most
-// kSmallPlan chunks (saves four launches on latency-bound calls).  Same
-// results as the five kernels.
+// All planning steps in one CTA, for launches with at most kSmallPlan chunks
+// (saves five launches on latency-bound calls).  The packing words stay in
+// shared memory and the greedy pass is split into 32 windows of
+// ceil(ptot / 32) chunks (rounded up to 16), one per warp, so a small launch
+// is packed by every warp; tiles are the same as the multi-kernel path's
+// except at window boundaries, which open a tile in both.
 constexpr uint32_t kSmallPlan = 16384;
+constexpr uint32_t kSmallPlanSmem = kSmallPlan * 4;
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp) {
+    extern __shared__ uint32_t pw[];  // packing words, kSmallPlan entries
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    __shared__ uint32_t wt[kPlanThreads / 32];
     // per-chunk counts and the exclusive scan, 1024 chunks per round
     uint32_t carry = 0;
     for (uint32_t base = 0; base < lp.ptot; base += kPlanThreads) {
         const uint32_t g = base + threadIdx.x;
         const uint32_t cost = g < lp.ptot ? chunk_count(lp, g) : 0;
+        if (g < lp.ptot) pw[g] = lp.cost[g];
         uint32_t total;
         const uint32_t ex = block_excl_scan<kPlanThreads>(cost, tmp, &total);
         if (g < lp.ptot) lp.off[g] = carry + ex;
         carry += total;
     }
-    if (threadIdx.x == 0) {
-        lp.off[lp.ptot] = carry;
-        lp.bsum[lp.nblk] = carry;  // the total, read by the tile windows below
-    }
+    if (threadIdx.x == 0) lp.off[lp.ptot] = carry;
     __syncthreads();
-    // tile windows and bases per group (as k_group_tiles)
     const uint32_t spread = (carry + lp.grid - 1) / lp.grid;
-    uint32_t tcarry = 0;
-    for (uint32_t base = 0; base < lp.ngroups; base += kPlanThreads) {
-        const uint32_t i = base + threadIdx.x;
-        uint32_t nt = 0;
-        if (i < lp.ngroups) {
-            const DevGroup gr = group_at(lp, i);
-            const DevDfa& dd = lp.dfas[gr.dfa];
-            const uint32_t eff = max(dd.cost_max, min(group_nt_eff(dd), spread));
-            lp.tile_eff[i] = eff;
-            nt = (lp.off[gr.end_chunk - 1] - lp.off[gr.first_chunk]) / eff + 1;
-        }
-        uint32_t total;
-        const uint32_t ex = block_excl_scan<kPlanThreads>(nt, tmp, &total);
-        if (i < lp.ngroups) lp.tile_base[i] = tcarry + ex;
-        tcarry += total;
-    }
+    const uint32_t nw = kPlanThreads / 32;
+    const uint32_t win = ((lp.ptot + nw - 1) / nw + 15u) & ~15u;
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t w0 = min(w * win, lp.ptot), w1 = min(w0 + win, lp.ptot);
+    const uint32_t n = pack_window(pw, w0, w1, spread, nullptr);
+    if ((threadIdx.x & 31) == 0) wt[w] = n;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        lp.tile_base[lp.ngroups] = tcarry;
-        *lp.num_tiles = tcarry;
-        lp.tile_first[tcarry] = lp.ptot;
+        uint32_t acc = 0;
+        for (uint32_t i = 0; i < nw; ++i) {
+            const uint32_t x = wt[i];
+            wt[i] = acc;
+            acc += x;
+        }
+        *lp.num_tiles = acc;
+        lp.tile_first[acc] = lp.ptot;
     }
     __syncthreads();
-    // first chunk of every tile (as k_tiles)
-    for (uint32_t g = threadIdx.x; g < lp.ptot; g += kPlanThreads) {
-        const uint32_t grp = test_at(lp, lp.chunk_test[g]).group;
-        const DevGroup gr = group_at(lp, grp);
-        const uint32_t eff = lp.tile_eff[grp];
-        const uint32_t b0 = lp.off[gr.first_chunk];
-        const uint32_t lt = (lp.off[g] - b0) / eff;
-        if (g == gr.first_chunk || (lp.off[g - 1] - b0) / eff != lt)
-            lp.tile_first[lp.tile_base[grp] + lt] = g;
-    }
+    pack_window(pw, w0, w1, spread, lp.tile_first + wt[w]);
 }
 
 // ------------------------------------------------------------ matching
@@ -1011,6 +1050,9 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
         if (cudaFuncSetAttribute(k_lookahead, cudaFuncAttributeMaxDynamicSharedMemorySize, la_max) !=
             cudaSuccess)
             return DFA_ECUDA;
+        if (cudaFuncSetAttribute(k_plan_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmallPlanSmem) != cudaSuccess)
+            return DFA_ECUDA;
         g_dev = dev;
     }
     if (kmax > 8) return grid_for<16, 2>(smem, grid);
@@ -1035,14 +1077,18 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
         ++nk;
     }
     if (lp.ptot <= kSmallPlan) {
-        k_plan_small<<<1, kPlanThreads, 0, st>>>(lp);
-        nk -= 4;
+        k_plan_small<<<1, kPlanThreads, kSmallPlanSmem, st>>>(lp);
+        nk -= 4;  // one planning kernel instead of five
     } else {
+        const uint32_t nwin = (lp.ptot + kPackWin - 1) / kPackWin;
+        const uint32_t pblocks = (nwin + kPackWarps - 1) / kPackWarps;
         k_count<<<nb, kPlanThreads, 0, st>>>(lp);
         k_scan_blocks<<<1, kPlanThreads, 0, st>>>(lp);
         k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
-        k_group_tiles<<<1, kPlanThreads, 0, st>>>(lp);
-        k_tiles<<<nb, kPlanThreads, 0, st>>>(lp);
+        k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 0);
+        k_scan_windows<<<1, kPlanThreads, 0, st>>>(lp, nwin);
+        k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 1);
+        ++nk;
     }
     if (plan_only) {
         if (kernels) *kernels = nk - 1;
