@@ -375,6 +375,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-mix", action="store_true", help="skip the batched and serving legs")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--tuning", default="",
+                    help="K,tiles_per_cta,ctas_per_sm instead of the autotuner (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -413,7 +415,11 @@ def main():
     n = len(w.data)
     dev = torch.from_numpy(w.data).cuda()
     tuning = None
-    if not w.num_chunks and not args.no_tune:
+    if args.tuning:
+        k, tpc, cps = (int(x) for x in args.tuning.split(","))
+        d.set_tuning(states_per_thread=k, tiles_per_cta=tpc, ctas_per_sm=cps)
+        tuning = {"states_per_thread": k, "tiles_per_cta": tpc, "ctas_per_sm": cps, "fixed": True}
+    elif not w.num_chunks and not args.no_tune:
         t, _ = d.autotune(dev)          # the library's per-DFA tuner, before any timing
         tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
                   "ctas_per_sm": t.ctas_per_sm}

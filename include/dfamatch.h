@@ -84,6 +84,11 @@ typedef struct {
     uint32_t batch_chunk_bytes; /* batched and served tests: chunk length (default 8192) */
     uint32_t ctas_per_sm;       /* single tests: match-kernel CTAs per SM to aim for
                                    (0 = 3 when K <= 4, else 2)                          */
+    uint32_t host_segment_bytes; /* dfa_match on a host buffer: length of the first
+                                   segment of the copy/match pipeline (later segments
+                                   double); 0 = automatic (len/8 clamped to
+                                   [16 MiB, 256 MiB]), 0xFFFFFFFF = copy the whole
+                                   string before matching                              */
 } dfa_tuning_t;
 
 /* Optional per-call planning overrides; pass NULL for the defaults. */
@@ -175,12 +180,20 @@ int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t *starts);
 
 /*
  * Synchronous membership test.  str may be a host or a device pointer
- * (detected with cudaPointerGetAttributes); host input is copied to the
- * device first (asynchronously when the host buffer is pinned).  Runs on the
- * legacy default stream; its device staging buffer and workspace are kept
- * per device between calls (grown on demand, calls are serialised by a
- * lock).  *out is a host struct.  Errors: DFA_EINVAL, DFA_ESYMBOL (also
- * in out->status), DFA_ENOMEM, DFA_ECUDA, DFA_EHOSTONLY.
+ * (detected with cudaPointerGetAttributes).  Host input of at least two
+ * first-segment lengths (dfa_tuning_t.host_segment_bytes) is copied and
+ * matched as a pipeline when opts sets neither num_chunks nor multiplicity:
+ * segment i+1 is copied on a library-owned copy stream while segment i is
+ * matched on a library-owned compute stream, each segment as its own launch
+ * whose Eq. (8) merge starts from the previous segment's final state (and
+ * whose first chunk takes its reverse lookahead from the previous segment's
+ * last bytes), so the answer equals the unsegmented one.  Shorter or
+ * explicitly partitioned host input is copied whole first.  The copies
+ * overlap only when the host buffer is pinned.  Device staging buffer,
+ * workspace and streams are kept per device between calls (grown on demand;
+ * calls are serialised by a lock).  *out is a host struct.  Errors:
+ * DFA_EINVAL, DFA_ESYMBOL (also in out->status), DFA_ENOMEM, DFA_ECUDA,
+ * DFA_EHOSTONLY.
  */
 int dfa_match(const dfa_t *dfa, const uint8_t *str, uint64_t len, const dfa_match_opts_t *opts,
               dfa_result_t *out);

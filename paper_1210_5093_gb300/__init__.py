@@ -48,7 +48,7 @@ class Info(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("states_per_thread", ctypes.c_uint32), ("tiles_per_cta", ctypes.c_uint32),
                 ("min_chunk_bytes", ctypes.c_uint32), ("batch_chunk_bytes", ctypes.c_uint32),
-                ("ctas_per_sm", ctypes.c_uint32)]
+                ("ctas_per_sm", ctypes.c_uint32), ("host_segment_bytes", ctypes.c_uint32)]
 
 
 class MatchOpts(ctypes.Structure):
@@ -219,8 +219,12 @@ class Dfa:
         return t
 
     def set_tuning(self, states_per_thread: int = 0, tiles_per_cta: int = 0,
-                   min_chunk_bytes: int = 0, batch_chunk_bytes: int = 0, ctas_per_sm: int = 0):
-        t = Tuning(states_per_thread, tiles_per_cta, min_chunk_bytes, batch_chunk_bytes, ctas_per_sm)
+                   min_chunk_bytes: int = 0, batch_chunk_bytes: int = 0, ctas_per_sm: int = 0,
+                   host_segment_bytes: int = 0):
+        """host_segment_bytes: first segment of dfa_match's copy/match pipeline for
+        host input (0 = automatic, 0xFFFFFFFF = copy the whole string first)."""
+        t = Tuning(states_per_thread, tiles_per_cta, min_chunk_bytes, batch_chunk_bytes, ctas_per_sm,
+                   host_segment_bytes)
         _check(lib().dfa_set_tuning(self._h, ctypes.byref(t)), "dfa_set_tuning")
 
     def autotune(self, dev_sample, stream=None):

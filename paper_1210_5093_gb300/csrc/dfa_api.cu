@@ -687,8 +687,47 @@ struct SyncBuffers {
     uint64_t str_cap = 0;
     uint8_t* ws = nullptr;
     uint64_t ws_cap = 0;
+    cudaStream_t ks = nullptr;  // compute stream of the host pipeline
+    cudaStream_t cs = nullptr;  // copy stream of the host pipeline
+    std::vector<cudaEvent_t> ev;  // one "segment copied" event per segment
 };
 static SyncBuffers g_sync[64];
+
+// Segment lengths of the pipelined host path.  The first segment is short,
+// so little copy time is exposed before the first launch; each later one
+// doubles, since the copy engine moves bytes faster than the match kernel
+// consumes them and the next copy still ends under the current match.  A
+// remainder shorter than half the next length joins the last segment.
+// Returns false when the input is too short to pipeline.
+static bool host_segments(uint64_t len, uint32_t first_bytes, std::vector<uint64_t>* seg) {
+    constexpr uint64_t kMin = 16ull << 20, kMax = 256ull << 20;
+    if (first_bytes == 0xFFFFFFFFu) return false;
+    uint64_t first = first_bytes ? first_bytes : std::min(kMax, std::max(kMin, len / 8));
+    if (first < 4096 || len < 2 * first) return false;
+    seg->clear();
+    uint64_t pos = 0, next = first;
+    while (pos < len) {
+        uint64_t take = std::min(next, len - pos);
+        if (len - pos - take < next / 2) take = len - pos;
+        seg->push_back(take);
+        pos += take;
+        next *= 2;
+    }
+    return seg->size() > 1;
+}
+
+static int pipeline_resources(SyncBuffers& B, size_t nseg) {
+    if (!B.ks && cudaStreamCreateWithFlags(&B.ks, cudaStreamNonBlocking) != cudaSuccess)
+        return DFA_ECUDA;
+    if (!B.cs && cudaStreamCreateWithFlags(&B.cs, cudaStreamNonBlocking) != cudaSuccess)
+        return DFA_ECUDA;
+    while (B.ev.size() < nseg) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DFA_ECUDA;
+        B.ev.push_back(e);
+    }
+    return DFA_OK;
+}
 
 static int grow_dev(uint8_t** p, uint64_t* cap, uint64_t need) {
     if (*cap >= need) return DFA_OK;
@@ -713,6 +752,50 @@ int dfa_plan_chunks(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, 
     return DFA_OK;
 }
 
+// Host input in segments: segment i is copied on B.cs and matched on B.ks
+// once its copy has landed; segments after the first are continuation tests
+// (kTestCont), so each launch's merge picks up the previous final state from
+// the shared result slot.  The launches reuse one workspace in stream order.
+static int match_pipelined(const dfa_t* d, const uint8_t* str, const std::vector<uint64_t>& seg,
+                           const dfa_match_opts_t* opts, SyncBuffers& B, dfa_result_t* out) {
+    const size_t ns = seg.size();
+    std::vector<Single> plan(ns);
+    uint64_t len = 0, ws_need = 0;
+    for (size_t i = 0; i < ns; ++i) {
+        int rc = plan_single(d, seg[i], opts, &plan[i]);
+        if (rc != DFA_OK) return rc;
+        len += seg[i];
+        ws_need = std::max(ws_need, plan[i].ws.total);
+    }
+    int rc = pipeline_resources(B, ns);
+    if (rc != DFA_OK) return rc;
+    if ((rc = grow_dev(&B.str, &B.str_cap, len)) != DFA_OK) return rc;
+    if ((rc = grow_dev(&B.ws, &B.ws_cap, ws_need + 256)) != DFA_OK) return rc;
+    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(B.ws + ws_need);
+    uint64_t pos = 0;
+    for (size_t i = 0; i < ns; ++i) {
+        if (cudaMemcpyAsync(B.str + pos, str + pos, seg[i], cudaMemcpyHostToDevice, B.cs) !=
+                cudaSuccess ||
+            cudaEventRecord(B.ev[i], B.cs) != cudaSuccess ||
+            cudaStreamWaitEvent(B.ks, B.ev[i], 0) != cudaSuccess)
+            return DFA_ECUDA;
+        Single& s = plan[i];
+        s.lp.test1.str = B.str + pos;
+        s.lp.test1.flags = i ? kTestCont : 0u;
+        bind(s.lp, B.ws, s.ws);
+        s.lp.results = dres;
+        rc = launch_plan(s.lp, s.kmax, s.smem, B.ks, nullptr,
+                         (opts && i == 0) ? opts->match_begin_event : nullptr,
+                         (opts && i + 1 == ns) ? opts->match_end_event : nullptr);
+        if (rc != DFA_OK) return rc;
+        pos += seg[i];
+    }
+    if (cudaMemcpyAsync(out, dres, sizeof *out, cudaMemcpyDeviceToHost, B.ks) != cudaSuccess ||
+        cudaStreamSynchronize(B.ks) != cudaSuccess)
+        return DFA_ECUDA;
+    return out->status != DFA_OK ? out->status : DFA_OK;
+}
+
 int dfa_match(const dfa_t* d, const uint8_t* str, uint64_t len, const dfa_match_opts_t* opts,
               dfa_result_t* out) {
     if (!d || !out || (len && !str)) return DFA_EINVAL;
@@ -731,6 +814,10 @@ int dfa_match(const dfa_t* d, const uint8_t* str, uint64_t len, const dfa_match_
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DFA_ECUDA;
     SyncBuffers& B = g_sync[dev];
     std::lock_guard<std::mutex> lock(B.mu);
+    std::vector<uint64_t> seg;
+    if (len && !on_dev && !(opts && (opts->num_chunks || opts->multiplicity)) &&
+        host_segments(len, d->tuning.host_segment_bytes, &seg))
+        return match_pipelined(d, str, seg, opts, B, out);
     const uint8_t* use = str;
     if (len && !on_dev) {
         if ((rc = grow_dev(&B.str, &B.str_cap, len)) != DFA_OK) return rc;

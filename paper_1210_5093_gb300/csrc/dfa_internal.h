@@ -67,9 +67,16 @@ struct DevTest {
     uint32_t group;       // run of consecutive tests sharing one DFA
     uint32_t lookahead;   // 1: Algorithm 3, 0: Algorithm 2 (all states)
     uint32_t out;         // index of its result in the caller's output array
-    uint32_t pad_;
+    uint32_t flags;       // kTestCont
 };
 static_assert(sizeof(DevTest) == 48, "DevTest layout");
+
+// A continuation test is one segment of a longer string whose earlier
+// segments were matched by earlier launches on the same stream: the bytes
+// before `str` are readable, its chunk 0 is speculative like any other chunk
+// (reverse lookahead into the previous segment), and Eq. (8) starts from the
+// final state (and status) already in its result slot instead of q0.
+constexpr uint32_t kTestCont = 1;
 
 struct DevGroup {
     uint32_t first_chunk, end_chunk, dfa, first_test;

@@ -119,6 +119,12 @@ __device__ __forceinline__ uint32_t find_test(const LaunchPlan& lp, uint32_t g) 
     return lo;
 }
 
+// Readable bytes of the string before position st of test t (unbounded for
+// a continuation segment, whose predecessor is in the same device buffer).
+__device__ __forceinline__ uint64_t bytes_before(const DevTest& t, uint64_t st) {
+    return (t.flags & kTestCont) ? (~0ull >> 1) : st;
+}
+
 constexpr int kLaWarps = 8;
 
 // r-symbol reverse lookahead (Eq. 13), one warp per chunk: with sigma_1..sigma_j
@@ -141,11 +147,12 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
     if (t.lookahead < 2) return;
     const DevDfa& d = lp.dfas[t.dfa];
     const uint64_t st = dstart(t.n, t.P, t.m, g - t.chunk_base);
-    const uint32_t j = (uint32_t)(st < t.lookahead ? st : t.lookahead);
+    const uint64_t avail = bytes_before(t, st);
+    const uint32_t j = (uint32_t)(avail < t.lookahead ? avail : t.lookahead);
     if (j < 2) return;
     const DevGroup gr = group_at(lp, t.group);
     uint16_t* out = lp.sets + gr.set_base + (uint64_t)(g - gr.first_chunk) * gr.set_stride;
-    const uint8_t* p = t.str + (st - j);
+    const uint8_t* p = t.str + ((int64_t)st - (int64_t)j);
     uint32_t c = d.byte_class[p[0]];
     if (c == kNone16) {
         if (lane == 0) { atomicOr(lp.test_err + ti, 1u); lp.set_size[g] = 0; }
@@ -220,19 +227,20 @@ __device__ uint32_t chunk_count(const LaunchPlan& lp, uint32_t g) {
     const DevDfa& d = lp.dfas[t.dfa];
     const uint32_t k = g - t.chunk_base;
     const uint64_t st = dstart(t.n, t.P, t.m, k);
+    const uint64_t avail = bytes_before(t, st);
     uint32_t cls;
-    if (st == 0) {
+    if (avail == 0) {
         cls = d.C;  // chunk 0, or a chunk preceded only by empty chunks: start set {q0}
     } else if (!t.lookahead) {
         cls = d.C + 1;  // Algorithm 2: all of Q
     } else {
-        uint32_t c = d.byte_class[t.str[st - 1]];
+        uint32_t c = d.byte_class[t.str[(int64_t)st - 1]];
         if (c == kNone16) {
             atomicOr(&lp.test_err[lo], 1u);
             c = d.C;
         }
         cls = c;
-        if (t.lookahead >= 2 && st >= 2 && c != d.C) cls = dyn_set(d.C);  // Eq. 13 set from k_lookahead
+        if (t.lookahead >= 2 && avail >= 2 && c != d.C) cls = dyn_set(d.C);  // Eq. 13 set from k_lookahead
     }
     const uint32_t size = cls == dyn_set(d.C) ? lp.set_size[g] : d.iset_off[cls + 1] - d.iset_off[cls];
     const uint32_t cnt = (size + d.K - 1) / d.K;
@@ -304,16 +312,16 @@ __device__ __forceinline__ uint32_t tile_budget(uint32_t cost_max, uint32_t spre
 // One warp packs chunks [w0, w1) from their packing words; returns its tile
 // count.  Every lane runs the same greedy pass (words are read 16 at a time
 // with independent loads, then scanned in registers); with out != nullptr,
-// lane 0 writes each tile's first chunk to out[0..].  `words` is global or
-// shared memory.
-__device__ uint32_t pack_window(const uint32_t* words, uint32_t w0, uint32_t w1, uint32_t spread,
-                                uint32_t* out) {
+// lane 0 writes each tile's first chunk to out[0..].  Chunk g's word is
+// words[g - wbase], in global or shared memory.
+__device__ uint32_t pack_window(const uint32_t* words, uint32_t wbase, uint32_t w0, uint32_t w1,
+                                uint32_t spread, uint32_t* out) {
     const uint32_t lane = threadIdx.x & 31;
     uint32_t tiles = 0, cur = 0, budget = 0;
     for (uint32_t b = w0; b < w1; b += 16) {
         uint32_t v[16];
 #pragma unroll
-        for (uint32_t i = 0; i < 16; ++i) v[i] = b + i < w1 ? words[b + i] : 0u;
+        for (uint32_t i = 0; i < 16; ++i) v[i] = b + i < w1 ? words[b + i - wbase] : 0u;
 #pragma unroll
         for (uint32_t i = 0; i < 16; ++i) {
             if (b + i >= w1) break;
@@ -335,19 +343,22 @@ __device__ uint32_t pack_window(const uint32_t* words, uint32_t w0, uint32_t w1,
 
 constexpr int kPackWarps = 8;
 
+// Each warp first copies its window's packing words into shared memory (one
+// coalesced read), so the serial greedy pass runs on shared-memory latency.
 __global__ void __launch_bounds__(kPackWarps * 32) k_pack(LaunchPlan lp, uint32_t pass) {
-    const uint32_t w = blockIdx.x * kPackWarps + (threadIdx.x >> 5);
+    __shared__ uint32_t win[kPackWarps][kPackWin];
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const uint32_t w = blockIdx.x * kPackWarps + wl;
     const uint32_t w0 = w * kPackWin;
     if (w0 >= lp.ptot) return;  // warp-uniform
     const uint32_t total = lp.bsum[lp.nblk];
     const uint32_t spread = (total + lp.grid - 1) / lp.grid;
     const uint32_t w1 = min(w0 + kPackWin, lp.ptot);
-    if (pass == 0) {
-        const uint32_t n = pack_window(lp.cost, w0, w1, spread, nullptr);
-        if ((threadIdx.x & 31) == 0) lp.wtiles[w] = n;
-    } else {
-        pack_window(lp.cost, w0, w1, spread, lp.tile_first + lp.wtiles[w]);
-    }
+    for (uint32_t i = lane; i < w1 - w0; i += 32) win[wl][i] = lp.cost[w0 + i];
+    __syncwarp();
+    uint32_t* out = pass == 0 ? nullptr : lp.tile_first + lp.wtiles[w];
+    const uint32_t n = pack_window(win[wl], w0, w0, w1, spread, out);
+    if (pass == 0 && lane == 0) lp.wtiles[w] = n;
 }
 
 // Exclusive scan of the per-window tile counts (one CTA); the total is the
@@ -400,7 +411,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp) {
     const uint32_t win = ((lp.ptot + nw - 1) / nw + 15u) & ~15u;
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t w0 = min(w * win, lp.ptot), w1 = min(w0 + win, lp.ptot);
-    const uint32_t n = pack_window(pw, w0, w1, spread, nullptr);
+    const uint32_t n = pack_window(pw, 0, w0, w1, spread, nullptr);
     if ((threadIdx.x & 31) == 0) wt[w] = n;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -414,7 +425,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp) {
         lp.tile_first[acc] = lp.ptot;
     }
     __syncthreads();
-    pack_window(pw, w0, w1, spread, lp.tile_first + wt[w]);
+    pack_window(pw, 0, w0, w1, spread, lp.tile_first + wt[w]);
 }
 
 // ------------------------------------------------------------ matching
@@ -727,7 +738,10 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
     const uint32_t words = (qe + 1) / 2;  // u32 words per map
     const uint32_t per = buf_bytes / (4 * words);
     uint32_t* sm = reinterpret_cast<uint32_t*>(buf);
-    if (threadIdx.x == 0) *cell = d.q0;
+    // a continuation segment starts from the previous segment's final state;
+    // that launch ran earlier on the same stream, so its result is complete
+    const bool cont = (tt.flags & kTestCont) != 0;
+    if (threadIdx.x == 0) *cell = cont ? lp.results[tt.out].final_state : d.q0;
     for (uint32_t i0 = 0; i0 < nseg; i0 += per) {
         const uint32_t nb = min(per, nseg - i0);
         __syncthreads();
@@ -749,7 +763,7 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
     if (threadIdx.x == 0) {
         const uint32_t s = *cell;
         dfa_result_t r;
-        const uint32_t err = atomicOr(lp.test_err + t, 0u);
+        const uint32_t err = atomicOr(lp.test_err + t, 0u) | (cont && lp.results[tt.out].status != DFA_OK);
         r.final_state = err ? 0u : s;
         r.accept = err ? 0 : d.accept[s];
         r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
@@ -800,7 +814,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
     auto end_segment = [&]() {
         const DevTest tt = test_at(lp, (uint32_t)cur_test);
         const DevDfa& td = lp.dfas[tt.dfa];
-        const bool covered = tt.chunk_base >= c_lo && tt.chunk_base + tt.P <= c_hi;
+        const bool covered = tt.chunk_base >= c_lo && tt.chunk_base + tt.P <= c_hi &&
+                             !(tt.flags & kTestCont);
         if (covered) {
             // the segment is the whole test, started at chunk 0 from {q0}: V[0] is the answer
             if (tid == 0) {
@@ -905,7 +920,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             m.toff = (uint16_t)(lp.off[g] - off0);
             m.cls = (uint16_t)cls;
             m.cnt = (uint16_t)((size + d.K - 1) / d.K);
-            m.lo_slack = (uint8_t)(st < 255 ? st : 255);
+            const uint64_t avail = bytes_before(tt, st);
+            m.lo_slack = (uint8_t)(avail < 255 ? avail : 255);
             m.hi_slack = (uint8_t)(tt.n - en < 255 ? tt.n - en : 255);
             meta[i] = m;
             atomicMax(misc + M_MAXLEN, m.len);
