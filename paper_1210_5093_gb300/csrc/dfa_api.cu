@@ -18,6 +18,7 @@ uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint
                           uint32_t target);
 uint32_t match_target_ctas(uint32_t kmax, uint32_t want);
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
+uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn);
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
                 uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr,
                 bool plan_only = false);
@@ -42,11 +43,15 @@ WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t pt
     w.chunk_cls = take(2ull * ptot);
     w.cost = take(4ull * ptot);
     w.off = take(4ull * (ptot + 1));
+    w.wk = take(8ull * (ptot + 1));
     w.bsum = take(4ull * (nblk + 1));
+    w.bsumw = take(8ull * (nblk + 1));
     w.tile_first = take(4ull * (ptot + 1));
-    w.wtiles = take(4ull * ((ptot + 511) / 512 + 1));
+    w.ccta = take(4ull * ptot);
+    w.share = take(4ull * (grid + 1));
+    w.ntiles = take(4ull * (grid + 1));
     w.num_tiles = take(4);
-    w.test_err = take(8ull * ntests);  // test_err[ntests] then arrived[ntests]
+    w.test_err = take(8ull * ntests + 8ull * grid);  // test_err, arrived, cta_range
     w.first_cta = take(4ull * ntests);
     w.last_cta = take(4ull * ntests);
     w.seg_hdr = take(16ull * (grid + ntests));
@@ -62,12 +67,17 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
     lp.chunk_cls = reinterpret_cast<uint16_t*>(base + w.chunk_cls);
     lp.cost = reinterpret_cast<uint32_t*>(base + w.cost);
     lp.off = reinterpret_cast<uint32_t*>(base + w.off);
+    lp.wk = reinterpret_cast<uint64_t*>(base + w.wk);
     lp.bsum = reinterpret_cast<uint32_t*>(base + w.bsum);
+    lp.bsumw = reinterpret_cast<uint64_t*>(base + w.bsumw);
     lp.tile_first = reinterpret_cast<uint32_t*>(base + w.tile_first);
-    lp.wtiles = reinterpret_cast<uint32_t*>(base + w.wtiles);
+    lp.ccta = reinterpret_cast<uint32_t*>(base + w.ccta);
+    lp.share = reinterpret_cast<uint32_t*>(base + w.share);
+    lp.ntiles = reinterpret_cast<uint32_t*>(base + w.ntiles);
     lp.num_tiles = reinterpret_cast<uint32_t*>(base + w.num_tiles);
     lp.test_err = reinterpret_cast<uint32_t*>(base + w.test_err);
     lp.arrived = lp.test_err + lp.ntests;
+    lp.cta_range = lp.arrived + lp.ntests;
     lp.first_cta = reinterpret_cast<uint32_t*>(base + w.first_cta);
     lp.last_cta = reinterpret_cast<uint32_t*>(base + w.last_cta);
     lp.seg_hdr = reinterpret_cast<uint32_t*>(base + w.seg_hdr);
@@ -168,6 +178,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         t.dfa = idx[d];
         t.P = plan_chunks(d, lens[i], p.grid, opts, batched);
         t.m = m;
+        t.qinv = recip64((uint64_t)m + t.P - 1);
         t.chunk_base = (uint32_t)chunks;
         t.lookahead = lookahead;
         t.out = i;
@@ -298,6 +309,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.test1.dfa = 0;
     lp.test1.P = P;
     lp.test1.m = m;
+    lp.test1.qinv = recip64((uint64_t)m + P - 1);
     lp.test1.chunk_base = 0;
     lp.test1.group = 0;
     lp.test1.lookahead = lookahead;
@@ -349,6 +361,13 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
     x.imax = h.imax;
     x.K = h.K;
     x.stage_fmt = h.placement == kGlobal ? kOff32 : (h.C + 1 <= 255 ? kCls8 : kOff16);
+    x.n_all = h.iset_off[h.C + 2] - h.iset_off[h.C + 1];
+    // planning lookup: one load gives a lookahead byte's class and |I_class|
+    uint32_t byte_plan[256];
+    for (int b = 0; b < 256; ++b) {
+        const uint32_t c = h.byte_class[b];
+        byte_plan[b] = c == kNone16 ? kNone32 : (c << 16) | (h.iset_off[c + 1] - h.iset_off[c]);
+    }
     if (device) {
         if (cudaGetDevice(&d->device) != cudaSuccess) {
             delete d;
@@ -361,7 +380,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         const uint64_t o_b16 = take(512), o_b32 = take(1024), o_bc = take(512);
         const uint64_t o_ioff = take(4 * h.iset_off.size()), o_iset = take(2 * h.iset.size());
         const uint64_t o_pos = take(2 * h.pos.size()), o_acc = take(h.accept.size());
-        const uint64_t o_exc = take(h.excluded.size());
+        const uint64_t o_exc = take(h.excluded.size()), o_bp = take(sizeof byte_plan);
         uint8_t* blk = nullptr;
         if (cudaMalloc(&blk, o) != cudaSuccess) {
             cudaGetLastError();
@@ -379,6 +398,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         x.pos = reinterpret_cast<const uint16_t*>(blk + o_pos);
         x.accept = blk + o_acc;
         x.excluded = blk + o_exc;
+        x.byte_plan = reinterpret_cast<const uint32_t*>(blk + o_bp);
         d->dev_desc = reinterpret_cast<DevDfa*>(blk + o_desc);
         DevDfa descs[2] = {launch_desc(d, 1), launch_desc(d, 0)};
         bool ok = cudaMemcpy(blk + o_desc, descs, sizeof descs, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -390,7 +410,8 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
                   cudaMemcpy(blk + o_iset, h.iset.data(), 2 * h.iset.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_pos, h.pos.data(), 2 * h.pos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_acc, h.accept.data(), h.accept.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(blk + o_exc, h.excluded.data(), h.excluded.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+                  cudaMemcpy(blk + o_exc, h.excluded.data(), h.excluded.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_bp, byte_plan, sizeof byte_plan, cudaMemcpyHostToDevice) == cudaSuccess;
         if (!ok) {
             cudaFree(blk);
             delete d;
@@ -616,7 +637,7 @@ int dfa_match_num_kernels(const dfa_t* d, uint64_t len, const dfa_match_opts_t* 
     Single s;
     int rc = plan_single(d, len, opts, &s);
     if (rc != DFA_OK) return rc;
-    *n = (s.lp.ptot <= 16384 ? 2u : 7u) + (s.lp.dyn ? 1u : 0u);
+    *n = launch_kernel_count(s.lp.ptot, s.lp.grid, s.lp.dyn != 0);
     return DFA_OK;
 }
 
@@ -934,7 +955,7 @@ int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) 
 
 int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
     if (!b || !n) return DFA_EINVAL;
-    *n = (b->p.ptot <= 16384 ? 2u : 7u) + (b->p.dyn ? 1u : 0u);
+    *n = launch_kernel_count(b->p.ptot, b->p.grid, b->p.dyn != 0);
     return DFA_OK;
 }
 

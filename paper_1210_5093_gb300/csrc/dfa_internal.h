@@ -36,6 +36,7 @@ struct DevDfa {
     const uint16_t* pos;         // [(C+2)*qe] index of state s in set c, kNone16 if absent
     const uint8_t* accept;       // [qe] 1 iff accepting
     const uint8_t* excluded;     // [qe] 1 iff left out of every initial-state set
+    const uint32_t* byte_plan;   // [256] (class << 16) | |I_class|; kNone32 for bytes outside Sigma
     uint32_t qe;                 // states incl. q_e
     uint32_t qpad;               // row stride (entries)
     uint32_t C;                  // classes (without the start set)
@@ -48,6 +49,8 @@ struct DevDfa {
     uint32_t cost_max;           // max thread slots one chunk can need: max(ceil(|I|/K), 2)
     uint32_t vcap;               // largest set size (incl. start set) = capacity of a state map
     uint32_t stage_fmt;          // StageFmt of the staged input stream
+    uint32_t n_all;              // |Q| minus the excluded states: the set Algorithm 2 matches
+    uint32_t pad_;
 };
 
 // How a chunk's input is staged in shared memory: 8-bit class indices
@@ -60,6 +63,7 @@ enum StageFmt : uint32_t { kCls8 = 0, kOff16 = 1, kOff32 = 2 };
 struct DevTest {
     const uint8_t* str;
     uint64_t n;
+    uint64_t qinv;        // floor((2^64 - 1) / (m + P - 1)): Eq. (6)'s divisor, inverted once
     uint32_t dfa;         // index into the launch's DevDfa array
     uint32_t P;           // chunks
     uint32_t m;           // multiplicity of Eq. (10) used in the partition
@@ -68,8 +72,13 @@ struct DevTest {
     uint32_t lookahead;   // 1: Algorithm 3, 0: Algorithm 2 (all states)
     uint32_t out;         // index of its result in the caller's output array
     uint32_t flags;       // kTestCont
+    uint64_t pad_;
 };
-static_assert(sizeof(DevTest) == 48, "DevTest layout");
+static_assert(sizeof(DevTest) == 64, "DevTest layout");
+
+// floor((2^64 - 1) / q) for q >= 1: the reciprocal the device uses to divide
+// by q with one 64-bit multiply-high and at most two corrections.
+inline uint64_t recip64(uint64_t q) { return ~0ull / q; }
 
 // A continuation test is one segment of a longer string whose earlier
 // segments were matched by earlier launches on the same stream: the bytes
@@ -109,14 +118,20 @@ struct LaunchPlan {
     uint32_t stage_bytes;       // bytes of one of the two stage buffers
     uint32_t* chunk_test;       // [ptot]
     uint16_t* chunk_cls;        // [ptot]
-    uint32_t* cost;             // [ptot] packing word: thread slots, DFA cost_max, group start
+    uint32_t* cost;             // [ptot] packing word (thread slots, opens-a-tile flag);
+                                // then scratch for the tile starts of each packing window
     uint32_t* off;              // [ptot+1] exclusive prefix of cost (within the launch)
+    uint64_t* wk;               // [ptot+1] scratch: chunk work (slots x length) or its midpoint
     uint32_t* bsum;             // [nblk+1]
+    uint64_t* bsumw;            // [nblk+1] block sums of wk
     uint32_t* tile_first;       // [ptot+1]
-    uint32_t* wtiles;           // [nwin+1] tiles per packing window, then their bases
+    uint32_t* ccta;             // [ptot] CTA share of each chunk
+    uint32_t* share;            // [grid+1] first chunk of each CTA share
+    uint32_t* ntiles;           // [grid+1] tiles per share, then their bases
     uint32_t* num_tiles;        // [1]
     uint32_t* test_err;         // [ntests]
     uint32_t* arrived;          // [ntests]
+    uint32_t* cta_range;        // [2*grid] tiles [first, end) of each CTA (cleared: empty)
     uint32_t* first_cta;        // [ntests]
     uint32_t* last_cta;         // [ntests]
     uint32_t* seg_hdr;          // [(grid+ntests)*4]: first chunk, nchunks, -, -
@@ -134,8 +149,8 @@ struct LaunchPlan {
 
 // Workspace carve-up of one launch (byte offsets into the device workspace).
 struct WsLayout {
-    uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, bsum, tile_first, wtiles,
-        num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
+    uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, wk, bsum, bsumw, tile_first,
+        ccta, share, ntiles, num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
 };
 
 // A batch planned on the host: descriptors, sizes and the workspace layout.

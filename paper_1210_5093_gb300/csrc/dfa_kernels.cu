@@ -1,12 +1,14 @@
 // Device side of the speculative chunked DFA membership test (sm_103a).
 //
 // A launch covers `ntests` independent membership tests.  Work flows through
-// five planning kernels and one persistent match kernel, all on one stream:
+// seven planning kernels (or k_plan_small, all of them in one CTA, for small
+// launches) and one persistent match kernel, all on one stream:
 //
-//   k_count        per chunk: test, reverse-lookahead class, thread slots  (Alg. 3 l.16, Eq. 11)
-//   k_scan_blocks  exclusive scan of the per-block slot sums
-//   k_offsets      per-chunk slot offsets
-//   k_pack (x2), k_scan_windows   greedy packing of chunks into tiles
+//   k_count        per chunk: test, reverse-lookahead class, thread slots, work  (Alg. 3 l.16, Eq. 11)
+//   k_scan_blocks  exclusive scans of the per-block sums
+//   k_offsets      per-chunk slot offsets and CTA shares of the work
+//   k_shares       share boundaries
+//   k_pack (x2), k_scan_shares   greedy packing of each share into tiles
 //   k_match        persistent: stage chunks, advance every (chunk, state) chain,
 //                  compose the chunk maps, combine per test             (Alg. 3 l.8-20, Eqs. 8-9)
 //
@@ -14,10 +16,10 @@
 // initial-state set I_k (the image of its reverse-lookahead symbol's class).
 // Each thread advances K of those chains together (one "lane task" per
 // (chunk, state) pair, K per thread so the class stream is read once for K
-// lookups).  A tile is a run of consecutive chunks whose threads fit one CTA;
-// each CTA owns a contiguous range of tiles and composes the maps of its
-// chunks in order (Eq. 9) into one running map per test; tests that span
-// several CTAs are finished by the CTA that completes last.
+// lookups).  Each CTA owns an equal share of the launch's work (a contiguous
+// run of chunks), packed into tiles whose threads fit the CTA; it composes
+// the maps of its chunks in order (Eq. 9) into one running map per test;
+// tests that span several CTAs are finished by the CTA that completes last.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -62,38 +64,54 @@ __device__ __forceinline__ uint32_t ldg_u16(const uint8_t* p) {
     return v;
 }
 
-// Eq. (6) with unit weights and m states per later chunk (see chunk_start on the host).
-__device__ __forceinline__ uint64_t dstart(uint64_t n, uint32_t P, uint32_t m, uint32_t k) {
-    if (k == 0) return 0;
-    if (k >= P) return n;
-    unsigned __int128 num = (unsigned __int128)n * (uint64_t)(m + k - 1);
-    return (uint64_t)(num / (uint64_t)(m + P - 1));
+// floor(x / q) given qinv = floor((2^64 - 1) / q): the multiply-high estimate
+// is at most 2 below the quotient (division by an invariant integer).
+__device__ __forceinline__ uint64_t div_by_recip(uint64_t x, uint64_t q, uint64_t qinv) {
+    uint64_t s = __umul64hi(x, qinv);
+    uint64_t r = x - s * q;
+    if (r >= q) {
+        ++s;
+        r -= q;
+    }
+    if (r >= q) ++s;
+    return s;
 }
 
-template <int NTH>
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp, uint32_t* total) {
-    // tmp: NTH/32 + 1 words of shared memory
+// Eq. (6) with unit weights and m states per later chunk (see chunk_start on
+// the host): Start(k) = floor(n (m + k - 1) / (m + P - 1)), exact.
+__device__ __forceinline__ uint64_t dstart(const DevTest& t, uint32_t k) {
+    if (k == 0) return 0;
+    if (k >= t.P) return t.n;
+    const uint64_t a = (uint64_t)t.m + k - 1, q = (uint64_t)t.m + t.P - 1;
+    if (__umul64hi(t.n, a) == 0) return div_by_recip(t.n * a, q, t.qinv);
+    const unsigned __int128 num = (unsigned __int128)t.n * a;
+    return (uint64_t)(num / q);
+}
+
+template <int NTH, typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* tmp, T* total) {
+    // tmp: NTH/32 + 1 entries of shared memory
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) tmp[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < NTH / 32 ? tmp[lane] : 0, z = w;
+        T w = lane < NTH / 32 ? tmp[lane] : 0, z = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            T y = __shfl_up_sync(0xffffffffu, z, o);
             if (lane >= o) z += y;
         }
         if (lane < NTH / 32) tmp[lane] = z - w;
         if (lane == NTH / 32 - 1) tmp[NTH / 32] = z;
     }
     __syncthreads();
-    uint32_t r = tmp[warp] + x - v;
+    T r = tmp[warp] + x - v;
     if (total) *total = tmp[NTH / 32];
     __syncthreads();
     return r;
@@ -146,7 +164,7 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
     const DevTest t = test_at(lp, ti);
     if (t.lookahead < 2) return;
     const DevDfa& d = lp.dfas[t.dfa];
-    const uint64_t st = dstart(t.n, t.P, t.m, g - t.chunk_base);
+    const uint64_t st = dstart(t, g - t.chunk_base);
     const uint64_t avail = bytes_before(t, st);
     const uint32_t j = (uint32_t)(avail < t.lookahead ? avail : t.lookahead);
     if (j < 2) return;
@@ -210,168 +228,303 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
     if (lane == 0) lp.set_size[g] = n;
 }
 
-// Per-chunk packing word: thread slots (bits 0-9), the cost_max of the
-// chunk's DFA (bits 10-19) and a group-start flag (bit 20).  Both costs are
-// at most kThreads / 2 (the compiler keeps ceil(|I| / K) <= 256).
-__device__ __forceinline__ uint32_t pack_word(uint32_t cost, uint32_t cost_max, bool fresh) {
-    return cost | (cost_max << 10) | ((uint32_t)fresh << 20);
-}
+// Per-chunk packing word: thread slots (bits 0-9; at most kThreads / 2, as
+// the compiler keeps ceil(|I| / K) <= 256) and kOpensTile, set when the chunk
+// starts a new DFA group or the share of a new CTA.
+constexpr uint32_t kOpensTile = 1u << 20;
 __device__ __forceinline__ uint32_t word_cost(uint32_t w) { return w & 0x3FFu; }
+
+// CTA shares.  The launch's work W (lane-steps: thread slots x chunk length,
+// summed over its chunks) is cut into G equal shares, one per CTA of the
+// match kernel; chunk g goes to the share holding its midpoint.  With mid2 =
+// twice that midpoint (2 x work before g + work of g) the share is
+// floor(mid2 * G / (2 W)), so every CTA gets W / G +- one chunk; when W / G is
+// below the heaviest chunk's work some CTAs get no chunk.
+__device__ __forceinline__ uint32_t cta_of_mid2(uint64_t mid2, uint64_t W, uint32_t G,
+                                                uint64_t winv) {
+    if (W == 0) return 0;
+    uint64_t c;
+    if (W < (1ull << 50) && G <= 4096)  // mid2 <= 2W, so mid2 * G < 2^63: 64-bit is exact
+        c = div_by_recip(mid2 * G, 2 * W, winv);
+    else
+        c = (uint64_t)((unsigned __int128)mid2 * G / ((unsigned __int128)W * 2));
+    return (uint32_t)(c < G ? c : G - 1);
+}
+
+// The reciprocal cta_of_mid2 takes (one real division per thread).
+__device__ __forceinline__ uint64_t share_recip(uint64_t W) { return W ? ~0ull / (2 * W) : 0; }
 
 // Per chunk g: owning test, reverse-lookahead class (Algorithm 3 line 16)
 // and the thread slots it is charged: ceil(|I_k| / K), at least 2.  Writes
-// chunk_test, chunk_cls and cost; returns the cost.
-__device__ uint32_t chunk_count(const LaunchPlan& lp, uint32_t g) {
-    const uint32_t lo = find_test(lp, g);
-    const DevTest t = test_at(lp, lo);
-    const DevDfa& d = lp.dfas[t.dfa];
-    const uint32_t k = g - t.chunk_base;
-    const uint64_t st = dstart(t.n, t.P, t.m, k);
-    const uint64_t avail = bytes_before(t, st);
-    uint32_t cls;
-    if (avail == 0) {
-        cls = d.C;  // chunk 0, or a chunk preceded only by empty chunks: start set {q0}
-    } else if (!t.lookahead) {
-        cls = d.C + 1;  // Algorithm 2: all of Q
-    } else {
-        uint32_t c = d.byte_class[t.str[(int64_t)st - 1]];
-        if (c == kNone16) {
-            atomicOr(&lp.test_err[lo], 1u);
-            c = d.C;
-        }
-        cls = c;
-        if (t.lookahead >= 2 && avail >= 2 && c != d.C) cls = dyn_set(d.C);  // Eq. 13 set from k_lookahead
+// chunk_test, chunk_cls and the packing word; returns in cost[i] and work[i]
+// the slots and cost x chunk length (the lane-steps the chunk occupies, used
+// to give every CTA an equal share) of chunks g0 .. g0+N-1 (those below
+// ptot).  The N chunks go through each step together so their dependent
+// global loads (lookahead byte, class, set size) overlap.
+template <int N>
+__device__ __forceinline__ void chunk_count_n(const LaunchPlan& lp, uint32_t g0, uint32_t* cost,
+                                              uint64_t* work) {
+    constexpr uint32_t kNoByte = 0x100;
+    uint32_t lo[N], b[N], C[N], K[N], dyn[N];
+    uint64_t st[N], en[N];
+    const uint32_t* bp[N];
+    // Two dependent load levels per chunk, issued for all N chunks together:
+    // (1) the byte before the chunk, the DFA's fields and the Eq. 13 set size;
+    // (2) that byte's class and |I_class| from the DFA's byte_plan.
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const uint32_t g = g0 + i;
+        const bool ok = g < lp.ptot;
+        lo[i] = ok ? find_test(lp, g) : 0;
+        const DevTest t = test_at(lp, lo[i]);
+        const DevDfa* d = lp.dfas + t.dfa;
+        C[i] = __ldg(&d->C);
+        K[i] = __ldg(&d->K);
+        bp[i] = (const uint32_t*)__ldg((const unsigned long long*)&d->byte_plan);
+        const uint32_t k = g - t.chunk_base;
+        st[i] = ok ? dstart(t, k) : 0;
+        en[i] = ok ? dstart(t, k + 1) : 0;
+        const uint64_t avail = bytes_before(t, st[i]);
+        b[i] = (ok && avail && t.lookahead) ? (uint32_t)__ldg(t.str + ((int64_t)st[i] - 1)) : kNoByte;
+        // Eq. 13 sets (r >= 2) were sized by k_lookahead
+        dyn[i] = (ok && avail >= 2 && t.lookahead >= 2) ? lp.set_size[g] + 1 : 0;
+        if (!ok) b[i] = kNoByte;
+        if (ok && avail == 0) C[i] |= 0x80000000u;  // chunk 0 (or after empty chunks): start set
+        if (ok && !t.lookahead) K[i] |= 0x80000000u;  // Algorithm 2
     }
-    const uint32_t size = cls == dyn_set(d.C) ? lp.set_size[g] : d.iset_off[cls + 1] - d.iset_off[cls];
-    const uint32_t cnt = (size + d.K - 1) / d.K;
-    const uint32_t cost = cnt < 2 ? 2 : cnt;
-    // a chunk opens a new DFA group when it is the first chunk of the launch,
-    // or the first of a test whose group differs from the previous chunk's
-    bool fresh = g == 0;
-    if (!fresh && k == 0) fresh = test_at(lp, find_test(lp, g - 1)).group != t.group;
-    lp.chunk_test[g] = lo;
-    lp.chunk_cls[g] = (uint16_t)cls;
-    lp.cost[g] = pack_word(cost, d.cost_max, fresh);
-    return cost;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const uint32_t g = g0 + i;
+        if (g >= lp.ptot) {
+            cost[i] = 0;
+            work[i] = 0;
+            continue;
+        }
+        const uint32_t Ci = C[i] & 0x7FFFFFFFu, Ki = K[i] & 0x7FFFFFFFu;
+        uint32_t cls, size;
+        if (C[i] & 0x80000000u) {
+            cls = Ci;  // start set {q0}
+            size = 1;
+        } else if (K[i] & 0x80000000u) {
+            cls = Ci + 1;  // all of Q
+            size = __ldg(&lp.dfas[test_at(lp, lo[i]).dfa].n_all);
+        } else {
+            const uint32_t v = __ldg(bp[i] + b[i]);
+            if (v == kNone32) {  // a byte outside Sigma: the test fails, the chunk runs from {q0}
+                atomicOr(&lp.test_err[lo[i]], 1u);
+                cls = Ci;
+                size = 1;
+            } else if (dyn[i]) {
+                cls = dyn_set(Ci);
+                size = dyn[i] - 1;
+            } else {
+                cls = v >> 16;
+                size = v & 0xFFFFu;
+            }
+        }
+        const uint32_t cnt = (size + Ki - 1) / Ki;
+        cost[i] = cnt < 2 ? 2 : cnt;
+        const DevTest t = test_at(lp, lo[i]);
+        // a chunk opens a new DFA group when it is the first chunk of the launch,
+        // or the first of a test whose group differs from the previous chunk's
+        bool fresh = g == 0;
+        if (!fresh && g == t.chunk_base) fresh = test_at(lp, find_test(lp, g - 1)).group != t.group;
+        lp.chunk_test[g] = lo[i];
+        lp.chunk_cls[g] = (uint16_t)cls;
+        lp.cost[g] = cost[i] | (fresh ? kOpensTile : 0u);
+        work[i] = (uint64_t)cost[i] * (en[i] - st[i]);
+    }
 }
 
+// Per-chunk counts, scanned within each block of 1024 chunks: off[g] gets the
+// block-local exclusive prefix of thread slots and wk[g] twice the
+// block-local midpoint of the chunk's work; bsum/bsumw get the block totals.
 __global__ void __launch_bounds__(kPlanThreads) k_count(LaunchPlan lp) {
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    __shared__ uint64_t tmpw[kPlanThreads / 32 + 1];
     const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
-    const uint32_t cost = g < lp.ptot ? chunk_count(lp, g) : 0;
+    uint32_t cost;
+    uint64_t work;
+    chunk_count_n<1>(lp, g, &cost, &work);
     uint32_t total;
-    block_excl_scan<kPlanThreads>(cost, tmp, &total);
-    if (threadIdx.x == 0) lp.bsum[blockIdx.x] = total;
+    uint64_t totalw;
+    const uint32_t ex = block_excl_scan<kPlanThreads>(cost, tmp, &total);
+    const uint64_t exw = block_excl_scan<kPlanThreads>(work, tmpw, &totalw);
+    if (g < lp.ptot) {
+        lp.off[g] = ex;
+        lp.wk[g] = 2 * exw + work;
+    }
+    if (threadIdx.x == 0) {
+        lp.bsum[blockIdx.x] = total;
+        lp.bsumw[blockIdx.x] = totalw;
+    }
 }
 
-// Exclusive scan of the block sums (one CTA).  bsum[nblk] = total.
+// Exclusive scans of the block sums (one CTA).  bsum[nblk] and bsumw[nblk]
+// receive the totals.
 __global__ void __launch_bounds__(kPlanThreads) k_scan_blocks(LaunchPlan lp) {
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    __shared__ uint64_t tmpw[kPlanThreads / 32 + 1];
     uint32_t carry = 0;
+    uint64_t carryw = 0;
     for (uint32_t base = 0; base < lp.nblk; base += kPlanThreads) {
-        uint32_t i = base + threadIdx.x;
-        uint32_t v = i < lp.nblk ? lp.bsum[i] : 0;
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < lp.nblk ? lp.bsum[i] : 0;
+        const uint64_t vw = i < lp.nblk ? lp.bsumw[i] : 0;
         uint32_t total;
-        uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
-        if (i < lp.nblk) lp.bsum[i] = carry + ex;
+        uint64_t totalw;
+        const uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
+        const uint64_t exw = block_excl_scan<kPlanThreads>(vw, tmpw, &totalw);
+        if (i < lp.nblk) {
+            lp.bsum[i] = carry + ex;
+            lp.bsumw[i] = carryw + exw;
+        }
         carry += total;
+        carryw += totalw;
     }
-    if (threadIdx.x == 0) lp.bsum[lp.nblk] = carry;
+    if (threadIdx.x == 0) {
+        lp.bsum[lp.nblk] = carry;
+        lp.bsumw[lp.nblk] = carryw;
+    }
 }
 
+// Block offsets turn the block-local prefixes into launch-wide ones; every
+// chunk gets its CTA share (ccta).
 __global__ void __launch_bounds__(kPlanThreads) k_offsets(LaunchPlan lp) {
-    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
     const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
-    uint32_t v = g < lp.ptot ? word_cost(lp.cost[g]) : 0;
-    uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, nullptr);
-    if (g < lp.ptot) lp.off[g] = lp.bsum[blockIdx.x] + ex;
+    const uint64_t W = lp.bsumw[lp.nblk];
+    if (g < lp.ptot) {
+        lp.off[g] += lp.bsum[blockIdx.x];
+        lp.ccta[g] = cta_of_mid2(lp.wk[g] + 2 * lp.bsumw[blockIdx.x], W, lp.grid, share_recip(W));
+    }
     if (g == 0) lp.off[lp.ptot] = lp.bsum[lp.nblk];
 }
 
-
-// Tile packing.  A tile is a run of consecutive chunks of one DFA group whose
-// thread slots fit one CTA; chunks are packed greedily in order: a chunk
-// opens a new tile when it starts a new group or would overflow the budget.
-// The budget is kThreads, or less when the whole launch needs fewer thread
-// slots than the grid holds: then tiles shrink to about ceil(total / CTAs)
-// slots so a small launch spreads over every SM (fewer chunks per tile,
-// longer staged segments).  A greedy tile leaves fewer than cost_max slots
-// unused, so a budget of ceil(total / CTAs) + cost_max - 1 keeps the tile
-// count within the grid.  It never drops below one chunk's slots.
-//
-// The greedy pass is split into windows of kPackWin chunks, one warp each
-// (a window boundary also opens a tile, so each window packs independently):
-// pass 0 counts each window's tiles, a scan turns the counts into bases,
-// pass 1 repeats the same packing and writes each tile's first chunk.
-constexpr uint32_t kPackWin = 512;  // chunks per window of the multi-kernel path
-
-__device__ __forceinline__ uint32_t tile_budget(uint32_t cost_max, uint32_t spread) {
-    return max(cost_max, min((uint32_t)kThreads, spread + cost_max - 1));
+// Share boundaries: share c is chunks [share[c], share[c+1]); a chunk that
+// starts a share is marked kOpensTile.  Shares that got no chunk are empty.
+// sh_of(g) gives chunk g's share, for the chunks [0, ptot).
+template <typename ShareOf>
+__device__ __forceinline__ void share_bounds(uint32_t g, uint32_t ptot, uint32_t G, ShareOf sh_of,
+                                             uint32_t* share, uint32_t* word) {
+    const uint32_t c = sh_of(g);
+    const int cp = g ? (int)sh_of(g - 1) : -1;
+    if ((int)c != cp) {
+        for (int x = cp + 1; x <= (int)c; ++x) share[x] = g;
+        *word |= kOpensTile;
+    }
+    if (g + 1 == ptot)
+        for (uint32_t x = c + 1; x <= G; ++x) share[x] = ptot;
 }
 
-// One warp packs chunks [w0, w1) from their packing words; returns its tile
-// count.  Every lane runs the same greedy pass (words are read 16 at a time
-// with independent loads, then scanned in registers); with out != nullptr,
-// lane 0 writes each tile's first chunk to out[0..].  Chunk g's word is
-// words[g - wbase], in global or shared memory.
-__device__ uint32_t pack_window(const uint32_t* words, uint32_t wbase, uint32_t w0, uint32_t w1,
-                                uint32_t spread, uint32_t* out) {
+// Tile packing.  A tile is a run of consecutive chunks of one DFA group,
+// inside one CTA share, whose thread slots fit one CTA (kThreads); each share
+// is packed greedily in order by one warp: a chunk opens a new tile when it is
+// marked kOpensTile (a new group or share) or would overflow the tile.  The
+// CTA that owns a share runs its tiles one after the other, so tile starts
+// come only from the shares' contents, never from how the work is split
+// among warps.
+struct Packer {
+    uint32_t cur = 0, tiles = 0;
+};
+
+// Greedy pass over the packing words v[0..n) of chunks g0 .. g0+n-1 of a
+// share starting at chunk f (every lane runs it; words are read 16 at a time
+// with independent loads, then scanned in registers).  With out != nullptr,
+// lane 0 writes each tile's first chunk to out[tile index].
+__device__ __forceinline__ void pack_words(const uint32_t* v, uint32_t n, uint32_t g0, uint32_t f,
+                                           Packer& pk, uint32_t* out) {
     const uint32_t lane = threadIdx.x & 31;
-    uint32_t tiles = 0, cur = 0, budget = 0;
-    for (uint32_t b = w0; b < w1; b += 16) {
-        uint32_t v[16];
+    for (uint32_t b = 0; b < n; b += 16) {
+        uint32_t x[16];
 #pragma unroll
-        for (uint32_t i = 0; i < 16; ++i) v[i] = b + i < w1 ? words[b + i - wbase] : 0u;
+        for (uint32_t i = 0; i < 16; ++i) x[i] = b + i < n ? v[b + i] : 0u;
 #pragma unroll
         for (uint32_t i = 0; i < 16; ++i) {
-            if (b + i >= w1) break;
-            const uint32_t c = word_cost(v[i]);
-            if ((v[i] >> 20) || b + i == w0) {
-                budget = tile_budget((v[i] >> 10) & 0x3FFu, spread);
-                cur = budget;  // force a new tile
+            if (b + i >= n) break;
+            const uint32_t g = g0 + b + i, c = word_cost(x[i]);
+            if ((x[i] & kOpensTile) || g == f || pk.cur + c > (uint32_t)kThreads) {
+                if (out && lane == 0) out[pk.tiles] = g;
+                ++pk.tiles;
+                pk.cur = 0;
             }
-            if (cur + c > budget) {
-                if (out && lane == 0) out[tiles] = b + i;
-                ++tiles;
-                cur = 0;
-            }
-            cur += c;
+            pk.cur += c;
         }
+    }
+}
+
+// The same greedy pass run by one thread over a whole share [f, e) of
+// shared-memory words (the fused planner gives every share its own thread).
+__device__ __forceinline__ uint32_t pack_share(const uint32_t* words, uint32_t f, uint32_t e,
+                                               uint32_t* out) {
+    uint32_t cur = 0, tiles = 0;
+    for (uint32_t g = f; g < e; ++g) {
+        const uint32_t x = words[g], c = word_cost(x);
+        if ((x & kOpensTile) || g == f || cur + c > (uint32_t)kThreads) {
+            if (out) out[tiles] = g;
+            ++tiles;
+            cur = 0;
+        }
+        cur += c;
     }
     return tiles;
 }
 
+// Share boundaries and tile-start marks for the multi-kernel path.
+__global__ void __launch_bounds__(kPlanThreads) k_shares(LaunchPlan lp) {
+    const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
+    if (g >= lp.ptot) return;
+    uint32_t w = lp.cost[g];
+    share_bounds(g, lp.ptot, lp.grid, [&](uint32_t x) { return lp.ccta[x]; }, lp.share, &w);
+    lp.cost[g] = w;
+}
+
+constexpr uint32_t kPackWin = 512;  // packing words one warp stages at a time
 constexpr int kPackWarps = 8;
 
-// Each warp first copies its window's packing words into shared memory (one
-// coalesced read), so the serial greedy pass runs on shared-memory latency.
+// One warp per share.  Pass 0 packs the share from its words, staged through
+// shared memory kPackWin at a time (one coalesced read each), and leaves its
+// tile starts in the share's own slice of lp.cost (a tile start never
+// overtakes the words still to be read); ntiles[c] gets the count.  Pass 1,
+// after the scan of the counts, copies each slice to its place in tile_first
+// and sets the CTA's tile range.
 __global__ void __launch_bounds__(kPackWarps * 32) k_pack(LaunchPlan lp, uint32_t pass) {
     __shared__ uint32_t win[kPackWarps][kPackWin];
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const uint32_t w = blockIdx.x * kPackWarps + wl;
-    const uint32_t w0 = w * kPackWin;
-    if (w0 >= lp.ptot) return;  // warp-uniform
-    const uint32_t total = lp.bsum[lp.nblk];
-    const uint32_t spread = (total + lp.grid - 1) / lp.grid;
-    const uint32_t w1 = min(w0 + kPackWin, lp.ptot);
-    for (uint32_t i = lane; i < w1 - w0; i += 32) win[wl][i] = lp.cost[w0 + i];
-    __syncwarp();
-    uint32_t* out = pass == 0 ? nullptr : lp.tile_first + lp.wtiles[w];
-    const uint32_t n = pack_window(win[wl], w0, w0, w1, spread, out);
-    if (pass == 0 && lane == 0) lp.wtiles[w] = n;
+    const uint32_t c = blockIdx.x * kPackWarps + wl;
+    if (c >= lp.grid) return;  // warp-uniform
+    const uint32_t f = lp.share[c], e = lp.share[c + 1];
+    if (pass == 0) {
+        Packer pk;
+        for (uint32_t p0 = f; p0 < e; p0 += kPackWin) {
+            const uint32_t p1 = min(p0 + kPackWin, e);
+            __syncwarp();
+            for (uint32_t i = lane; i < p1 - p0; i += 32) win[wl][i] = lp.cost[p0 + i];
+            __syncwarp();
+            pack_words(win[wl], p1 - p0, p0, f, pk, lp.cost + f);
+        }
+        if (lane == 0) lp.ntiles[c] = pk.tiles;
+    } else {
+        const uint32_t base = lp.ntiles[c];
+        const uint32_t n = (c + 1 < lp.grid ? lp.ntiles[c + 1] : *lp.num_tiles) - base;
+        for (uint32_t i = lane; i < n; i += 32) lp.tile_first[base + i] = lp.cost[f + i];
+        if (lane == 0) {
+            lp.cta_range[2 * c] = base;
+            lp.cta_range[2 * c + 1] = base + n;
+        }
+    }
 }
 
-// Exclusive scan of the per-window tile counts (one CTA); the total is the
+// Exclusive scan of the per-share tile counts (one CTA); the total is the
 // number of tiles, and tile_first[T] = ptot closes the last tile.
-__global__ void __launch_bounds__(kPlanThreads) k_scan_windows(LaunchPlan lp, uint32_t nwin) {
+__global__ void __launch_bounds__(kPlanThreads) k_scan_shares(LaunchPlan lp) {
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
     uint32_t carry = 0;
-    for (uint32_t base = 0; base < nwin; base += kPlanThreads) {
+    for (uint32_t base = 0; base < lp.grid; base += kPlanThreads) {
         const uint32_t i = base + threadIdx.x;
-        const uint32_t v = i < nwin ? lp.wtiles[i] : 0;
+        const uint32_t v = i < lp.grid ? lp.ntiles[i] : 0;
         uint32_t total;
         const uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
-        if (i < nwin) lp.wtiles[i] = carry + ex;
+        if (i < lp.grid) lp.ntiles[i] = carry + ex;
         carry += total;
     }
     if (threadIdx.x == 0) {
@@ -380,52 +533,104 @@ __global__ void __launch_bounds__(kPlanThreads) k_scan_windows(LaunchPlan lp, ui
     }
 }
 
-// All planning steps in one CTA, for launches with at most kSmallPlan chunks
-// (saves five launches on latency-bound calls).  The packing words stay in
-// shared memory and the greedy pass is split into 32 windows of
-// ceil(ptot / 32) chunks (rounded up to 16), one per warp, so a small launch
-// is packed by every warp; tiles are the same as the multi-kernel path's
-// except at window boundaries, which open a tile in both.
+// The planning steps after the count in one CTA, for launches with at most
+// kSmallPlan chunks and kSmallShares CTAs (saves five launches on
+// latency-bound calls); with counted == 0 (at most kFusedPlan chunks) it also
+// counts the chunks itself, else k_count has run.  The packing words, shares
+// and per-share tile counts stay in shared memory; thread c packs share c.
+// Same tiles as the multi-kernel path.
 constexpr uint32_t kSmallPlan = 16384;
-constexpr uint32_t kSmallPlanSmem = kSmallPlan * 4;
+constexpr uint32_t kFusedPlan = 2048;
+constexpr uint32_t kSmallShares = 2048;
+constexpr uint32_t kSmallPlanSmem = kSmallPlan * 4 + kSmallPlan * 2 + (2 * kSmallShares + 1) * 4;
 
-__global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp) {
-    extern __shared__ uint32_t pw[];  // packing words, kSmallPlan entries
+__global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp, uint32_t counted) {
+    extern __shared__ uint32_t pw[];                                       // [kSmallPlan] words
+    uint16_t* cc = reinterpret_cast<uint16_t*>(pw + kSmallPlan);           // [kSmallPlan] shares
+    uint32_t* share = reinterpret_cast<uint32_t*>(cc + kSmallPlan);        // [G + 1]
+    uint32_t* cnt = share + kSmallShares + 1;                              // [G]
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
-    __shared__ uint32_t wt[kPlanThreads / 32];
-    // per-chunk counts and the exclusive scan, 1024 chunks per round
+    __shared__ uint64_t tmpw[kPlanThreads / 32 + 1];
+    __shared__ uint32_t boff[kSmallPlan / kPlanThreads + 1];
+    __shared__ uint64_t bwoff[kSmallPlan / kPlanThreads + 1];
+    const uint32_t G = lp.grid;
     uint32_t carry = 0;
-    for (uint32_t base = 0; base < lp.ptot; base += kPlanThreads) {
-        const uint32_t g = base + threadIdx.x;
-        const uint32_t cost = g < lp.ptot ? chunk_count(lp, g) : 0;
-        if (g < lp.ptot) pw[g] = lp.cost[g];
-        uint32_t total;
-        const uint32_t ex = block_excl_scan<kPlanThreads>(cost, tmp, &total);
-        if (g < lp.ptot) lp.off[g] = carry + ex;
-        carry += total;
+    uint64_t carryw = 0;
+    if (!counted) {
+        // the whole count here: at most kFusedPlan chunks, one per thread and round
+        if (!lp.dyn) {  // otherwise k_lookahead ran first and the launch cleared them
+            for (uint32_t i = threadIdx.x; i < 2 * lp.ntests; i += kPlanThreads) lp.test_err[i] = 0;
+            __syncthreads();
+        }
+        for (uint32_t base = 0; base < lp.ptot; base += kPlanThreads) {
+            const uint32_t g = base + threadIdx.x;
+            uint32_t cost;
+            uint64_t work;
+            chunk_count_n<1>(lp, g, &cost, &work);
+            uint32_t total;
+            uint64_t totalw;
+            const uint32_t ex = block_excl_scan<kPlanThreads>(cost, tmp, &total);
+            const uint64_t exw = block_excl_scan<kPlanThreads>(work, tmpw, &totalw);
+            if (g < lp.ptot) {
+                pw[g] = lp.cost[g];
+                lp.off[g] = carry + ex;
+                lp.wk[g] = 2 * (carryw + exw) + work;
+            }
+            carry += total;
+            carryw += totalw;
+        }
+    } else {
+        // k_count ran on every SM: add the block offsets to its block-local prefixes
+        if (threadIdx.x == 0) {
+            for (uint32_t k = 0; k < lp.nblk; ++k) {
+                boff[k] = carry;
+                bwoff[k] = carryw;
+                carry += lp.bsum[k];
+                carryw += lp.bsumw[k];
+            }
+            boff[lp.nblk] = carry;
+            bwoff[lp.nblk] = carryw;
+        }
+        __syncthreads();
+        carry = boff[lp.nblk];
+        carryw = bwoff[lp.nblk];
+        for (uint32_t g = threadIdx.x; g < lp.ptot; g += kPlanThreads) {
+            const uint32_t k = g / kPlanThreads;
+            pw[g] = lp.cost[g];
+            lp.off[g] += boff[k];
+            lp.wk[g] += 2 * bwoff[k];
+        }
     }
     if (threadIdx.x == 0) lp.off[lp.ptot] = carry;
     __syncthreads();
-    const uint32_t spread = (carry + lp.grid - 1) / lp.grid;
-    const uint32_t nw = kPlanThreads / 32;
-    const uint32_t win = ((lp.ptot + nw - 1) / nw + 15u) & ~15u;
-    const uint32_t w = threadIdx.x >> 5;
-    const uint32_t w0 = min(w * win, lp.ptot), w1 = min(w0 + win, lp.ptot);
-    const uint32_t n = pack_window(pw, 0, w0, w1, spread, nullptr);
-    if ((threadIdx.x & 31) == 0) wt[w] = n;
+    const uint64_t winv = share_recip(carryw);
+    for (uint32_t g = threadIdx.x; g < lp.ptot; g += kPlanThreads)
+        cc[g] = (uint16_t)cta_of_mid2(lp.wk[g], carryw, G, winv);
     __syncthreads();
+    for (uint32_t g = threadIdx.x; g < lp.ptot; g += kPlanThreads)
+        share_bounds(g, lp.ptot, G, [&](uint32_t x) { return (uint32_t)cc[x]; }, share, pw + g);
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < G; c += kPlanThreads)
+        cnt[c] = pack_share(pw, share[c], share[c + 1], nullptr);
+    __syncthreads();
+    uint32_t acc = 0;
+    for (uint32_t base = 0; base < G; base += kPlanThreads) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < G ? cnt[i] : 0;
+        uint32_t total;
+        const uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
+        if (i < G) cnt[i] = acc + ex;
+        acc += total;
+    }
     if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (uint32_t i = 0; i < nw; ++i) {
-            const uint32_t x = wt[i];
-            wt[i] = acc;
-            acc += x;
-        }
         *lp.num_tiles = acc;
         lp.tile_first[acc] = lp.ptot;
     }
-    __syncthreads();
-    pack_window(pw, 0, w0, w1, spread, lp.tile_first + wt[w]);
+    for (uint32_t c = threadIdx.x; c < G; c += kPlanThreads) {
+        const uint32_t n = pack_share(pw, share[c], share[c + 1], lp.tile_first + cnt[c]);
+        lp.cta_range[2 * c] = cnt[c];
+        lp.cta_range[2 * c + 1] = cnt[c] + n;
+    }
 }
 
 // ------------------------------------------------------------ matching
@@ -747,8 +952,15 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
         __syncthreads();
         for (uint32_t k = threadIdx.x; k < nb * words; k += kThreads) {
             const uint32_t j = k / words, w = k - j * words;
+            const uint32_t cb = b0 + i0 + j;
+            // a CTA between the test's first and last CTA either holds a part
+            // of it or got no share at all (then its map is the identity)
+            if (__ldcg(lp.cta_range + 2 * cb) == __ldcg(lp.cta_range + 2 * cb + 1)) {
+                sm[j * words + w] = (2 * w) | ((2 * w + 1) << 16);
+                continue;
+            }
             const uint32_t* src = reinterpret_cast<const uint32_t*>(
-                lp.seg_vals + (size_t)(b0 + i0 + j + t) * lp.seg_stride);
+                lp.seg_vals + (size_t)(cb + t) * lp.seg_stride);
             sm[j * words + w] = __ldcg(src + w);
         }
         __syncthreads();
@@ -788,17 +1000,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
     const uint16_t* linit = reinterpret_cast<const uint16_t*>(sm + L.linit);
     const int tid = threadIdx.x;
 
-    const uint32_t T = *lp.num_tiles;
-    const uint32_t G = gridDim.x, b = blockIdx.x;
-    // CTA b owns tiles [t0, t1); the CTAs that own tiles are 0, 1, 2, ... without gaps
-    uint32_t t0, t1;
-    if (T >= G) {
-        t0 = (uint32_t)((uint64_t)b * T / G);
-        t1 = (uint32_t)((uint64_t)(b + 1) * T / G);
-    } else {
-        t0 = b < T ? b : T;
-        t1 = b + 1 < T ? b + 1 : T;
-    }
+    const uint32_t b = blockIdx.x;
+    // CTA b owns tiles [t0, t1): its share of the launch's work (chunk_cta);
+    // a CTA without a share returns at once
+    const uint32_t t0 = lp.cta_range[2 * b], t1 = lp.cta_range[2 * b + 1];
     if (t0 >= t1) return;
     const uint32_t c_lo = lp.tile_first[t0], c_hi = lp.tile_first[t1];
 
@@ -901,7 +1106,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             const uint32_t te = lp.chunk_test[g];
             const DevTest tt = test_at(lp, te);
             const uint32_t k = g - tt.chunk_base;
-            const uint64_t st = dstart(tt.n, tt.P, tt.m, k), en = dstart(tt.n, tt.P, tt.m, k + 1);
+            const uint64_t st = dstart(tt, k), en = dstart(tt, k + 1);
             const uint32_t cls = lp.chunk_cls[g];
             ChunkMeta m;
             uint32_t size;
@@ -1076,35 +1281,43 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
     return grid_for<4, 3>(smem, grid);
 }
 
+uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn) {
+    const bool small = ptot <= kSmallPlan && grid <= kSmallShares;
+    return (small ? (ptot <= kFusedPlan ? 2u : 3u) : 8u) + (dyn ? 1u : 0u);
+}
+
 // Issue the whole launch on `st`: memsets of the per-test counters, the
 // planning kernels (k_lookahead only for r >= 2) and the match kernel.
 // With plan_only the match kernel is skipped.
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
                 uint32_t* kernels, void* ev_begin, void* ev_end, bool plan_only) {
-    if (cudaMemsetAsync(lp.test_err, 0, sizeof(uint32_t) * lp.ntests * 2, st) != cudaSuccess)
-        return DFA_ECUDA;  // test_err and arrived are adjacent
     const uint32_t nb = lp.nblk;
-    uint32_t nk = 6;
+    const bool small = lp.ptot <= kSmallPlan && lp.grid <= kSmallShares;
+    const bool fused = small && lp.ptot <= kFusedPlan;
+    // test_err and arrived (adjacent) start at zero; the fused planner clears
+    // them itself unless k_lookahead, which may flag a test, runs first
+    if ((!fused || lp.dyn) &&
+        cudaMemsetAsync(lp.test_err, 0, sizeof(uint32_t) * lp.ntests * 2, st) != cudaSuccess)
+        return DFA_ECUDA;
+    uint32_t nk = launch_kernel_count(lp.ptot, lp.grid, lp.dyn != 0);
     if (lp.dyn) {
         const uint32_t qe_words = (lp.qe_max + 31) / 32, set_words = (lp.vcap + 1) / 2;
         const uint32_t smem = kLaWarps * (qe_words + set_words) * 4;
         k_lookahead<<<(lp.ptot + kLaWarps - 1) / kLaWarps, kLaWarps * 32, smem, st>>>(lp, qe_words,
                                                                                    set_words);
-        ++nk;
     }
-    if (lp.ptot <= kSmallPlan) {
-        k_plan_small<<<1, kPlanThreads, kSmallPlanSmem, st>>>(lp);
-        nk -= 4;  // one planning kernel instead of five
+    if (small) {
+        if (!fused) k_count<<<nb, kPlanThreads, 0, st>>>(lp);
+        k_plan_small<<<1, kPlanThreads, kSmallPlanSmem, st>>>(lp, fused ? 0u : 1u);
     } else {
-        const uint32_t nwin = (lp.ptot + kPackWin - 1) / kPackWin;
-        const uint32_t pblocks = (nwin + kPackWarps - 1) / kPackWarps;
+        const uint32_t pblocks = (lp.grid + kPackWarps - 1) / kPackWarps;
         k_count<<<nb, kPlanThreads, 0, st>>>(lp);
         k_scan_blocks<<<1, kPlanThreads, 0, st>>>(lp);
         k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
+        k_shares<<<nb, kPlanThreads, 0, st>>>(lp);
         k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 0);
-        k_scan_windows<<<1, kPlanThreads, 0, st>>>(lp, nwin);
+        k_scan_shares<<<1, kPlanThreads, 0, st>>>(lp);
         k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 1);
-        ++nk;
     }
     if (plan_only) {
         if (kernels) *kernels = nk - 1;
