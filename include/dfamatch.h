@@ -213,8 +213,8 @@ int dfa_plan_sets(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
                   const dfa_match_opts_t *opts, uint32_t *sizes, uint32_t cap, uint32_t *P);
 
 /* Kernel launches one dfa_match_async / dfa_match call issues for (dfa, len,
- * opts): the planning kernels (one fused kernel for plans of at most 16384
- * chunks, else six), k_lookahead when opts->lookahead >= 2, and the match
+ * opts): the planning kernels (one fused kernel for plans of at most 2048
+ * chunks, else four), k_lookahead when opts->lookahead >= 2, and the match
  * kernel. */
 int dfa_match_num_kernels(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts,
                           uint32_t *n);

@@ -1,14 +1,12 @@
 // Device side of the speculative chunked DFA membership test (sm_103a).
 //
 // A launch covers `ntests` independent membership tests.  Work flows through
-// seven planning kernels (or k_plan_small, all of them in one CTA, for small
+// four planning kernels (or k_plan_small, all of them in one CTA, for small
 // launches) and one persistent match kernel, all on one stream:
 //
 //   k_count        per chunk: test, reverse-lookahead class, thread slots, work  (Alg. 3 l.16, Eq. 11)
-//   k_scan_blocks  exclusive scans of the per-block sums
-//   k_offsets      per-chunk slot offsets and CTA shares of the work
-//   k_shares       share boundaries
-//   k_pack (x2), k_scan_shares   greedy packing of each share into tiles
+//   k_offsets      per-chunk slot offsets, CTA shares of the work, share bounds
+//   k_pack (x2)    greedy packing of each share into tiles, tile ranges
 //   k_match        persistent: stage chunks, advance every (chunk, state) chain,
 //                  compose the chunk maps, combine per test             (Alg. 3 l.8-20, Eqs. 8-9)
 //
@@ -360,46 +358,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_count(LaunchPlan lp) {
     }
 }
 
-// Exclusive scans of the block sums (one CTA).  bsum[nblk] and bsumw[nblk]
-// receive the totals.
-__global__ void __launch_bounds__(kPlanThreads) k_scan_blocks(LaunchPlan lp) {
-    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
-    __shared__ uint64_t tmpw[kPlanThreads / 32 + 1];
-    uint32_t carry = 0;
-    uint64_t carryw = 0;
-    for (uint32_t base = 0; base < lp.nblk; base += kPlanThreads) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t v = i < lp.nblk ? lp.bsum[i] : 0;
-        const uint64_t vw = i < lp.nblk ? lp.bsumw[i] : 0;
-        uint32_t total;
-        uint64_t totalw;
-        const uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
-        const uint64_t exw = block_excl_scan<kPlanThreads>(vw, tmpw, &totalw);
-        if (i < lp.nblk) {
-            lp.bsum[i] = carry + ex;
-            lp.bsumw[i] = carryw + exw;
-        }
-        carry += total;
-        carryw += totalw;
-    }
-    if (threadIdx.x == 0) {
-        lp.bsum[lp.nblk] = carry;
-        lp.bsumw[lp.nblk] = carryw;
-    }
-}
-
-// Block offsets turn the block-local prefixes into launch-wide ones; every
-// chunk gets its CTA share (ccta).
-__global__ void __launch_bounds__(kPlanThreads) k_offsets(LaunchPlan lp) {
-    const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
-    const uint64_t W = lp.bsumw[lp.nblk];
-    if (g < lp.ptot) {
-        lp.off[g] += lp.bsum[blockIdx.x];
-        lp.ccta[g] = cta_of_mid2(lp.wk[g] + 2 * lp.bsumw[blockIdx.x], W, lp.grid, share_recip(W));
-    }
-    if (g == 0) lp.off[lp.ptot] = lp.bsum[lp.nblk];
-}
-
 // Share boundaries: share c is chunks [share[c], share[c+1]); a chunk that
 // starts a share is marked kOpensTile.  Shares that got no chunk are empty.
 // sh_of(g) gives chunk g's share, for the chunks [0, ptot).
@@ -414,6 +372,55 @@ __device__ __forceinline__ void share_bounds(uint32_t g, uint32_t ptot, uint32_t
     }
     if (g + 1 == ptot)
         for (uint32_t x = c + 1; x <= G; ++x) share[x] = ptot;
+}
+
+// Sum of v[0..n) by all threads of a block of NTH threads (tmp: NTH/32+1 entries).
+template <int NTH, typename T>
+__device__ __forceinline__ T block_sum(const T* v, uint32_t n, T* tmp) {
+    T acc = 0;
+    for (uint32_t base = 0; base < n; base += NTH) {
+        const uint32_t i = base + threadIdx.x;
+        T total;
+        block_excl_scan<NTH>(i < n ? v[i] : (T)0, tmp, &total);
+        acc += total;
+    }
+    return acc;
+}
+
+// Launch-wide prefixes and CTA shares (multi-kernel path).  Every block adds
+// the sums of the blocks before it (and needs the launch total W for the
+// shares); chunk g gets its share, and a chunk that starts a share records
+// the share boundaries and is marked kOpensTile.
+__global__ void __launch_bounds__(kPlanThreads) k_offsets(LaunchPlan lp) {
+    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
+    __shared__ uint64_t tmpw[kPlanThreads / 32 + 1];
+    __shared__ uint32_t cs[kPlanThreads];
+    const uint32_t blk = blockIdx.x, g = blk * kPlanThreads + threadIdx.x;
+    const uint32_t boff = block_sum<kPlanThreads>(lp.bsum, blk, tmp);
+    const uint64_t bwoff = block_sum<kPlanThreads>(lp.bsumw, blk, tmpw);
+    const uint32_t total = boff + block_sum<kPlanThreads>(lp.bsum + blk, lp.nblk - blk, tmp);
+    const uint64_t W = bwoff + block_sum<kPlanThreads>(lp.bsumw + blk, lp.nblk - blk, tmpw);
+    const uint64_t winv = share_recip(W);
+    const uint32_t G = lp.grid;
+    uint32_t c = 0;
+    if (g < lp.ptot) {
+        lp.off[g] += boff;
+        c = cta_of_mid2(lp.wk[g] + 2 * bwoff, W, G, winv);
+        cs[threadIdx.x] = c;
+    }
+    __syncthreads();
+    if (g < lp.ptot) {
+        uint32_t w = lp.cost[g];
+        // the previous chunk's share: from this block, or recomputed for the first thread
+        auto sh_of = [&](uint32_t x) -> uint32_t {
+            if (x == g) return c;
+            if (x >= blk * kPlanThreads) return cs[x - blk * kPlanThreads];
+            return cta_of_mid2(lp.wk[x] + 2 * (bwoff - lp.bsumw[blk - 1]), W, G, winv);
+        };
+        share_bounds(g, lp.ptot, G, sh_of, lp.share, &w);
+        lp.cost[g] = w;
+    }
+    if (g == 0) lp.off[lp.ptot] = total;
 }
 
 // Tile packing.  A tile is a run of consecutive chunks of one DFA group,
@@ -469,31 +476,24 @@ __device__ __forceinline__ uint32_t pack_share(const uint32_t* words, uint32_t f
     return tiles;
 }
 
-// Share boundaries and tile-start marks for the multi-kernel path.
-__global__ void __launch_bounds__(kPlanThreads) k_shares(LaunchPlan lp) {
-    const uint32_t g = blockIdx.x * kPlanThreads + threadIdx.x;
-    if (g >= lp.ptot) return;
-    uint32_t w = lp.cost[g];
-    share_bounds(g, lp.ptot, lp.grid, [&](uint32_t x) { return lp.ccta[x]; }, lp.share, &w);
-    lp.cost[g] = w;
-}
-
 constexpr uint32_t kPackWin = 512;  // packing words one warp stages at a time
 constexpr int kPackWarps = 8;
 
 // One warp per share.  Pass 0 packs the share from its words, staged through
 // shared memory kPackWin at a time (one coalesced read each), and leaves its
 // tile starts in the share's own slice of lp.cost (a tile start never
-// overtakes the words still to be read); ntiles[c] gets the count.  Pass 1,
-// after the scan of the counts, copies each slice to its place in tile_first
-// and sets the CTA's tile range.
+// overtakes the words still to be read); ntiles[c] gets the count.  Pass 1
+// scans the counts (every block for itself), copies each slice to its place
+// in tile_first and sets the CTA's tile range; the block of the last share
+// also writes the tile count and closes the last tile.
 __global__ void __launch_bounds__(kPackWarps * 32) k_pack(LaunchPlan lp, uint32_t pass) {
     __shared__ uint32_t win[kPackWarps][kPackWin];
+    __shared__ uint32_t tmp[kPackWarps + 1];
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const uint32_t c = blockIdx.x * kPackWarps + wl;
-    if (c >= lp.grid) return;  // warp-uniform
-    const uint32_t f = lp.share[c], e = lp.share[c + 1];
     if (pass == 0) {
+        if (c >= lp.grid) return;  // warp-uniform
+        const uint32_t f = lp.share[c], e = lp.share[c + 1];
         Packer pk;
         for (uint32_t p0 = f; p0 < e; p0 += kPackWin) {
             const uint32_t p1 = min(p0 + kPackWin, e);
@@ -503,103 +503,68 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(LaunchPlan lp, uint32_
             pack_words(win[wl], p1 - p0, p0, f, pk, lp.cost + f);
         }
         if (lane == 0) lp.ntiles[c] = pk.tiles;
-    } else {
-        const uint32_t base = lp.ntiles[c];
-        const uint32_t n = (c + 1 < lp.grid ? lp.ntiles[c + 1] : *lp.num_tiles) - base;
-        for (uint32_t i = lane; i < n; i += 32) lp.tile_first[base + i] = lp.cost[f + i];
-        if (lane == 0) {
-            lp.cta_range[2 * c] = base;
-            lp.cta_range[2 * c + 1] = base + n;
+        return;
+    }
+    // pass 1: the first share of this block starts after the tiles of shares [0, c0)
+    const uint32_t c0 = blockIdx.x * kPackWarps;
+    const uint32_t before = block_sum<kPackWarps * 32>(lp.ntiles, c0, tmp);
+    const uint32_t mine = c < lp.grid ? lp.ntiles[c] : 0;
+    uint32_t blk_total;
+    const uint32_t wex = block_excl_scan<kPackWarps * 32>(lane == 0 ? mine : 0u, tmp, &blk_total);
+    if (c >= lp.grid) return;  // warp-uniform
+    const uint32_t base = before + __shfl_sync(0xffffffffu, wex, 0);
+    const uint32_t f = lp.share[c];
+    for (uint32_t i = lane; i < mine; i += 32) lp.tile_first[base + i] = lp.cost[f + i];
+    if (lane == 0) {
+        lp.cta_range[2 * c] = base;
+        lp.cta_range[2 * c + 1] = base + mine;
+        if (c + 1 == lp.grid) {
+            *lp.num_tiles = base + mine;
+            lp.tile_first[base + mine] = lp.ptot;
         }
     }
 }
 
-// Exclusive scan of the per-share tile counts (one CTA); the total is the
-// number of tiles, and tile_first[T] = ptot closes the last tile.
-__global__ void __launch_bounds__(kPlanThreads) k_scan_shares(LaunchPlan lp) {
-    __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
-    uint32_t carry = 0;
-    for (uint32_t base = 0; base < lp.grid; base += kPlanThreads) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t v = i < lp.grid ? lp.ntiles[i] : 0;
-        uint32_t total;
-        const uint32_t ex = block_excl_scan<kPlanThreads>(v, tmp, &total);
-        if (i < lp.grid) lp.ntiles[i] = carry + ex;
-        carry += total;
-    }
-    if (threadIdx.x == 0) {
-        *lp.num_tiles = carry;
-        lp.tile_first[carry] = lp.ptot;
-    }
-}
-
-// The planning steps after the count in one CTA, for launches with at most
-// kSmallPlan chunks and kSmallShares CTAs (saves five launches on
-// latency-bound calls); with counted == 0 (at most kFusedPlan chunks) it also
-// counts the chunks itself, else k_count has run.  The packing words, shares
-// and per-share tile counts stay in shared memory; thread c packs share c.
-// Same tiles as the multi-kernel path.
-constexpr uint32_t kSmallPlan = 16384;
-constexpr uint32_t kFusedPlan = 2048;
+// All planning steps in one CTA, for launches with at most kSmallPlan chunks
+// and kSmallShares CTAs (one launch instead of four on latency-bound calls).
+// The packing words, shares and per-share tile counts stay in shared memory;
+// thread c packs share c.  Same tiles as the multi-kernel path.
+constexpr uint32_t kSmallPlan = 2048;
 constexpr uint32_t kSmallShares = 2048;
 constexpr uint32_t kSmallPlanSmem = kSmallPlan * 4 + kSmallPlan * 2 + (2 * kSmallShares + 1) * 4;
 
-__global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp, uint32_t counted) {
+__global__ void __launch_bounds__(kPlanThreads) k_plan_small(LaunchPlan lp) {
     extern __shared__ uint32_t pw[];                                       // [kSmallPlan] words
     uint16_t* cc = reinterpret_cast<uint16_t*>(pw + kSmallPlan);           // [kSmallPlan] shares
     uint32_t* share = reinterpret_cast<uint32_t*>(cc + kSmallPlan);        // [G + 1]
     uint32_t* cnt = share + kSmallShares + 1;                              // [G]
     __shared__ uint32_t tmp[kPlanThreads / 32 + 1];
     __shared__ uint64_t tmpw[kPlanThreads / 32 + 1];
-    __shared__ uint32_t boff[kSmallPlan / kPlanThreads + 1];
-    __shared__ uint64_t bwoff[kSmallPlan / kPlanThreads + 1];
     const uint32_t G = lp.grid;
     uint32_t carry = 0;
     uint64_t carryw = 0;
-    if (!counted) {
-        // the whole count here: at most kFusedPlan chunks, one per thread and round
-        if (!lp.dyn) {  // otherwise k_lookahead ran first and the launch cleared them
-            for (uint32_t i = threadIdx.x; i < 2 * lp.ntests; i += kPlanThreads) lp.test_err[i] = 0;
-            __syncthreads();
-        }
-        for (uint32_t base = 0; base < lp.ptot; base += kPlanThreads) {
-            const uint32_t g = base + threadIdx.x;
-            uint32_t cost;
-            uint64_t work;
-            chunk_count_n<1>(lp, g, &cost, &work);
-            uint32_t total;
-            uint64_t totalw;
-            const uint32_t ex = block_excl_scan<kPlanThreads>(cost, tmp, &total);
-            const uint64_t exw = block_excl_scan<kPlanThreads>(work, tmpw, &totalw);
-            if (g < lp.ptot) {
-                pw[g] = lp.cost[g];
-                lp.off[g] = carry + ex;
-                lp.wk[g] = 2 * (carryw + exw) + work;
-            }
-            carry += total;
-            carryw += totalw;
-        }
-    } else {
-        // k_count ran on every SM: add the block offsets to its block-local prefixes
-        if (threadIdx.x == 0) {
-            for (uint32_t k = 0; k < lp.nblk; ++k) {
-                boff[k] = carry;
-                bwoff[k] = carryw;
-                carry += lp.bsum[k];
-                carryw += lp.bsumw[k];
-            }
-            boff[lp.nblk] = carry;
-            bwoff[lp.nblk] = carryw;
-        }
+    // per-chunk counts and the exclusive scans, one chunk per thread and round;
+    // wk[g] keeps twice the chunk's work midpoint until the total is known
+    if (!lp.dyn) {  // otherwise k_lookahead ran first and the launch cleared them
+        for (uint32_t i = threadIdx.x; i < 2 * lp.ntests; i += kPlanThreads) lp.test_err[i] = 0;
         __syncthreads();
-        carry = boff[lp.nblk];
-        carryw = bwoff[lp.nblk];
-        for (uint32_t g = threadIdx.x; g < lp.ptot; g += kPlanThreads) {
-            const uint32_t k = g / kPlanThreads;
+    }
+    for (uint32_t base = 0; base < lp.ptot; base += kPlanThreads) {
+        const uint32_t g = base + threadIdx.x;
+        uint32_t cost;
+        uint64_t work;
+        chunk_count_n<1>(lp, g, &cost, &work);
+        uint32_t total;
+        uint64_t totalw;
+        const uint32_t ex = block_excl_scan<kPlanThreads>(cost, tmp, &total);
+        const uint64_t exw = block_excl_scan<kPlanThreads>(work, tmpw, &totalw);
+        if (g < lp.ptot) {
             pw[g] = lp.cost[g];
-            lp.off[g] += boff[k];
-            lp.wk[g] += 2 * bwoff[k];
+            lp.off[g] = carry + ex;
+            lp.wk[g] = 2 * (carryw + exw) + work;
         }
+        carry += total;
+        carryw += totalw;
     }
     if (threadIdx.x == 0) lp.off[lp.ptot] = carry;
     __syncthreads();
@@ -1282,8 +1247,7 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
 }
 
 uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn) {
-    const bool small = ptot <= kSmallPlan && grid <= kSmallShares;
-    return (small ? (ptot <= kFusedPlan ? 2u : 3u) : 8u) + (dyn ? 1u : 0u);
+    return (ptot <= kSmallPlan && grid <= kSmallShares ? 2u : 5u) + (dyn ? 1u : 0u);
 }
 
 // Issue the whole launch on `st`: memsets of the per-test counters, the
@@ -1293,10 +1257,9 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
                 uint32_t* kernels, void* ev_begin, void* ev_end, bool plan_only) {
     const uint32_t nb = lp.nblk;
     const bool small = lp.ptot <= kSmallPlan && lp.grid <= kSmallShares;
-    const bool fused = small && lp.ptot <= kFusedPlan;
-    // test_err and arrived (adjacent) start at zero; the fused planner clears
-    // them itself unless k_lookahead, which may flag a test, runs first
-    if ((!fused || lp.dyn) &&
+    // test_err and arrived (adjacent) start at zero; k_plan_small clears them
+    // itself unless k_lookahead, which may flag a test, runs first
+    if ((!small || lp.dyn) &&
         cudaMemsetAsync(lp.test_err, 0, sizeof(uint32_t) * lp.ntests * 2, st) != cudaSuccess)
         return DFA_ECUDA;
     uint32_t nk = launch_kernel_count(lp.ptot, lp.grid, lp.dyn != 0);
@@ -1307,16 +1270,12 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
                                                                                    set_words);
     }
     if (small) {
-        if (!fused) k_count<<<nb, kPlanThreads, 0, st>>>(lp);
-        k_plan_small<<<1, kPlanThreads, kSmallPlanSmem, st>>>(lp, fused ? 0u : 1u);
+        k_plan_small<<<1, kPlanThreads, kSmallPlanSmem, st>>>(lp);
     } else {
         const uint32_t pblocks = (lp.grid + kPackWarps - 1) / kPackWarps;
         k_count<<<nb, kPlanThreads, 0, st>>>(lp);
-        k_scan_blocks<<<1, kPlanThreads, 0, st>>>(lp);
         k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
-        k_shares<<<nb, kPlanThreads, 0, st>>>(lp);
         k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 0);
-        k_scan_shares<<<1, kPlanThreads, 0, st>>>(lp);
         k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 1);
     }
     if (plan_only) {
