@@ -524,6 +524,11 @@ def main():
             # r-symbol reverse lookahead (Eq. 13): same input, smaller initial-state sets
             la = {}
             for r in (2, 4):
+                tr = None
+                if not args.tuning and not args.no_tune:
+                    t, _ = d.autotune(dev, lookahead=r)   # this depth's own tuning record
+                    tr = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
+                          "ctas_per_sm": t.ctas_per_sm}
                 kb2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                 ke2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                 for e in kb2 + ke2:
@@ -539,7 +544,8 @@ def main():
                 Wr, _ = lookups_per_launch(dm, d, dev, n, 0, r)
                 la["r%d" % r] = {"gbs": round(n / kms / 1e6, 3), "kernel_ms": round(kms, 3),
                                  "lookups_per_byte": round(Wr / n, 3),
-                                 "lookup_roof_frac": round(Wr / (kms / 1e3) / lookup_peak, 4)}
+                                 "lookup_roof_frac": round(Wr / (kms / 1e3) / lookup_peak, 4),
+                                 "tuning": tr}
                 del ws2
             line["lookahead"] = la
         if not args.no_mix and args.workload == "regex":

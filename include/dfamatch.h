@@ -159,6 +159,24 @@ int dfa_set_tuning(dfa_t *dfa, const dfa_tuning_t *tuning);
 int dfa_autotune(dfa_t *dfa, const uint8_t *dev_sample, uint64_t len, void *stream,
                  dfa_tuning_t *chosen, double *best_ms);
 
+/*
+ * Tuning records per lookahead depth.  A DFA keeps one base record (the one
+ * dfa_get_tuning / dfa_set_tuning / dfa_autotune read and write, used for
+ * lookahead 1) and may keep one record per other depth r = opts->lookahead
+ * (0 = Algorithm 2, 2..8 = Eq. (13) sets): the sets shrink as r grows, so the
+ * best chains per thread and tiles per CTA differ.  A depth without its own
+ * record uses the base record.  These three calls read, write or autotune the
+ * record of opts->lookahead (opts NULL = lookahead 1 = the base record).
+ * dfa_autotune_opts times launches with that lookahead (k_lookahead
+ * included).  Errors: as dfa_get_tuning / dfa_set_tuning / dfa_autotune, and
+ * DFA_EINVAL for a lookahead above 8.
+ */
+int dfa_get_tuning_opts(const dfa_t *dfa, const dfa_match_opts_t *opts, dfa_tuning_t *out);
+int dfa_set_tuning_opts(dfa_t *dfa, const dfa_match_opts_t *opts, const dfa_tuning_t *tuning);
+int dfa_autotune_opts(dfa_t *dfa, const uint8_t *dev_sample, uint64_t len,
+                      const dfa_match_opts_t *opts, void *stream, dfa_tuning_t *chosen,
+                      double *best_ms);
+
 /* out[256]: alphabet class of every byte, 0xFFFF for bytes not in Sigma. */
 int dfa_class_of_bytes(const dfa_t *dfa, uint16_t *out);
 

@@ -80,6 +80,9 @@ SIGNATURES = {
     "dfa_get_tuning": (_I, [_P, _P]),
     "dfa_set_tuning": (_I, [_P, _P]),
     "dfa_autotune": (_I, [_P, _P, _U64, _P, _P, _P]),
+    "dfa_get_tuning_opts": (_I, [_P, _P, _P]),
+    "dfa_set_tuning_opts": (_I, [_P, _P, _P]),
+    "dfa_autotune_opts": (_I, [_P, _P, _U64, _P, _P, _P, _P]),
     "dfa_iset": (_I, [_P, _U32, _P, _U32, _P]),
     "dfa_partition": (_I, [_U64, _U32, _U32, _P]),
     "dfa_match": (_I, [_P, _P, _U64, _P, _P]),
@@ -213,29 +216,38 @@ class Dfa:
         _check(lib().dfa_info(self._h, ctypes.byref(out)), "dfa_info")
         return out
 
-    def tuning(self) -> Tuning:
+    def tuning(self, lookahead: int = 1) -> Tuning:
+        """The tuning record used for launches with this lookahead (1: the base record)."""
         t = Tuning()
-        _check(lib().dfa_get_tuning(self._h, ctypes.byref(t)), "dfa_get_tuning")
+        o = _opts(lookahead=lookahead)
+        _check(lib().dfa_get_tuning_opts(self._h, ctypes.byref(o), ctypes.byref(t)),
+               "dfa_get_tuning_opts")
         return t
 
     def set_tuning(self, states_per_thread: int = 0, tiles_per_cta: int = 0,
                    min_chunk_bytes: int = 0, batch_chunk_bytes: int = 0, ctas_per_sm: int = 0,
-                   host_segment_bytes: int = 0):
+                   host_segment_bytes: int = 0, lookahead: int = 1):
         """host_segment_bytes: first segment of dfa_match's copy/match pipeline for
-        host input (0 = automatic, 0xFFFFFFFF = copy the whole string first)."""
+        host input (0 = automatic, 0xFFFFFFFF = copy the whole string first).
+        lookahead: the depth whose record is set (1: the base record)."""
         t = Tuning(states_per_thread, tiles_per_cta, min_chunk_bytes, batch_chunk_bytes, ctas_per_sm,
                    host_segment_bytes)
-        _check(lib().dfa_set_tuning(self._h, ctypes.byref(t)), "dfa_set_tuning")
+        o = _opts(lookahead=lookahead)
+        _check(lib().dfa_set_tuning_opts(self._h, ctypes.byref(o), ctypes.byref(t)),
+               "dfa_set_tuning_opts")
 
-    def autotune(self, dev_sample, stream=None):
-        """Time the candidate tunings on a device sample and keep the fastest.
+    def autotune(self, dev_sample, stream=None, lookahead: int = 1):
+        """Time the candidate tunings on a device sample (launches with this
+        lookahead) and keep the fastest in that lookahead's record.
         Returns (Tuning, best_ms)."""
         t = Tuning()
         ms = ctypes.c_double()
         n = dev_sample.numel()
-        _check(lib().dfa_autotune(self._h, dev_sample.data_ptr() if n else None, n,
-                                  _stream_ptr(stream), ctypes.byref(t), ctypes.byref(ms)),
-               "dfa_autotune")
+        o = _opts(lookahead=lookahead)
+        _check(lib().dfa_autotune_opts(self._h, dev_sample.data_ptr() if n else None, n,
+                                       ctypes.byref(o), _stream_ptr(stream), ctypes.byref(t),
+                                       ctypes.byref(ms)),
+               "dfa_autotune_opts")
         return t, float(ms.value)
 
     def class_of_bytes(self) -> np.ndarray:

@@ -88,7 +88,6 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
 
 // Reverse-lookahead symbols requested by opts: 1 (Algorithm 3) by default,
 // 0 for Algorithm 2, up to kMaxLookahead for Eq. (13).
-constexpr uint32_t kMaxLookahead = 8;
 inline uint32_t opts_lookahead(const dfa_match_opts_t* o) { return o ? o->lookahead : 1u; }
 inline uint32_t seg_stride_for(uint32_t qe_max) { return (qe_max + 1) & ~1u; }
 
@@ -96,6 +95,8 @@ inline uint32_t seg_stride_for(uint32_t qe_max) { return (qe_max + 1) & ~1u; }
 // largest set the launch matches would not fit one tile.
 DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
     DevDfa x = d->dev;
+    const uint32_t tk = d->tuning_for(lookahead).states_per_thread;
+    x.K = tk ? tk : d->h.K;
     const uint32_t vmax = lookahead ? std::max(d->h.imax, 1u) : d->h.qe;
     while ((vmax + x.K - 1) / x.K > (uint32_t)kThreads / 2 && x.K < 16) x.K *= 2;
     x.cost_max = std::max((vmax + x.K - 1) / x.K, 2u);
@@ -106,11 +107,12 @@ DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
 // Chunk count for one test (Sec. 4.1's partition is applied per test with P chunks).
 uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_opts_t* o,
                      bool batched) {
+    const dfa_tuning_t& tu = d->tuning_for(opts_lookahead(o));
     uint64_t P;
     if (o && o->num_chunks) {
         P = o->num_chunks;
     } else if (batched) {
-        uint64_t L = d->tuning.batch_chunk_bytes ? d->tuning.batch_chunk_bytes : kBatchChunk;
+        uint64_t L = tu.batch_chunk_bytes ? tu.batch_chunk_bytes : kBatchChunk;
         P = (n + L - 1) / L;
     } else {
         // enough lane tasks for kTilesPerCta tiles on every CTA, chunks >= kMinChunk
@@ -118,12 +120,13 @@ uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_
         const HostDfa& h = d->h;
         for (uint32_t c = 0; c < h.C; ++c) {
             uint32_t sz = h.iset_off[c + 1] - h.iset_off[c];
-            mean_cost += std::max((sz + h.K - 1) / h.K, 2u);
+            const uint32_t K = tu.states_per_thread ? tu.states_per_thread : h.K;
+            mean_cost += std::max((sz + K - 1) / K, 2u);
         }
         mean_cost = h.C ? mean_cost / h.C : 2.0;
-        const uint32_t tpc = d->tuning.tiles_per_cta ? d->tuning.tiles_per_cta : kTilesPerCta;
+        const uint32_t tpc = tu.tiles_per_cta ? tu.tiles_per_cta : kTilesPerCta;
         double want = (double)grid * kThreads * tpc * 0.9 / mean_cost;
-        uint64_t by_len = n / (d->tuning.min_chunk_bytes ? d->tuning.min_chunk_bytes : kMinChunk);
+        uint64_t by_len = n / (tu.min_chunk_bytes ? tu.min_chunk_bytes : kMinChunk);
         P = std::min<uint64_t>((uint64_t)want, by_len);
     }
     P = std::max<uint64_t>(P, (n + kMaxChunk - 1) / kMaxChunk);
@@ -283,7 +286,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     s->kmax = x.K;
     uint32_t stage = 0;
     s->smem = match_smem_bytes(tcap, x.K, x.vcap, &stage,
-                               match_target_ctas(x.K, d->tuning.ctas_per_sm));
+                               match_target_ctas(x.K, d->tuning_for(lookahead).ctas_per_sm));
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
@@ -331,8 +334,17 @@ using namespace dfam;
 
 // ------------------------------------------------------------------ dfa_t
 
-const DevDfa* dfa_s::dev_desc_for(uint32_t lookahead) const {
-    return lookahead ? dev_desc : dev_desc + 1;
+const DevDfa* dfa_s::dev_desc_for(uint32_t lookahead) const { return dev_desc + lookahead; }
+
+// Uploads the launch descriptors of every lookahead depth (their K follows
+// the depth's tuning record).
+static int upload_descs(dfa_t* d) {
+    if (!d->dev_desc) return DFA_OK;  // a host-only DFA
+    DevDfa descs[kMaxLookahead + 1];
+    for (uint32_t r = 0; r <= kMaxLookahead; ++r) descs[r] = launch_desc(d, r);
+    return cudaMemcpy(d->dev_desc, descs, sizeof descs, cudaMemcpyHostToDevice) == cudaSuccess
+               ? DFA_OK
+               : DFA_ECUDA;
 }
 
 static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0,
@@ -375,7 +387,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         }
         uint64_t o = 0;
         auto take = [&](uint64_t bytes) { uint64_t r = o; o = up(o + bytes, 256); return r; };
-        const uint64_t o_desc = take(2 * sizeof(DevDfa));
+        const uint64_t o_desc = take((kMaxLookahead + 1) * sizeof(DevDfa));
         const uint64_t o_table = take(h.table.size());
         const uint64_t o_b16 = take(512), o_b32 = take(1024), o_bc = take(512);
         const uint64_t o_ioff = take(4 * h.iset_off.size()), o_iset = take(2 * h.iset.size());
@@ -400,8 +412,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         x.excluded = blk + o_exc;
         x.byte_plan = reinterpret_cast<const uint32_t*>(blk + o_bp);
         d->dev_desc = reinterpret_cast<DevDfa*>(blk + o_desc);
-        DevDfa descs[2] = {launch_desc(d, 1), launch_desc(d, 0)};
-        bool ok = cudaMemcpy(blk + o_desc, descs, sizeof descs, cudaMemcpyHostToDevice) == cudaSuccess &&
+        bool ok = upload_descs(d) == DFA_OK &&
                   cudaMemcpy(blk + o_table, h.table.data(), h.table.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_b16, h.byte_off16.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_b32, h.byte_off32.data(), 1024, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -462,37 +473,44 @@ int dfa_info(const dfa_t* d, dfa_info_t* o) {
     return DFA_OK;
 }
 
-int dfa_get_tuning(const dfa_t* d, dfa_tuning_t* out) {
-    if (!d || !out) return DFA_EINVAL;
-    *out = d->tuning;
-    out->states_per_thread = d->h.K;
+// Tuning record of lookahead depth r: the base record for r == 1 (and for
+// depths without their own record when read).
+static int get_tuning_r(const dfa_t* d, uint32_t r, dfa_tuning_t* out) {
+    if (!d || !out || r > kMaxLookahead) return DFA_EINVAL;
+    *out = d->tuning_for(r);
+    if (!out->states_per_thread) out->states_per_thread = d->h.K;
     return DFA_OK;
 }
 
-int dfa_set_tuning(dfa_t* d, const dfa_tuning_t* t) {
-    if (!d || !t) return DFA_EINVAL;
-    uint32_t K = t->states_per_thread ? t->states_per_thread : d->h.K;
+static int set_tuning_r(dfa_t* d, uint32_t r, const dfa_tuning_t* t) {
+    if (!d || !t || r > kMaxLookahead) return DFA_EINVAL;
+    const uint32_t K = t->states_per_thread ? t->states_per_thread : d->h.K;
     if (K != 2 && K != 4 && K != 8 && K != 16) return DFA_EINVAL;
     if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) return DFA_EINVAL;
-    d->tuning = *t;
-    d->tuning.states_per_thread = K;
-    d->h.K = K;
-    d->dev.K = K;
-    if (d->on_device) {
-        DevDfa descs[2] = {launch_desc(d, 1), launch_desc(d, 0)};
-        if (cudaMemcpy(d->dev_desc, descs, sizeof descs, cudaMemcpyHostToDevice) != cudaSuccess)
-            return DFA_ECUDA;
+    dfa_tuning_t v = *t;
+    v.states_per_thread = K;
+    if (r == 1) {
+        d->tuning = v;
+        d->h.K = K;
+        d->dev.K = K;
+    } else {
+        d->tuning_r[r] = v;
+        d->has_tuning_r[r] = true;
     }
-    return DFA_OK;
+    return upload_descs(d);
 }
 
-int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream,
-                 dfa_tuning_t* chosen, double* best_ms) {
-    if (!d || (len && !dev_sample)) return DFA_EINVAL;
+// Times every candidate tuning on a device sample with lookahead r and keeps
+// the fastest in r's record.
+static int autotune_r(dfa_t* d, uint32_t r, const uint8_t* dev_sample, uint64_t len, void* stream,
+                      dfa_tuning_t* chosen, double* best_ms) {
+    if (!d || (len && !dev_sample) || r > kMaxLookahead) return DFA_EINVAL;
     if (!d->on_device) return DFA_EHOSTONLY;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const dfa_tuning_t saved = d->tuning;
-    const uint32_t savedK = d->h.K;
+    dfa_tuning_t saved;
+    get_tuning_r(d, r, &saved);
+    dfa_match_opts_t o{};
+    o.lookahead = r;
     std::vector<dfa_tuning_t> cands;
     for (uint32_t K : {2u, 4u, 8u, 16u}) {
         if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) continue;
@@ -510,16 +528,14 @@ int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream
     // workspace for the largest plan
     uint64_t ws_need = 0;
     for (const dfa_tuning_t& t : cands) {
-        if (dfa_set_tuning(d, &t) != DFA_OK) continue;
+        if (set_tuning_r(d, r, &t) != DFA_OK) continue;
         Single s;
-        if (plan_single(d, len, nullptr, &s) == DFA_OK) ws_need = std::max(ws_need, s.ws.total);
+        if (plan_single(d, len, &o, &s) == DFA_OK) ws_need = std::max(ws_need, s.ws.total);
     }
     uint8_t* ws = nullptr;
     if (cudaMalloc(&ws, ws_need + 256) != cudaSuccess) {
         cudaGetLastError();
-        dfa_tuning_t t = saved;
-        t.states_per_thread = savedK;
-        dfa_set_tuning(d, &t);
+        set_tuning_r(d, r, &saved);
         return DFA_ENOMEM;
     }
     dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(ws + ws_need);
@@ -528,25 +544,24 @@ int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream
     cudaEventCreate(&e1);
     double best = 1e30;
     dfa_tuning_t best_t = saved;
-    best_t.states_per_thread = savedK;
     uint32_t best_P = 1;
     int rc = DFA_OK;
     for (const dfa_tuning_t& t : cands) {
-        if (dfa_set_tuning(d, &t) != DFA_OK) continue;
+        if (set_tuning_r(d, r, &t) != DFA_OK) continue;
         Single s;
-        if (plan_single(d, len, nullptr, &s) != DFA_OK) continue;
+        if (plan_single(d, len, &o, &s) != DFA_OK) continue;
         s.lp.test1.str = dev_sample;
         bind(s.lp, ws, s.ws);
         s.lp.results = dres;
         std::vector<float> ms;
-        for (int r = 0; r < 4 && rc == DFA_OK; ++r) {
+        for (int i = 0; i < 4 && rc == DFA_OK; ++i) {
             cudaEventRecord(e0, st);
             rc = launch_plan(s.lp, s.kmax, s.smem, st, nullptr);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) rc = DFA_ECUDA;
             float x = 0;
             cudaEventElapsedTime(&x, e0, e1);
-            if (r > 0) ms.push_back(x);  // the first launch is a warm-up
+            if (i > 0) ms.push_back(x);  // the first launch is a warm-up
         }
         if (rc != DFA_OK) break;
         std::sort(ms.begin(), ms.end());
@@ -562,11 +577,34 @@ int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream
     cudaFree(ws);
     uint64_t clen = best_P ? len / best_P : kBatchChunk;
     best_t.batch_chunk_bytes = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(clen, 2048), 65536);
-    int rc2 = dfa_set_tuning(d, &best_t);
+    int rc2 = set_tuning_r(d, r, &best_t);
     if (rc == DFA_OK) rc = rc2;
-    if (chosen) *chosen = d->tuning;
+    if (chosen) get_tuning_r(d, r, chosen);
     if (best_ms) *best_ms = best;
     return rc;
+}
+
+int dfa_get_tuning(const dfa_t* d, dfa_tuning_t* out) { return get_tuning_r(d, 1, out); }
+
+int dfa_set_tuning(dfa_t* d, const dfa_tuning_t* t) { return set_tuning_r(d, 1, t); }
+
+int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream,
+                 dfa_tuning_t* chosen, double* best_ms) {
+    return autotune_r(d, 1, dev_sample, len, stream, chosen, best_ms);
+}
+
+int dfa_get_tuning_opts(const dfa_t* d, const dfa_match_opts_t* opts, dfa_tuning_t* out) {
+    return get_tuning_r(d, opts_lookahead(opts), out);
+}
+
+int dfa_set_tuning_opts(dfa_t* d, const dfa_match_opts_t* opts, const dfa_tuning_t* t) {
+    return set_tuning_r(d, opts_lookahead(opts), t);
+}
+
+int dfa_autotune_opts(dfa_t* d, const uint8_t* dev_sample, uint64_t len,
+                      const dfa_match_opts_t* opts, void* stream, dfa_tuning_t* chosen,
+                      double* best_ms) {
+    return autotune_r(d, opts_lookahead(opts), dev_sample, len, stream, chosen, best_ms);
 }
 
 int dfa_class_of_bytes(const dfa_t* d, uint16_t* out) {

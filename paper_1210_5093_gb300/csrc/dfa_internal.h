@@ -19,7 +19,8 @@ constexpr int kMaxSegLen = 2048;         // longest staged segment per chunk (po
 constexpr uint16_t kNone16 = 0xFFFF;     // "not a member" in pos tables / invalid byte
 constexpr uint32_t kNone32 = 0xFFFFFFFFu;
 constexpr uint32_t kSmemTableMax = 112 * 1024;  // tables larger than this are read through L2
-constexpr uint32_t kMaxStates = 4095;    // |Q| limit: a chunk's chains (|I| <= |Q|+1) fit one tile at K=16
+constexpr uint32_t kMaxStates = 4095;
+constexpr uint32_t kMaxLookahead = 8;    // reverse-lookahead symbols r of Eq. (13)    // |Q| limit: a chunk's chains (|I| <= |Q|+1) fit one tile at K=16
 
 enum Placement : uint32_t { kSmem = 0, kGlobal = 1 };
 
@@ -218,7 +219,17 @@ struct dfa_s {
     void* dev_block = nullptr;       // one allocation holding every device array
     uint64_t dev_bytes = 0;
     dfam::DevDfa dev;                // pointers into dev_block
-    dfam::DevDfa* dev_desc = nullptr;  // device copies of `dev` for launches with lookahead 1 and 0
+    // device descriptors for launches with lookahead r = 0 .. kMaxLookahead
+    // (index r), each with the K of that lookahead's tuning
+    dfam::DevDfa* dev_desc = nullptr;
     const dfam::DevDfa* dev_desc_for(uint32_t lookahead) const;
-    dfa_tuning_t tuning{};           // per-DFA tuning record (dfa_set_tuning / dfa_autotune)
+    dfa_tuning_t tuning{};           // base tuning record (dfa_set_tuning / dfa_autotune)
+    // records for one lookahead depth (dfa_set_tuning_opts / dfa_autotune_opts);
+    // a depth without its own record uses the base record
+    dfa_tuning_t tuning_r[dfam::kMaxLookahead + 1]{};
+    bool has_tuning_r[dfam::kMaxLookahead + 1]{};
+    const dfa_tuning_t& tuning_for(uint32_t lookahead) const {
+        return lookahead <= dfam::kMaxLookahead && has_tuning_r[lookahead] ? tuning_r[lookahead]
+                                                                          : tuning;
+    }
 };

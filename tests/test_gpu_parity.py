@@ -430,3 +430,26 @@ def test_chunk_maps_equal_algorithm3(dm, which):
         g2 = got2.astype(np.uint32)
         assert fs2 == efs
         assert np.all((g2 == want) | (g2 == ident))
+
+
+def test_tuning_records_per_lookahead(dm):
+    """A depth's own tuning record changes how its launches are planned, never
+    their answer, and leaves the base record (lookahead 1) alone."""
+    import torch
+    w = gen.regex_workload(4, (3 << 20) + 77)
+    d = dm.Dfa.from_spec(w.spec)
+    dev = torch.from_numpy(w.data).cuda()
+    want = oracle.Dfa.from_spec(w.spec).run(w.data)
+    d.set_tuning(states_per_thread=8, tiles_per_cta=4, min_chunk_bytes=4096)
+    d.set_tuning(states_per_thread=2, tiles_per_cta=16, min_chunk_bytes=512, lookahead=4)
+    d.set_tuning(states_per_thread=16, tiles_per_cta=4, lookahead=0)
+    assert (d.tuning().states_per_thread, d.tuning().tiles_per_cta) == (8, 4)
+    assert (d.tuning(lookahead=4).states_per_thread, d.tuning(lookahead=4).tiles_per_cta) == (2, 16)
+    assert d.tuning(lookahead=2).states_per_thread == 8       # no record of its own: the base
+    assert d.plan_chunks(dev.numel(), lookahead=4) != d.plan_chunks(dev.numel(), lookahead=1)
+    for r in (0, 1, 2, 4):
+        assert d.match(dev, lookahead=r) == want, r
+    t, ms = d.autotune(dev, lookahead=2)
+    assert ms > 0 and d.tuning(lookahead=2).states_per_thread == t.states_per_thread
+    assert d.tuning().states_per_thread == 8
+    assert d.match(dev, lookahead=2) == want
