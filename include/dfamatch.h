@@ -86,7 +86,7 @@ typedef struct {
                                    (0 = 3 when K <= 4, else 2)                          */
     uint32_t host_segment_bytes; /* dfa_match on a host buffer: length of the first
                                    segment of the copy/match pipeline (later segments
-                                   double); 0 = automatic (len/8 clamped to
+                                   double); 0 = automatic (len/32 clamped to
                                    [16 MiB, 256 MiB]), 0xFFFFFFFF = copy the whole
                                    string before matching                              */
 } dfa_tuning_t;
@@ -201,11 +201,13 @@ int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t *starts);
  * (detected with cudaPointerGetAttributes).  Host input of at least two
  * first-segment lengths (dfa_tuning_t.host_segment_bytes) is copied and
  * matched as a pipeline when opts sets neither num_chunks nor multiplicity:
- * segment i+1 is copied on a library-owned copy stream while segment i is
- * matched on a library-owned compute stream, each segment as its own launch
- * whose Eq. (8) merge starts from the previous segment's final state (and
- * whose first chunk takes its reverse lookahead from the previous segment's
- * last bytes), so the answer equals the unsegmented one.  Shorter or
+ * each segment is copied on a library-owned copy stream and matched, once its
+ * copy has landed, as its own launch on one of two library-owned compute
+ * streams (so consecutive launches overlap).  Every segment after the first
+ * takes its first chunk's reverse lookahead from the previous segment's last
+ * bytes and yields the state map of the whole segment; a final kernel applies
+ * those maps to the first segment's final state (Eq. 8), so the answer equals
+ * the unsegmented one.  Shorter or
  * explicitly partitioned host input is copied whole first.  The copies
  * overlap only when the host buffer is pinned.  Device staging buffer,
  * workspace and streams are kept per device between calls (grown on demand;

@@ -746,9 +746,10 @@ struct SyncBuffers {
     uint64_t str_cap = 0;
     uint8_t* ws = nullptr;
     uint64_t ws_cap = 0;
-    cudaStream_t ks = nullptr;  // compute stream of the host pipeline
-    cudaStream_t cs = nullptr;  // copy stream of the host pipeline
-    std::vector<cudaEvent_t> ev;  // one "segment copied" event per segment
+    cudaStream_t ks[2] = {nullptr, nullptr};  // compute streams of the host pipeline
+    cudaStream_t cs = nullptr;                 // copy stream of the host pipeline
+    cudaEvent_t join = nullptr;                // the second compute stream's last launch
+    std::vector<cudaEvent_t> ev;               // one "segment copied" event per segment
 };
 static SyncBuffers g_sync[64];
 
@@ -761,7 +762,7 @@ static SyncBuffers g_sync[64];
 static bool host_segments(uint64_t len, uint32_t first_bytes, std::vector<uint64_t>* seg) {
     constexpr uint64_t kMin = 16ull << 20, kMax = 256ull << 20;
     if (first_bytes == 0xFFFFFFFFu) return false;
-    uint64_t first = first_bytes ? first_bytes : std::min(kMax, std::max(kMin, len / 8));
+    uint64_t first = first_bytes ? first_bytes : std::min(kMax, std::max(kMin, len / 32));
     if (first < 4096 || len < 2 * first) return false;
     seg->clear();
     uint64_t pos = 0, next = first;
@@ -776,9 +777,10 @@ static bool host_segments(uint64_t len, uint32_t first_bytes, std::vector<uint64
 }
 
 static int pipeline_resources(SyncBuffers& B, size_t nseg) {
-    if (!B.ks && cudaStreamCreateWithFlags(&B.ks, cudaStreamNonBlocking) != cudaSuccess)
-        return DFA_ECUDA;
-    if (!B.cs && cudaStreamCreateWithFlags(&B.cs, cudaStreamNonBlocking) != cudaSuccess)
+    for (cudaStream_t* s : {&B.ks[0], &B.ks[1], &B.cs})
+        if (!*s && cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess)
+            return DFA_ECUDA;
+    if (!B.join && cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming) != cudaSuccess)
         return DFA_ECUDA;
     while (B.ev.size() < nseg) {
         cudaEvent_t e = nullptr;
@@ -811,10 +813,12 @@ int dfa_plan_chunks(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, 
     return DFA_OK;
 }
 
-// Host input in segments: segment i is copied on B.cs and matched on B.ks
-// once its copy has landed; segments after the first are continuation tests
-// (kTestCont), so each launch's merge picks up the previous final state from
-// the shared result slot.  The launches reuse one workspace in stream order.
+// Host input in segments: segment i is copied on B.cs and matched once its
+// copy has landed, on compute stream i % 2 with its own workspace, so the
+// tail of one launch overlaps the start of the next.  Segment 0 is a plain
+// test; later segments are map tests (kTestCont | kTestMap) that need nothing
+// from the launches before them, and k_compose_segments applies their maps
+// to segment 0's final state (Eq. 8) once both streams are done.
 static int match_pipelined(const dfa_t* d, const uint8_t* str, const std::vector<uint64_t>& seg,
                            const dfa_match_opts_t* opts, SyncBuffers& B, dfa_result_t* out) {
     const size_t ns = seg.size();
@@ -828,29 +832,44 @@ static int match_pipelined(const dfa_t* d, const uint8_t* str, const std::vector
     }
     int rc = pipeline_resources(B, ns);
     if (rc != DFA_OK) return rc;
+    const uint32_t stride = (d->h.qe + 1) & ~1u;
+    const uint64_t res_off = 2 * ws_need, map_off = up(res_off + sizeof(dfa_result_t) * (ns + 1), 256);
     if ((rc = grow_dev(&B.str, &B.str_cap, len)) != DFA_OK) return rc;
-    if ((rc = grow_dev(&B.ws, &B.ws_cap, ws_need + 256)) != DFA_OK) return rc;
-    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(B.ws + ws_need);
+    if ((rc = grow_dev(&B.ws, &B.ws_cap, map_off + 2ull * stride * ns + 256)) != DFA_OK) return rc;
+    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(B.ws + res_off);  // [ns] + the answer
+    uint16_t* maps = reinterpret_cast<uint16_t*>(B.ws + map_off);
     uint64_t pos = 0;
     for (size_t i = 0; i < ns; ++i) {
+        cudaStream_t ks = B.ks[i & 1];
         if (cudaMemcpyAsync(B.str + pos, str + pos, seg[i], cudaMemcpyHostToDevice, B.cs) !=
                 cudaSuccess ||
             cudaEventRecord(B.ev[i], B.cs) != cudaSuccess ||
-            cudaStreamWaitEvent(B.ks, B.ev[i], 0) != cudaSuccess)
+            cudaStreamWaitEvent(ks, B.ev[i], 0) != cudaSuccess)
             return DFA_ECUDA;
         Single& s = plan[i];
         s.lp.test1.str = B.str + pos;
-        s.lp.test1.flags = i ? kTestCont : 0u;
-        bind(s.lp, B.ws, s.ws);
-        s.lp.results = dres;
-        rc = launch_plan(s.lp, s.kmax, s.smem, B.ks, nullptr,
-                         (opts && i == 0) ? opts->match_begin_event : nullptr,
-                         (opts && i + 1 == ns) ? opts->match_end_event : nullptr);
+        s.lp.test1.flags = i ? (kTestCont | kTestMap) : 0u;
+        bind(s.lp, B.ws + (i & 1) * ws_need, s.ws);
+        s.lp.results = dres + i;
+        s.lp.maps = maps + i * stride;
+        s.lp.map_stride = stride;
+        rc = launch_plan(s.lp, s.kmax, s.smem, ks, nullptr,
+                         (opts && i == 0) ? opts->match_begin_event : nullptr, nullptr);
         if (rc != DFA_OK) return rc;
         pos += seg[i];
     }
-    if (cudaMemcpyAsync(out, dres, sizeof *out, cudaMemcpyDeviceToHost, B.ks) != cudaSuccess ||
-        cudaStreamSynchronize(B.ks) != cudaSuccess)
+    if (cudaEventRecord(B.join, B.ks[1]) != cudaSuccess ||
+        cudaStreamWaitEvent(B.ks[0], B.join, 0) != cudaSuccess)
+        return DFA_ECUDA;
+    if ((rc = launch_compose_segments(dres, maps, stride, (uint32_t)ns, d->dev.accept, dres + ns,
+                                      B.ks[0])) != DFA_OK)
+        return rc;
+    if (opts && opts->match_end_event &&
+        cudaEventRecord(static_cast<cudaEvent_t>(opts->match_end_event), B.ks[0]) != cudaSuccess)
+        return DFA_ECUDA;
+    if (cudaMemcpyAsync(out, dres + ns, sizeof *out, cudaMemcpyDeviceToHost, B.ks[0]) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(B.ks[0]) != cudaSuccess)
         return DFA_ECUDA;
     return out->status != DFA_OK ? out->status : DFA_OK;
 }

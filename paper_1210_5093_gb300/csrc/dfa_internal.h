@@ -72,7 +72,7 @@ struct DevTest {
     uint32_t group;       // run of consecutive tests sharing one DFA
     uint32_t lookahead;   // 1: Algorithm 3, 0: Algorithm 2 (all states)
     uint32_t out;         // index of its result in the caller's output array
-    uint32_t flags;       // kTestCont
+    uint32_t flags;       // kTestCont, kTestMap
     uint64_t pad_;
 };
 static_assert(sizeof(DevTest) == 64, "DevTest layout");
@@ -87,6 +87,12 @@ inline uint64_t recip64(uint64_t q) { return ~0ull / q; }
 // (reverse lookahead into the previous segment), and Eq. (8) starts from the
 // final state (and status) already in its result slot instead of q0.
 constexpr uint32_t kTestCont = 1;
+// A map test (always also a continuation) publishes the state map of its
+// whole string instead of a final state: map[s] = delta*(s, str) for every s
+// that can enter it (the reverse-lookahead set of its first chunk and the
+// excluded states; other entries are the identity), written to
+// LaunchPlan::maps + out * map_stride.  Its result slot gets only the status.
+constexpr uint32_t kTestMap = 2;
 
 struct DevGroup {
     uint32_t first_chunk, end_chunk, dfa, first_test;
@@ -143,6 +149,8 @@ struct LaunchPlan {
     uint16_t* dbg_maps;         // optional [ptot * qe_max]: chunk maps L_k (identity pre-filled)
     uint32_t qe_max;            // largest |Q|+1 of the launch's DFAs
     dfa_result_t* results;      // [ntests] in the caller's order (DevTest::out)
+    uint16_t* maps;             // map tests: their state maps, map_stride entries each
+    uint32_t map_stride;
     // single-test launches carry their descriptors by value (tests/groups == nullptr)
     DevTest test1;
     DevGroup group1;
@@ -209,6 +217,10 @@ struct Single {
 int plan_single(const dfa_s* d, uint64_t len, const dfa_match_opts_t* opts, Single* s);
 void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w);
 int launch_single(const Single& s, void* stream, void* ev_begin, void* ev_end);
+// Eq. (8) over the segments of one string: the first segment's result, then
+// the state maps of the map tests that follow it (one thread, on `st`).
+int launch_compose_segments(const dfa_result_t* seg_res, const uint16_t* maps, uint32_t stride,
+                            uint32_t nseg, const uint8_t* accept, dfa_result_t* out, void* st);
 }  // namespace dfam
 
 // The opaque handle of the C ABI.

@@ -892,6 +892,66 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
     }
 }
 
+// Stages segment maps i0 .. i0+nb-1 of test t (CTAs b0 + i0 + j) into sm,
+// words u32 words each; a CTA without a share contributes the identity.
+__device__ __forceinline__ void stage_seg_maps(const LaunchPlan& lp, uint32_t t, uint32_t b0,
+                                               uint32_t i0, uint32_t nb, uint32_t words,
+                                               uint32_t* sm) {
+    for (uint32_t k = threadIdx.x; k < nb * words; k += kThreads) {
+        const uint32_t j = k / words, w = k - j * words;
+        const uint32_t cb = b0 + i0 + j;
+        // a CTA between the test's first and last CTA either holds a part
+        // of it or got no share at all (then its map is the identity)
+        if (__ldcg(lp.cta_range + 2 * cb) == __ldcg(lp.cta_range + 2 * cb + 1)) {
+            sm[j * words + w] = (2 * w) | ((2 * w + 1) << 16);
+            continue;
+        }
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(
+            lp.seg_vals + (size_t)(cb + t) * lp.seg_stride);
+        sm[j * words + w] = __ldcg(src + w);
+    }
+}
+
+constexpr uint32_t kMapStatesPerThread = (kMaxStates + 1 + kThreads - 1) / kThreads;
+
+// Map test: compose the whole segment maps (Eq. 9) for every state at once;
+// thread x follows states x, x + kThreads, ... through the maps in order.
+__device__ void combine_test_map(const LaunchPlan& lp, uint32_t t, const DevTest& tt,
+                                 const DevDfa& d, uint32_t b0, uint32_t nseg, uint32_t* sm,
+                                 uint32_t per, uint32_t words) {
+    const uint32_t qe = d.qe;
+    uint32_t cur[kMapStatesPerThread];
+#pragma unroll
+    for (uint32_t i = 0; i < kMapStatesPerThread; ++i) cur[i] = threadIdx.x + i * kThreads;
+    for (uint32_t i0 = 0; i0 < nseg; i0 += per) {
+        const uint32_t nb = min(per, nseg - i0);
+        __syncthreads();
+        stage_seg_maps(lp, t, b0, i0, nb, words, sm);
+        __syncthreads();
+        const uint16_t* m = reinterpret_cast<const uint16_t*>(sm);
+        for (uint32_t j = 0; j < nb; ++j) {
+#pragma unroll
+            for (uint32_t i = 0; i < kMapStatesPerThread; ++i)
+                if (cur[i] < qe) cur[i] = m[(size_t)j * 2 * words + cur[i]];
+        }
+    }
+    uint16_t* out = lp.maps + (size_t)tt.out * lp.map_stride;
+#pragma unroll
+    for (uint32_t i = 0; i < kMapStatesPerThread; ++i) {
+        const uint32_t x = threadIdx.x + i * kThreads;
+        if (x < qe) out[x] = (uint16_t)cur[i];
+    }
+    if (threadIdx.x == 0) {
+        dfa_result_t r;
+        r.final_state = 0;
+        r.accept = 0;
+        r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
+        r.status = atomicOr(lp.test_err + t, 0u) ? DFA_ESYMBOL : DFA_OK;
+        lp.results[tt.out] = r;
+    }
+    __syncthreads();
+}
+
 // Final state of test t from its segment maps (slots b + t for b in
 // [first_cta, last_cta]), applied in order to q0: Eq. (8) segment by segment.
 // Each segment map is dense over Q (identity outside its domain), so one
@@ -911,23 +971,15 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
     // a continuation segment starts from the previous segment's final state;
     // that launch ran earlier on the same stream, so its result is complete
     const bool cont = (tt.flags & kTestCont) != 0;
+    if (tt.flags & kTestMap) {
+        combine_test_map(lp, t, tt, d, b0, nseg, sm, per, words);
+        return;
+    }
     if (threadIdx.x == 0) *cell = cont ? lp.results[tt.out].final_state : d.q0;
     for (uint32_t i0 = 0; i0 < nseg; i0 += per) {
         const uint32_t nb = min(per, nseg - i0);
         __syncthreads();
-        for (uint32_t k = threadIdx.x; k < nb * words; k += kThreads) {
-            const uint32_t j = k / words, w = k - j * words;
-            const uint32_t cb = b0 + i0 + j;
-            // a CTA between the test's first and last CTA either holds a part
-            // of it or got no share at all (then its map is the identity)
-            if (__ldcg(lp.cta_range + 2 * cb) == __ldcg(lp.cta_range + 2 * cb + 1)) {
-                sm[j * words + w] = (2 * w) | ((2 * w + 1) << 16);
-                continue;
-            }
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(
-                lp.seg_vals + (size_t)(cb + t) * lp.seg_stride);
-            sm[j * words + w] = __ldcg(src + w);
-        }
+        stage_seg_maps(lp, t, b0, i0, nb, words, sm);
         __syncthreads();
         if (threadIdx.x == 0) {
             uint32_t s = *cell;
@@ -1244,6 +1296,33 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
     if (kmax > 8) return grid_for<16, 2>(smem, grid);
     if (kmax > 4) return grid_for<8, 2>(smem, grid);
     return grid_for<4, 3>(smem, grid);
+}
+
+// Eq. (8) over the segments of one string: seg_res[0] is the first
+// segment's result, segments 1 .. nseg-1 are map tests.
+__global__ void k_compose_segments(const dfa_result_t* seg_res, const uint16_t* maps,
+                                   uint32_t stride, uint32_t nseg, const uint8_t* accept,
+                                   dfa_result_t* out) {
+    if (threadIdx.x != 0) return;
+    uint32_t s = seg_res[0].final_state;
+    bool err = seg_res[0].status != DFA_OK;
+    for (uint32_t i = 1; i < nseg; ++i) {
+        err |= seg_res[i].status != DFA_OK;
+        if (!err) s = maps[(size_t)i * stride + s];
+    }
+    dfa_result_t r;
+    r.final_state = err ? 0u : s;
+    r.accept = err ? 0 : accept[s];
+    r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
+    r.status = err ? DFA_ESYMBOL : DFA_OK;
+    *out = r;
+}
+
+int launch_compose_segments(const dfa_result_t* seg_res, const uint16_t* maps, uint32_t stride,
+                            uint32_t nseg, const uint8_t* accept, dfa_result_t* out, void* st) {
+    k_compose_segments<<<1, 32, 0, static_cast<cudaStream_t>(st)>>>(seg_res, maps, stride, nseg,
+                                                                    accept, out);
+    return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
 }
 
 uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn) {
