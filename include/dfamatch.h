@@ -151,8 +151,10 @@ int dfa_set_tuning(dfa_t *dfa, const dfa_tuning_t *tuning);
  * (len bytes) for every allowed K in {2, 4, 8, 16}, tiles-per-CTA in
  * {4, 8, 16} and, for K <= 4, 2 or 3 CTAs per SM (median of 3 timed
  * launches each, CUDA events on `stream`),
- * keeps the fastest as the DFA's tuning record and returns it in *chosen and
- * its time in *best_ms (either may be NULL).  The batched chunk length is set
+ * keeps the fastest as the DFA's tuning record (of the candidates within 1%
+ * of the fastest, the one with the most CTAs per SM: more, smaller CTAs let
+ * consecutive or concurrent launches share the SMs) and returns it in
+ * *chosen and its time in *best_ms (either may be NULL).  The batched chunk length is set
  * to the chosen single-test chunk length, clamped to [2 KiB, 64 KiB].
  * Allocates a temporary workspace; synchronises the stream.
  */

@@ -542,11 +542,14 @@ static int autotune_r(dfa_t* d, uint32_t r, const uint8_t* dev_sample, uint64_t 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    double best = 1e30;
-    dfa_tuning_t best_t = saved;
-    uint32_t best_P = 1;
+    // median time per candidate; among those within 1% of the fastest the one
+    // with the most CTAs per SM wins (more, smaller CTAs also let consecutive
+    // or concurrent launches share the SMs, as in the host pipeline)
+    std::vector<double> med_ms(cands.size(), 1e30);
+    std::vector<uint32_t> cand_P(cands.size(), 1);
     int rc = DFA_OK;
-    for (const dfa_tuning_t& t : cands) {
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        const dfa_tuning_t& t = cands[ci];
         if (set_tuning_r(d, r, &t) != DFA_OK) continue;
         Single s;
         if (plan_single(d, len, &o, &s) != DFA_OK) continue;
@@ -565,16 +568,28 @@ static int autotune_r(dfa_t* d, uint32_t r, const uint8_t* dev_sample, uint64_t 
         }
         if (rc != DFA_OK) break;
         std::sort(ms.begin(), ms.end());
-        const double med = ms[ms.size() / 2];
-        if (med < best) {
-            best = med;
-            best_t = t;
-            best_P = s.lp.ptot;
-        }
+        med_ms[ci] = ms[ms.size() / 2];
+        cand_P[ci] = s.lp.ptot;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(ws);
+    double best = 1e30;
+    for (double m : med_ms) best = std::min(best, m);
+    dfa_tuning_t best_t = saved;
+    uint32_t best_P = 1;
+    int pick = -1;
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        if (med_ms[ci] > best * 1.01) continue;
+        if (pick < 0 || cands[ci].ctas_per_sm > cands[pick].ctas_per_sm ||
+            (cands[ci].ctas_per_sm == cands[pick].ctas_per_sm && med_ms[ci] < med_ms[pick]))
+            pick = (int)ci;
+    }
+    if (pick >= 0) {
+        best_t = cands[pick];
+        best_P = cand_P[pick];
+        best = med_ms[pick];
+    }
     uint64_t clen = best_P ? len / best_P : kBatchChunk;
     best_t.batch_chunk_bytes = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(clen, 2048), 65536);
     int rc2 = set_tuning_r(d, r, &best_t);
