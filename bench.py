@@ -473,6 +473,17 @@ def main():
     for _ in range(e2e_steps):
         d.match(pinned)
     e2e_s = (time.perf_counter() - te) / e2e_steps
+    # context: this box's plain host-to-device copy rate (the pipelined host
+    # path cannot run faster than the copies that feed it)
+    h2d_buf = torch.empty(n, dtype=torch.uint8, device="cuda")
+    h2d_buf.copy_(pinned, non_blocking=True)
+    torch.cuda.synchronize()
+    th = time.perf_counter()
+    for _ in range(3):
+        h2d_buf.copy_(pinned, non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * n / (time.perf_counter() - th) / 1e9
+    del h2d_buf
     if world > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -514,7 +525,7 @@ def main():
                              "peak_source": peak_src},
             "e2e": {"value": round(n * world / e2e_s / 1e9, 3), "unit": "GB/s",
                     "h2d_bytes_per_step": n, "d2h_bytes_per_step": 12,
-                    "api": "dfa_match (pinned host buffer)"},
+                    "api": "dfa_match (pinned host buffer)", "h2d_copy_gbs": round(h2d_gbs, 1)},
             "gpu_launches": d.num_kernels(n, num_chunks=w.num_chunks) * args.steps,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"]},

@@ -149,13 +149,17 @@ int dfa_set_tuning(dfa_t *dfa, const dfa_tuning_t *tuning);
 /*
  * Autotuner: times single-test launches of the device string dev_sample
  * (len bytes) for every allowed K in {2, 4, 8, 16}, tiles-per-CTA in
- * {4, 8, 16} and, for K <= 4, 2 or 3 CTAs per SM (median of 3 timed
- * launches each, CUDA events on `stream`),
+ * {4, 8, 16} and, for K <= 4, 2 or 3 CTAs per SM, plus shortest chunks of
+ * 2 and 8 KiB where the default shortest chunk bounds the chunk count
+ * (median of 3 timed launches each, CUDA events on `stream`),
  * keeps the fastest as the DFA's tuning record (of the candidates within 1%
  * of the fastest, the one with the most CTAs per SM: more, smaller CTAs let
  * consecutive or concurrent launches share the SMs) and returns it in
- * *chosen and its time in *best_ms (either may be NULL).  The batched chunk length is set
- * to the chosen single-test chunk length, clamped to [2 KiB, 64 KiB].
+ * *chosen and its time in *best_ms (either may be NULL).  The batched chunk
+ * length is set to the chosen single-test chunk length, clamped to
+ * [8 KiB, 64 KiB].  Launches of several DFAs (batches, the server) use each
+ * DFA's compiler K capped at 8 rather than the tuned K: one kernel variant
+ * serves the whole launch.
  * Allocates a temporary workspace; synchronises the stream.
  */
 int dfa_autotune(dfa_t *dfa, const uint8_t *dev_sample, uint64_t len, void *stream,

@@ -25,7 +25,11 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
 
 constexpr uint32_t kTilesPerCta = 8;       // persistent CTAs each get about this many tiles
 constexpr uint64_t kMinChunk = 512;        // bytes; shorter chunks cost more in tile overhead
+constexpr uint32_t kBatchSmemTable = 64 * 1024;  // largest shared-memory table in a multi-DFA launch
+constexpr uint32_t kBatchKMax = 8;                // largest K in a multi-DFA launch, unless needed
 constexpr uint64_t kBatchChunk = 8192;     // default chunk length for batched tests
+constexpr uint64_t kBatchChunksTarget = 65536;  // chunks a batched launch aims for at least
+constexpr uint64_t kBatchChunkMin = 2048;       // shortest batched chunk
 constexpr uint64_t kMaxChunk = 1ull << 31; // chunk lengths are 32-bit on the device
 
 inline uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -104,15 +108,19 @@ DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
     return x;
 }
 
-// Chunk count for one test (Sec. 4.1's partition is applied per test with P chunks).
+// Chunk count for one test (Sec. 4.1's partition is applied per test with P
+// chunks).  Batched tests use the DFA's batched chunk length, at most
+// batch_cap bytes (the launch's bytes spread over kBatchChunksTarget chunks):
+// a launch holding little input gets shorter chunks and so more parallelism.
 uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_opts_t* o,
-                     bool batched) {
+                     bool batched, uint64_t batch_cap) {
     const dfa_tuning_t& tu = d->tuning_for(opts_lookahead(o));
     uint64_t P;
     if (o && o->num_chunks) {
         P = o->num_chunks;
     } else if (batched) {
         uint64_t L = tu.batch_chunk_bytes ? tu.batch_chunk_bytes : kBatchChunk;
+        if (batch_cap) L = std::min(L, batch_cap);
         P = (n + L - 1) / L;
     } else {
         // enough lane tasks for kTilesPerCta tiles on every CTA, chunks >= kMinChunk
@@ -158,6 +166,23 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
     }
     for (const dfa_t* d : uniq) {
         DevDfa x = launch_desc(d, lookahead);
+        if (uniq.size() > 1) {
+            // One launch has one kernel variant and one shared-memory layout,
+            // sized for its largest K and largest shared-memory table.  In a
+            // launch of several DFAs each DFA takes the compiler's K (from its
+            // mean set size; a single-test tuning says little about a mixed
+            // launch), capped at kBatchKMax unless a chunk's chains need more
+            // to fit a tile, and a table above kBatchSmemTable is read through
+            // L2, so that one DFA does not cut the occupancy of every other test.
+            if (x.placement == kSmem && x.table_bytes > kBatchSmemTable) {
+                x.placement = kGlobal;
+                x.stage_fmt = kOff32;
+            }
+            uint32_t K = std::min(d->h.K0, kBatchKMax);
+            while ((x.vcap + K - 1) / K > (uint32_t)kThreads / 2) K *= 2;
+            x.K = K;
+            x.cost_max = std::max((x.vcap + K - 1) / K, 2u);
+        }
         p.dfas.push_back(x);
         p.kmax = std::max(p.kmax, x.K);
         p.vcap = std::max(p.vcap, x.vcap);
@@ -167,6 +192,9 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
     p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap, &p.stage, match_target_ctas(p.kmax, 0));
     int rc = match_grid(p.smem, p.kmax, &p.grid);
     if (rc != DFA_OK) return rc;
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < count; ++i) total += lens[i];
+    const uint64_t batch_cap = std::max<uint64_t>(kBatchChunkMin, total / kBatchChunksTarget);
     std::vector<uint32_t> order(count);
     for (uint32_t i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
@@ -179,7 +207,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         t.str = strs[i];
         t.n = lens[i];
         t.dfa = idx[d];
-        t.P = plan_chunks(d, lens[i], p.grid, opts, batched);
+        t.P = plan_chunks(d, lens[i], p.grid, opts, batched, batch_cap);
         t.m = m;
         t.qinv = recip64((uint64_t)m + t.P - 1);
         t.chunk_base = (uint32_t)chunks;
@@ -290,7 +318,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
-    const uint32_t P = plan_chunks(d, len, grid, opts, false);
+    const uint32_t P = plan_chunks(d, len, grid, opts, false, 0);
     LaunchPlan& lp = s->lp;
     std::memset(&lp, 0, sizeof lp);
     lp.ntests = 1;
@@ -525,6 +553,23 @@ static int autotune_r(dfa_t* d, uint32_t r, const uint8_t* dev_sample, uint64_t 
             }
         }
     }
+    // Where the chunk count is bound by the shortest chunk (sets so small that
+    // filling the CTAs would need ever shorter chunks), longer chunks are tried
+    // too: per-chunk work (metadata, composition) then stops dominating.
+    const size_t nbase = cands.size();
+    for (size_t ci = 0; ci < nbase; ++ci) {
+        const uint32_t min_chunk = cands[ci].min_chunk_bytes ? cands[ci].min_chunk_bytes : kMinChunk;
+        Single s;
+        if (set_tuning_r(d, r, &cands[ci]) != DFA_OK || plan_single(d, len, &o, &s) != DFA_OK)
+            continue;
+        if (s.lp.ptot < std::max<uint64_t>(len / min_chunk, 1)) continue;
+        for (uint32_t mc : {2048u, 8192u}) {
+            if (mc <= min_chunk) continue;
+            dfa_tuning_t t = cands[ci];
+            t.min_chunk_bytes = mc;
+            cands.push_back(t);
+        }
+    }
     // workspace for the largest plan
     uint64_t ws_need = 0;
     for (const dfa_tuning_t& t : cands) {
@@ -591,7 +636,8 @@ static int autotune_r(dfa_t* d, uint32_t r, const uint8_t* dev_sample, uint64_t 
         best = med_ms[pick];
     }
     uint64_t clen = best_P ? len / best_P : kBatchChunk;
-    best_t.batch_chunk_bytes = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(clen, 2048), 65536);
+    // batched launches: chunks of 8-32 KiB measure best on the 64-DFA mix
+    best_t.batch_chunk_bytes = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(clen, 8192), 65536);
     int rc2 = set_tuning_r(d, r, &best_t);
     if (rc == DFA_OK) rc = rc2;
     if (chosen) get_tuning_r(d, r, chosen);

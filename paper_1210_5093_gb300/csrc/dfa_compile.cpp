@@ -137,10 +137,12 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
             if (h.sb == 1) h.table[at] = (uint8_t)v;
             else { h.table[at] = (uint8_t)(v & 0xFF); h.table[at + 1] = (uint8_t)(v >> 8); }
         }
-    // Shared-memory placement needs 16-bit row offsets (kNone16 reserved) and a
-    // table that leaves room for the rest of the CTA's shared memory.
+    // Shared-memory placement needs a table that leaves room for the rest of
+    // the CTA's shared memory, and a way to address its rows from the staged
+    // input: 8-bit class indices (at most 254 classes, 255 marks a byte
+    // outside Sigma) or else 16-bit row offsets (kNone16 reserved).
     bool fits16 = (uint64_t)C * h.qpad * h.sb < kNone16;
-    h.placement = (fits16 && tbytes <= kSmemTableMax) ? kSmem : kGlobal;
+    h.placement = (tbytes <= kSmemTableMax && (C + 1 <= 255 || fits16)) ? kSmem : kGlobal;
     h.byte_off16.assign(256, kNone16);
     h.byte_off32.assign(256, kNone32);
     for (int b = 0; b < 256; ++b) {
@@ -156,6 +158,7 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
     // a chunk's chains must fit in one tile: ceil(I_max/K) <= kThreads/2
     // (launches of Algorithm 2, which match all of Q, raise K further)
     while ((std::max(h.imax, 1u) + h.K - 1) / h.K > (uint32_t)kThreads / 2 && h.K < 16) h.K *= 2;
+    h.K0 = h.K;
     if ((qe + 15) / 16 > (uint32_t)kThreads / 2) return DFA_EINVAL;
     *out = std::move(h);
     return DFA_OK;

@@ -177,6 +177,7 @@ struct Prepared {
 struct HostDfa {
     uint32_t Q = 0, S = 0, qe = 0, q0 = 0, C = 0, qpad = 0, sb = 0;
     uint32_t imax = 0, num_excluded = 0, placement = kSmem, K = 4;
+    uint32_t K0 = 4;  // the compiler's K (from the mean set size), kept when tuning changes K
     double gamma = 0, mean_iset = 0;
     std::vector<uint16_t> byte_class;   // 256, kNone16 = not in Sigma
     std::vector<uint8_t> accept;        // qe

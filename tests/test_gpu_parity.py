@@ -453,3 +453,17 @@ def test_tuning_records_per_lookahead(dm):
     assert ms > 0 and d.tuning(lookahead=2).states_per_thread == t.states_per_thread
     assert d.tuning().states_per_thread == 8
     assert d.match(dev, lookahead=2) == want
+
+
+def test_smem_table_beyond_16bit_row_offsets(dm):
+    """A 32-class, 1288-state table (85 KB, row offsets above 16 bits) stays in
+    shared memory: the 8-bit class stream addresses its rows without offsets."""
+    spec = gen.class_dfa(93, 1288, 32, 0.02, 0.4, 12, "byte")
+    d = dm.Dfa.from_spec(spec)
+    info = d.info()
+    assert info.placement == 0 and info.num_classes == 32 and info.state_bytes == 2
+    assert 32 * 1288 * 2 > 0xFFFF
+    data = gen.zipf_text(94, 5 << 20)
+    for P in (0, 1, 7, 4000):
+        for r in (0, 1, 3):
+            _check(dm, d, spec, data, num_chunks=P, lookahead=r)
