@@ -103,7 +103,6 @@ DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
     x.K = tk ? tk : d->h.K;
     const uint32_t vmax = lookahead ? std::max(d->h.imax, 1u) : d->h.qe;
     while ((vmax + x.K - 1) / x.K > (uint32_t)kThreads / 2 && x.K < 16) x.K *= 2;
-    x.cost_max = std::max((vmax + x.K - 1) / x.K, 2u);
     x.vcap = vmax;
     return x;
 }
@@ -181,7 +180,6 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
             uint32_t K = std::min(d->h.K0, kBatchKMax);
             while ((x.vcap + K - 1) / K > (uint32_t)kThreads / 2) K *= 2;
             x.K = K;
-            x.cost_max = std::max((x.vcap + K - 1) / K, 2u);
         }
         p.dfas.push_back(x);
         p.kmax = std::max(p.kmax, x.K);

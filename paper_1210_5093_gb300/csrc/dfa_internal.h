@@ -47,7 +47,6 @@ struct DevDfa {
     uint32_t q0;
     uint32_t imax;               // Eq. (12) over real classes
     uint32_t K;                  // states per thread
-    uint32_t cost_max;           // max thread slots one chunk can need: max(ceil(|I|/K), 2)
     uint32_t vcap;               // largest set size (incl. start set) = capacity of a state map
     uint32_t stage_fmt;          // StageFmt of the staged input stream
     uint32_t n_all;              // |Q| minus the excluded states: the set Algorithm 2 matches
@@ -126,7 +125,7 @@ struct LaunchPlan {
     uint32_t* chunk_test;       // [ptot]
     uint16_t* chunk_cls;        // [ptot]
     uint32_t* cost;             // [ptot] packing word (thread slots, opens-a-tile flag);
-                                // then scratch for the tile starts of each packing window
+                                // then scratch for the tile starts of each CTA share
     uint32_t* off;              // [ptot+1] exclusive prefix of cost (within the launch)
     uint64_t* wk;               // [ptot+1] scratch: chunk work (slots x length) or its midpoint
     uint32_t* bsum;             // [nblk+1]
