@@ -49,7 +49,7 @@ def _workload(name: str, seed: int, nbytes: int = 0):
     if name == "plain":
         return gen.plain_workload(seed, nbytes or (4 << 20))
     if name == "protein":
-        return gen.protein_workload(seed, nbytes or 2 * 10**9)
+        return gen.protein_workload(seed, nbytes or 10 * 10**9)
     return gen.regex_workload(seed, nbytes or (1 << 30))
 
 
@@ -420,7 +420,7 @@ def main():
         d.set_tuning(states_per_thread=k, tiles_per_cta=tpc, ctas_per_sm=cps)
         tuning = {"states_per_thread": k, "tiles_per_cta": tpc, "ctas_per_sm": cps, "fixed": True}
     elif not w.num_chunks and not args.no_tune:
-        t, _ = d.autotune(dev)          # the library's per-DFA tuner, before any timing
+        t, _ = d.autotune(dev[: 1 << 30])  # the library's per-DFA tuner (on at most 1 GiB), before any timing
         tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
                   "ctas_per_sm": t.ctas_per_sm}
     P = d.plan_chunks(n, num_chunks=w.num_chunks)
@@ -537,7 +537,7 @@ def main():
             for r in (2, 4):
                 tr = None
                 if not args.tuning and not args.no_tune:
-                    t, _ = d.autotune(dev, lookahead=r)   # this depth's own tuning record
+                    t, _ = d.autotune(dev[: 1 << 30], lookahead=r)   # this depth's own tuning record
                     tr = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
                           "ctas_per_sm": t.ctas_per_sm}
                 kb2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]

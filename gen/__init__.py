@@ -448,11 +448,11 @@ def protein_workload(seed: int = 3, n: int = 10 * 10**9, words=None) -> Workload
 
 
 def _size_name(n: int) -> str:
+    if n >= 10**9 and n % 10**9 == 0:
+        return "%dGB" % (n // 10**9)
     for unit_, nm in ((1 << 30, "GiB"), (1 << 20, "MiB"), (1 << 10, "KiB")):
         if n >= unit_ and n % unit_ == 0:
             return "%d%s" % (n // unit_, nm)
-    if n >= 10**9 and n % 10**9 == 0:
-        return "%dGB" % (n // 10**9)
     return "%dB" % n
 
 
