@@ -14,7 +14,6 @@ namespace dfam {
 // ------------------------------------------------------------------ tuning
 constexpr int kThreads = 512;            // threads per CTA of the match kernel
 constexpr int kMaxChunksPerTile = kThreads / 2;  // every chunk is charged >= 2 thread slots
-constexpr int kStageBytes = 16384;       // one staging buffer of class-row offsets
 constexpr int kMaxSegLen = 2048;         // longest staged segment per chunk (positions)
 constexpr uint16_t kNone16 = 0xFFFF;     // "not a member" in pos tables / invalid byte
 constexpr uint32_t kNone32 = 0xFFFFFFFFu;

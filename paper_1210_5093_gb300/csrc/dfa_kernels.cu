@@ -1244,11 +1244,23 @@ uint32_t match_target_ctas(uint32_t kmax, uint32_t want) {
     return t;
 }
 
-// Shared memory of k_match and the stage-buffer size: the largest stage (8 to
-// 64 KB per buffer) that lets `target` CTAs share an SM, else fewer CTAs.
+// Smallest stage buffer: a tile's kMaxChunksPerTile chunks each stage at
+// least 16 positions of up to 4 bytes (32-bit row offsets).
+constexpr uint32_t kMinStage = kMaxChunksPerTile * 16u * 4u;
+static_assert(kMinStage == 16u * 1024u, "stage floor");
+
+// Shared memory of k_match and the stage-buffer size: the largest stage
+// (kMinStage to 64 KB per buffer) that lets `target` CTAs share an SM, else
+// fewer CTAs.  A launch whose tables are all read through L2 takes the
+// smallest stage instead: the shared memory it leaves to L1 caches the hot
+// table rows.
 uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes,
                           uint32_t target) {
-    const uint32_t per_sm = 228u * 1024u, reserved = 1024u, min_stage = 8u * 1024u;
+    const uint32_t per_sm = 228u * 1024u, reserved = 1024u, min_stage = kMinStage;
+    if (table_cap == 0) {
+        *stage_bytes = min_stage;
+        return smem_layout(table_cap, kmax, vcap, min_stage).total;
+    }
     for (uint32_t ctas = target; ctas >= 1; --ctas) {
         for (uint32_t sb = 64u * 1024u; sb >= min_stage; sb -= 2048u) {
             if (ctas * (smem_layout(table_cap, kmax, vcap, sb).total + reserved) <= per_sm) {
