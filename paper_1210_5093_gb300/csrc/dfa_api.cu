@@ -143,7 +143,8 @@ uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_
 }
 
 int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
-            const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out) {
+            const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out,
+            const uint32_t* out_ids) {
     if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
     const uint32_t lookahead = opts_lookahead(opts);
     if (lookahead > kMaxLookahead) return DFA_EINVAL;
@@ -210,7 +211,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         t.qinv = recip64((uint64_t)m + t.P - 1);
         t.chunk_base = (uint32_t)chunks;
         t.lookahead = lookahead;
-        t.out = i;
+        t.out = out_ids ? out_ids[i] : i;
         if (p.groups.empty() || p.groups.back().dfa != t.dfa) {
             if (!p.groups.empty()) {
                 const DevGroup& pg = p.groups.back();
@@ -979,8 +980,13 @@ int dfa_match(const dfa_t* d, const uint8_t* str, uint64_t len, const dfa_match_
 
 // ------------------------------------------------------------------ batches
 
+// A batch runs as one launch per part: tests whose DFA table is read from
+// shared memory, then tests whose table is read through L2.  Each part has
+// its own shared-memory layout, so the L2 part takes small stage buffers and
+// leaves L1 to the hot table rows (one layout for both would give L1 little).
 struct dfa_batch_s {
-    Prepared p;
+    std::vector<Prepared> parts;
+    std::vector<uint64_t> ws_off;  // each part's offset in ws
     uint8_t* ws = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -989,29 +995,81 @@ struct dfa_batch_s {
     void* ev_end = nullptr;
 };
 
+// Every part of the batch in order on `st` (the events bracket all match kernels).
+static int launch_parts(const dfa_batch_t* b, dfa_result_t* dev_out, cudaStream_t st, void* ev_begin,
+                        void* ev_end) {
+    const size_t n = b->parts.size();
+    for (size_t i = 0; i < n; ++i) {
+        LaunchPlan lp;
+        fill_plan(b->parts[i], lp, b->ws + b->ws_off[i], dev_out);
+        int rc = launch_plan(lp, b->parts[i].kmax, b->parts[i].smem, st, nullptr,
+                             i == 0 ? ev_begin : nullptr, i + 1 == n ? ev_end : nullptr);
+        if (rc != DFA_OK) return rc;
+    }
+    return DFA_OK;
+}
+
 extern "C" {
 
 int dfa_batch_prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
                       const uint64_t* lens, const dfa_match_opts_t* opts, dfa_batch_t** out) {
     if (!out) return DFA_EINVAL;
     *out = nullptr;
+    if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
+    const uint32_t lookahead = opts_lookahead(opts);
+    if (lookahead > kMaxLookahead) return DFA_EINVAL;
     dfa_batch_t* b = new (std::nothrow) dfa_batch_t();
     if (!b) return DFA_ENOMEM;
-    int rc = prepare(count, dfas, strs, lens, opts, true, &b->p);
-    if (rc != DFA_OK) {
-        delete b;
-        return rc;
+    // split by where each DFA's table is read from in a launch of several DFAs
+    std::vector<uint32_t> ids[2];
+    const dfa_t* first = dfas[0];
+    bool several = false;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (!dfas[i]) { delete b; return DFA_EINVAL; }
+        several |= dfas[i] != first;
+        const DevDfa x = launch_desc(dfas[i], lookahead);
+        const bool smem = x.placement == kSmem && x.table_bytes <= kBatchSmemTable;
+        ids[smem ? 0 : 1].push_back(i);
     }
-    if (cudaMalloc(&b->ws, b->p.ws.total) != cudaSuccess) {
+    if (!several || ids[0].empty() || ids[1].empty()) {
+        ids[0].clear();
+        ids[1].clear();
+        for (uint32_t i = 0; i < count; ++i) ids[0].push_back(i);
+    }
+    uint64_t total = 0;
+    for (int k = 0; k < 2; ++k) {
+        if (ids[k].empty()) continue;
+        std::vector<const dfa_t*> pd;
+        std::vector<const uint8_t*> ps;
+        std::vector<uint64_t> pl;
+        for (uint32_t i : ids[k]) {
+            pd.push_back(dfas[i]);
+            ps.push_back(strs[i]);
+            pl.push_back(lens[i]);
+        }
+        Prepared p;
+        int rc = prepare((uint32_t)ids[k].size(), pd.data(), ps.data(), pl.data(), opts, true, &p,
+                         ids[k].data());
+        if (rc != DFA_OK) {
+            delete b;
+            return rc;
+        }
+        b->ws_off.push_back(total);
+        total += up(p.ws.total, 256);
+        b->parts.push_back(std::move(p));
+    }
+    if (cudaMalloc(&b->ws, total) != cudaSuccess) {
         cudaGetLastError();
         delete b;
         return DFA_ENOMEM;
     }
-    rc = upload_desc(b->p, b->ws);
-    if (rc != DFA_OK) {
-        cudaFree(b->ws);
-        delete b;
-        return rc;
+    for (size_t i = 0; i < b->parts.size(); ++i) {
+        int rc = upload_desc(b->parts[i], b->ws + b->ws_off[i]);
+        if (rc != DFA_OK) {
+            cudaFree(b->ws);
+            delete b;
+            return rc;
+        }
     }
     *out = b;
     return DFA_OK;
@@ -1019,10 +1077,7 @@ int dfa_batch_prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* c
 
 int dfa_batch_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) {
     if (!b || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 3u)) return DFA_EINVAL;
-    LaunchPlan lp;
-    fill_plan(b->p, lp, b->ws, dev_out);
-    return launch_plan(lp, b->p.kmax, b->p.smem, static_cast<cudaStream_t>(stream), nullptr,
-                       b->ev_begin, b->ev_end);
+    return launch_parts(b, dev_out, static_cast<cudaStream_t>(stream), b->ev_begin, b->ev_end);
 }
 
 int dfa_batch_set_events(dfa_batch_t* b, void* ev_begin, void* ev_end) {
@@ -1048,9 +1103,7 @@ int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) 
             if (own) cudaStreamDestroy(cap);
             return DFA_ECUDA;
         }
-        LaunchPlan lp;
-        fill_plan(b->p, lp, b->ws, dev_out);
-        int rc = launch_plan(lp, b->p.kmax, b->p.smem, cap, nullptr);
+        int rc = launch_parts(b, dev_out, cap, nullptr, nullptr);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cap, &g);
         if (own) cudaStreamDestroy(cap);
@@ -1071,7 +1124,9 @@ int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) 
 
 int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
     if (!b || !n) return DFA_EINVAL;
-    *n = launch_kernel_count(b->p.ptot, b->p.grid, b->p.dyn != 0);
+    uint32_t k = 0;
+    for (const Prepared& p : b->parts) k += launch_kernel_count(p.ptot, p.grid, p.dyn != 0);
+    *n = k;
     return DFA_OK;
 }
 

@@ -200,8 +200,10 @@ uint64_t chunk_start(uint64_t n, uint32_t P, uint32_t m, uint32_t k);
 struct dfa_s;
 namespace dfam {
 // Batch planning and launching (dfa_api.cu), shared with the serving loop.
+// out_ids (optional): the result index of each test (default: its position).
 int prepare(uint32_t count, const dfa_s* const* dfas, const uint8_t* const* strs,
-            const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out);
+            const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out,
+            const uint32_t* out_ids = nullptr);
 void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out);
 int upload_desc_async(const Prepared& p, uint8_t* ws, uint8_t* pinned, void* stream);
 uint64_t desc_span(const Prepared& p);

@@ -1274,12 +1274,11 @@ uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint
 }
 
 static int g_sm_count = -1, g_dev = -1;
+static uint32_t g_smem_optin = 0;
 
 template <int KMAX, int MINB>
 static int grid_for(uint32_t smem, uint32_t* grid) {
-    if (cudaFuncSetAttribute(k_match<KMAX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return DFA_ECUDA;
+    if (smem > g_smem_optin) return DFA_ECUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<KMAX, MINB>, kThreads,
                                                       smem) != cudaSuccess ||
@@ -1303,6 +1302,21 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
         if (cudaFuncSetAttribute(k_plan_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmallPlanSmem) != cudaSuccess)
             return DFA_ECUDA;
+        // The match kernels may take up to the opt-in maximum per launch.  Set
+        // once: plans prepared in any order (batch parts, concurrent server
+        // batches) then launch with whatever shared memory each needs; a
+        // per-plan value could be lowered by a later plan before an earlier
+        // one launches.
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncSetAttribute(k_match<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_match<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_match<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                cudaSuccess)
+            return DFA_ECUDA;
+        g_smem_optin = (uint32_t)optin;
         g_dev = dev;
     }
     if (kmax > 8) return grid_for<16, 2>(smem, grid);
