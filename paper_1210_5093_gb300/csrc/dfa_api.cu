@@ -355,6 +355,59 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     return DFA_OK;
 }
 
+// The launches of one batch: tests whose DFA table is read from shared
+// memory in a launch of several DFAs, then tests whose table is read through
+// L2.  Each part has its own shared-memory layout, so the L2 part takes small
+// stage buffers and leaves L1 to the hot table rows (one layout for both
+// would give L1 little).  A batch of one DFA, or with tables of one kind,
+// has one part.  ws_off receives each part's workspace offset and *ws_total
+// their sum (256-byte aligned parts).
+int prepare_parts(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
+                  const uint64_t* lens, const dfa_match_opts_t* opts, std::vector<Prepared>* parts,
+                  std::vector<uint64_t>* ws_off, uint64_t* ws_total) {
+    if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
+    const uint32_t lookahead = opts_lookahead(opts);
+    if (lookahead > kMaxLookahead) return DFA_EINVAL;
+    std::vector<uint32_t> ids[2];
+    const dfa_t* first = dfas[0];
+    bool several = false;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (!dfas[i]) return DFA_EINVAL;
+        several |= dfas[i] != first;
+        const DevDfa x = launch_desc(dfas[i], lookahead);
+        const bool smem = x.placement == kSmem && x.table_bytes <= kBatchSmemTable;
+        ids[smem ? 0 : 1].push_back(i);
+    }
+    if (!several || ids[0].empty() || ids[1].empty()) {
+        ids[0].clear();
+        ids[1].clear();
+        for (uint32_t i = 0; i < count; ++i) ids[0].push_back(i);
+    }
+    parts->clear();
+    ws_off->clear();
+    uint64_t total = 0;
+    for (int k = 0; k < 2; ++k) {
+        if (ids[k].empty()) continue;
+        std::vector<const dfa_t*> pd;
+        std::vector<const uint8_t*> ps;
+        std::vector<uint64_t> pl;
+        for (uint32_t i : ids[k]) {
+            pd.push_back(dfas[i]);
+            ps.push_back(strs[i]);
+            pl.push_back(lens[i]);
+        }
+        Prepared p;
+        int rc = prepare((uint32_t)ids[k].size(), pd.data(), ps.data(), pl.data(), opts, true, &p,
+                         ids[k].data());
+        if (rc != DFA_OK) return rc;
+        ws_off->push_back(total);
+        total += up(p.ws.total, 256);
+        parts->push_back(std::move(p));
+    }
+    *ws_total = total;
+    return DFA_OK;
+}
+
 }  // namespace dfam
 
 using namespace dfam;
@@ -980,10 +1033,7 @@ int dfa_match(const dfa_t* d, const uint8_t* str, uint64_t len, const dfa_match_
 
 // ------------------------------------------------------------------ batches
 
-// A batch runs as one launch per part: tests whose DFA table is read from
-// shared memory, then tests whose table is read through L2.  Each part has
-// its own shared-memory layout, so the L2 part takes small stage buffers and
-// leaves L1 to the hot table rows (one layout for both would give L1 little).
+// A batch runs as one launch per part (prepare_parts).
 struct dfa_batch_s {
     std::vector<Prepared> parts;
     std::vector<uint64_t> ws_off;  // each part's offset in ws
@@ -1015,48 +1065,13 @@ int dfa_batch_prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* c
                       const uint64_t* lens, const dfa_match_opts_t* opts, dfa_batch_t** out) {
     if (!out) return DFA_EINVAL;
     *out = nullptr;
-    if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
-    const uint32_t lookahead = opts_lookahead(opts);
-    if (lookahead > kMaxLookahead) return DFA_EINVAL;
     dfa_batch_t* b = new (std::nothrow) dfa_batch_t();
     if (!b) return DFA_ENOMEM;
-    // split by where each DFA's table is read from in a launch of several DFAs
-    std::vector<uint32_t> ids[2];
-    const dfa_t* first = dfas[0];
-    bool several = false;
-    for (uint32_t i = 0; i < count; ++i) {
-        if (!dfas[i]) { delete b; return DFA_EINVAL; }
-        several |= dfas[i] != first;
-        const DevDfa x = launch_desc(dfas[i], lookahead);
-        const bool smem = x.placement == kSmem && x.table_bytes <= kBatchSmemTable;
-        ids[smem ? 0 : 1].push_back(i);
-    }
-    if (!several || ids[0].empty() || ids[1].empty()) {
-        ids[0].clear();
-        ids[1].clear();
-        for (uint32_t i = 0; i < count; ++i) ids[0].push_back(i);
-    }
     uint64_t total = 0;
-    for (int k = 0; k < 2; ++k) {
-        if (ids[k].empty()) continue;
-        std::vector<const dfa_t*> pd;
-        std::vector<const uint8_t*> ps;
-        std::vector<uint64_t> pl;
-        for (uint32_t i : ids[k]) {
-            pd.push_back(dfas[i]);
-            ps.push_back(strs[i]);
-            pl.push_back(lens[i]);
-        }
-        Prepared p;
-        int rc = prepare((uint32_t)ids[k].size(), pd.data(), ps.data(), pl.data(), opts, true, &p,
-                         ids[k].data());
-        if (rc != DFA_OK) {
-            delete b;
-            return rc;
-        }
-        b->ws_off.push_back(total);
-        total += up(p.ws.total, 256);
-        b->parts.push_back(std::move(p));
+    int rc = prepare_parts(count, dfas, strs, lens, opts, &b->parts, &b->ws_off, &total);
+    if (rc != DFA_OK) {
+        delete b;
+        return rc;
     }
     if (cudaMalloc(&b->ws, total) != cudaSuccess) {
         cudaGetLastError();
@@ -1064,7 +1079,7 @@ int dfa_batch_prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* c
         return DFA_ENOMEM;
     }
     for (size_t i = 0; i < b->parts.size(); ++i) {
-        int rc = upload_desc(b->parts[i], b->ws + b->ws_off[i]);
+        rc = upload_desc(b->parts[i], b->ws + b->ws_off[i]);
         if (rc != DFA_OK) {
             cudaFree(b->ws);
             delete b;

@@ -204,6 +204,9 @@ namespace dfam {
 int prepare(uint32_t count, const dfa_s* const* dfas, const uint8_t* const* strs,
             const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out,
             const uint32_t* out_ids = nullptr);
+int prepare_parts(uint32_t count, const dfa_s* const* dfas, const uint8_t* const* strs,
+                  const uint64_t* lens, const dfa_match_opts_t* opts, std::vector<Prepared>* parts,
+                  std::vector<uint64_t>* ws_off, uint64_t* ws_total);
 void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out);
 int upload_desc_async(const Prepared& p, uint8_t* ws, uint8_t* pinned, void* stream);
 uint64_t desc_span(const Prepared& p);

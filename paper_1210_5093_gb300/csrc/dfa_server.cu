@@ -6,6 +6,8 @@
 // Each batch is one persistent launch of the batched match kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -169,11 +171,17 @@ bool dfa_server_s::launch_one() {
     std::vector<Req> batch;
     {
         std::lock_guard<std::mutex> g(mu);
-        // admission in arrival order while the arena has room
+        // admission in arrival order while the arena has room; one batch takes
+        // at most budget / slots bytes, so that every slot can be in flight and
+        // one batch's copies overlap another's matching
+        const uint64_t batch_cap = std::max<uint64_t>(budget / slots.size(), 1);
+        uint64_t batch_bytes = 0;
         while (!pending.empty() && batch.size() < kMaxBatch) {
             Req r = pending.front();
+            if (!batch.empty() && batch_bytes + r.len > batch_cap) break;
             uint64_t off = 0;
             if (!arena.alloc(r.len, &off)) break;
+            batch_bytes += r.len;
             r.dev_off = off;
             st.bytes_in_flight += r.len;
             if (st.bytes_in_flight > st.max_bytes_in_flight) st.max_bytes_in_flight = st.bytes_in_flight;
@@ -191,22 +199,33 @@ bool dfa_server_s::launch_one() {
         strs[i] = arena_mem + batch[i].dev_off;
         lens[i] = batch[i].len;
     }
-    dfam::Prepared p;
-    int rc = dfam::prepare(n, dfas.data(), strs.data(), lens.data(), nullptr, true, &p);
-    // device: [workspace | results]; pinned host: [results | descriptor staging]
-    const uint64_t out_off = (p.ws.total + 255) & ~255ull;
-    const uint64_t stage_off = (12ull * n + 255) & ~255ull;
+    // one launch per part (tables in shared memory / through L2)
+    std::vector<dfam::Prepared> parts;
+    std::vector<uint64_t> ws_off;
+    uint64_t ws_total = 0;
+    int rc = dfam::prepare_parts(n, dfas.data(), strs.data(), lens.data(), nullptr, &parts, &ws_off,
+                                 &ws_total);
+    // device: [part workspaces | results]; pinned host: [results | descriptor staging per part]
+    const uint64_t out_off = (ws_total + 255) & ~255ull;
+    std::vector<uint64_t> stage_off;
+    uint64_t pinned_need = (12ull * n + 255) & ~255ull;
+    for (const dfam::Prepared& p : parts) {
+        stage_off.push_back(pinned_need);
+        pinned_need += (dfam::desc_span(p) + 255) & ~255ull;
+    }
     if (rc == DFA_OK) rc = grow(&slot->ws, &slot->ws_bytes, out_off + 12ull * n, false);
-    if (rc == DFA_OK) rc = grow(&slot->pinned, &slot->pinned_bytes, stage_off + dfam::desc_span(p), true);
+    if (rc == DFA_OK) rc = grow(&slot->pinned, &slot->pinned_bytes, pinned_need, true);
     if (rc == DFA_OK) {
         cudaStream_t s = slot->stream;
         for (uint32_t i = 0; i < n && rc == DFA_OK; ++i)
             if (lens[i] && cudaMemcpyAsync(arena_mem + batch[i].dev_off, batch[i].host, lens[i],
                                            cudaMemcpyHostToDevice, s) != cudaSuccess)
                 rc = DFA_ECUDA;
-        if (rc == DFA_OK) rc = dfam::upload_desc_async(p, slot->ws, slot->pinned + stage_off, s);
         slot->dev_out = reinterpret_cast<dfa_result_t*>(slot->ws + out_off);
-        if (rc == DFA_OK) rc = dfam::launch_prepared(p, slot->ws, slot->dev_out, s);
+        for (size_t k = 0; k < parts.size() && rc == DFA_OK; ++k) {
+            rc = dfam::upload_desc_async(parts[k], slot->ws + ws_off[k], slot->pinned + stage_off[k], s);
+            if (rc == DFA_OK) rc = dfam::launch_prepared(parts[k], slot->ws + ws_off[k], slot->dev_out, s);
+        }
         if (rc == DFA_OK &&
             cudaMemcpyAsync(slot->pinned, slot->dev_out, 12ull * n, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)
