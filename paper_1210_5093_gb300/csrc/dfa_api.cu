@@ -14,8 +14,8 @@
 #include "dfa_internal.h"
 
 namespace dfam {
-uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes,
-                          uint32_t target);
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t esz_max,
+                          uint32_t* stage_bytes, uint32_t target);
 uint32_t match_target_ctas(uint32_t kmax, uint32_t want);
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
 uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn);
@@ -188,7 +188,10 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         p.qe_max = std::max(p.qe_max, x.qe);
         if (x.placement == kSmem) p.table_cap = std::max(p.table_cap, (uint32_t)up(x.table_bytes, 16));
     }
-    p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap, &p.stage, match_target_ctas(p.kmax, 0));
+    uint32_t esz_max = 1;
+    for (const DevDfa& x : p.dfas) esz_max = std::max(esz_max, stage_esz(x.stage_fmt));
+    p.smem = match_smem_bytes(p.table_cap, p.kmax, p.vcap, esz_max, &p.stage,
+                              match_target_ctas(p.kmax, 0));
     int rc = match_grid(p.smem, p.kmax, &p.grid);
     if (rc != DFA_OK) return rc;
     uint64_t total = 0;
@@ -312,7 +315,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     const uint32_t tcap = x.placement == kSmem ? (uint32_t)up(x.table_bytes, 16) : 0u;
     s->kmax = x.K;
     uint32_t stage = 0;
-    s->smem = match_smem_bytes(tcap, x.K, x.vcap, &stage,
+    s->smem = match_smem_bytes(tcap, x.K, x.vcap, stage_esz(x.stage_fmt), &stage,
                                match_target_ctas(x.K, d->tuning_for(lookahead).ctas_per_sm));
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);

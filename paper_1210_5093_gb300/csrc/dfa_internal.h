@@ -58,6 +58,14 @@ struct DevDfa {
 // row byte offsets (tables read through L2).
 enum StageFmt : uint32_t { kCls8 = 0, kOff16 = 1, kOff32 = 2 };
 
+// Bytes per staged position of a stage format.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr uint32_t stage_esz(uint32_t fmt) {
+    return fmt == kOff32 ? 4u : (fmt == kOff16 ? 2u : 1u);
+}
+
 // One membership test of a launch.
 struct DevTest {
     const uint8_t* str;

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 
 #include "dfa_internal.h"
 
@@ -811,10 +812,6 @@ __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, ui
     if (bad) atomicOr(test_err + m.test, 1u);
 }
 
-__host__ __device__ constexpr uint32_t stage_esz(uint32_t fmt) {
-    return fmt == kOff32 ? 4u : (fmt == kOff16 ? 2u : 1u);
-}
-
 template <uint32_t FMT>
 __device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, uint32_t stage,
                               uint32_t boff, uint32_t id_off, uint32_t* test_err) {
@@ -1244,19 +1241,23 @@ uint32_t match_target_ctas(uint32_t kmax, uint32_t want) {
     return t;
 }
 
-// Smallest stage buffer: a tile's kMaxChunksPerTile chunks each stage at
-// least 16 positions of up to 4 bytes (32-bit row offsets).
-constexpr uint32_t kMinStage = kMaxChunksPerTile * 16u * 4u;
-static_assert(kMinStage == 16u * 1024u, "stage floor");
+// Smallest stage buffer for stage entries of esz bytes: a tile's
+// kMaxChunksPerTile chunks each stage at least 16 positions (and at least
+// 8 KB, below which segments get too short).  32-bit row offsets need 16 KB.
+__host__ __device__ constexpr uint32_t min_stage_bytes(uint32_t esz) {
+    return kMaxChunksPerTile * 16u * esz > 8192u ? kMaxChunksPerTile * 16u * esz : 8192u;
+}
+static_assert(min_stage_bytes(4) == 16u * 1024u && min_stage_bytes(1) == 8192u, "stage floor");
 
 // Shared memory of k_match and the stage-buffer size: the largest stage
-// (kMinStage to 64 KB per buffer) that lets `target` CTAs share an SM, else
-// fewer CTAs.  A launch whose tables are all read through L2 takes the
+// (min_stage_bytes(esz_max) to 64 KB per buffer) that lets `target` CTAs
+// share an SM, else fewer CTAs.  esz_max is the widest stage entry of the
+// launch's DFAs.  A launch whose tables are all read through L2 takes the
 // smallest stage instead: the shared memory it leaves to L1 caches the hot
 // table rows.
-uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t* stage_bytes,
-                          uint32_t target) {
-    const uint32_t per_sm = 228u * 1024u, reserved = 1024u, min_stage = kMinStage;
+uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint32_t esz_max,
+                          uint32_t* stage_bytes, uint32_t target) {
+    const uint32_t per_sm = 228u * 1024u, reserved = 1024u, min_stage = min_stage_bytes(esz_max);
     if (table_cap == 0) {
         *stage_bytes = min_stage;
         return smem_layout(table_cap, kmax, vcap, min_stage).total;
@@ -1275,6 +1276,7 @@ uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint
 
 static int g_sm_count = -1, g_dev = -1;
 static uint32_t g_smem_optin = 0;
+static uint32_t g_smem_per_sm = 228u * 1024u;
 
 template <int KMAX, int MINB>
 static int grid_for(uint32_t smem, uint32_t* grid) {
@@ -1302,11 +1304,10 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
         if (cudaFuncSetAttribute(k_plan_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmallPlanSmem) != cudaSuccess)
             return DFA_ECUDA;
-        // The match kernels may take up to the opt-in maximum per launch.  Set
-        // once: plans prepared in any order (batch parts, concurrent server
-        // batches) then launch with whatever shared memory each needs; a
-        // per-plan value could be lowered by a later plan before an earlier
-        // one launches.
+        // The match kernels may take up to the opt-in maximum per launch: set
+        // once, so plans prepared in any order (batch parts, concurrent server
+        // batches) launch with whatever shared memory each needs.  The split
+        // between shared memory and L1 is chosen per launch (launch_match).
         int optin = 0;
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
             cudaFuncSetAttribute(k_match<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
@@ -1317,6 +1318,11 @@ int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
                 cudaSuccess)
             return DFA_ECUDA;
         g_smem_optin = (uint32_t)optin;
+        int per_sm = 0;
+        if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ==
+                cudaSuccess &&
+            per_sm > 0)
+            g_smem_per_sm = (uint32_t)per_sm;
         g_dev = dev;
     }
     if (kmax > 8) return grid_for<16, 2>(smem, grid);
@@ -1351,6 +1357,34 @@ int launch_compose_segments(const dfa_result_t* seg_res, const uint16_t* maps, u
     return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
 }
 
+// Every kernel of a launch runs with one shared-memory carve-out: what the
+// match kernel's CTAs per SM need (a per-launch hint).  The rest of the SM's
+// unified L1/shared storage stays L1, which caches input sectors, descriptors
+// and L2-placed tables; without the hint the split would follow the kernel's
+// dynamic shared memory limit.  One value for all kernels of the launch
+// spares the SMs a reconfiguration between them.
+static uint32_t carveout_pct(const LaunchPlan& lp, uint32_t smem) {
+    const uint32_t per_sm = (lp.grid + (uint32_t)g_sm_count - 1) / (uint32_t)g_sm_count;
+    const uint32_t need = std::max(per_sm * (smem + 1024u), kSmallPlanSmem + 1024u);
+    return std::min(100u, (need * 100u + g_smem_per_sm - 1) / g_smem_per_sm);
+}
+
+template <typename... Params, typename... Args>
+static cudaError_t launch_ex(void (*kernel)(Params...), uint32_t grid, uint32_t block, uint32_t smem,
+                             cudaStream_t st, uint32_t pct, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[0].val.sharedMemCarveout = pct;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn) {
     return (ptot <= kSmallPlan && grid <= kSmallShares ? 2u : 5u) + (dyn ? 1u : 0u);
 }
@@ -1368,32 +1402,34 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
         cudaMemsetAsync(lp.test_err, 0, sizeof(uint32_t) * lp.ntests * 2, st) != cudaSuccess)
         return DFA_ECUDA;
     uint32_t nk = launch_kernel_count(lp.ptot, lp.grid, lp.dyn != 0);
+    const uint32_t pct = carveout_pct(lp, smem);
+    int e = 0;  // launch errors (cudaError_t values OR-ed: nonzero = failed)
     if (lp.dyn) {
         const uint32_t qe_words = (lp.qe_max + 31) / 32, set_words = (lp.vcap + 1) / 2;
-        const uint32_t smem = kLaWarps * (qe_words + set_words) * 4;
-        k_lookahead<<<(lp.ptot + kLaWarps - 1) / kLaWarps, kLaWarps * 32, smem, st>>>(lp, qe_words,
-                                                                                   set_words);
+        const uint32_t la_smem = kLaWarps * (qe_words + set_words) * 4;
+        e |= launch_ex(k_lookahead, (lp.ptot + kLaWarps - 1) / kLaWarps, kLaWarps * 32, la_smem, st, pct,
+                  lp, qe_words, set_words);
     }
     if (small) {
-        k_plan_small<<<1, kPlanThreads, kSmallPlanSmem, st>>>(lp);
+        e |= launch_ex(k_plan_small, 1, kPlanThreads, kSmallPlanSmem, st, pct, lp);
     } else {
         const uint32_t pblocks = (lp.grid + kPackWarps - 1) / kPackWarps;
-        k_count<<<nb, kPlanThreads, 0, st>>>(lp);
-        k_offsets<<<nb, kPlanThreads, 0, st>>>(lp);
-        k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 0);
-        k_pack<<<pblocks, kPackWarps * 32, 0, st>>>(lp, 1);
+        e |= launch_ex(k_count, nb, kPlanThreads, 0, st, pct, lp);
+        e |= launch_ex(k_offsets, nb, kPlanThreads, 0, st, pct, lp);
+        e |= launch_ex(k_pack, pblocks, kPackWarps * 32, 0, st, pct, lp, 0u);
+        e |= launch_ex(k_pack, pblocks, kPackWarps * 32, 0, st, pct, lp, 1u);
     }
     if (plan_only) {
         if (kernels) *kernels = nk - 1;
-        return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
+        return e == 0 && cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
     }
     if (ev_begin) cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), st);
-    if (kmax > 8) k_match<16, 2><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
-    else if (kmax > 4) k_match<8, 2><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
-    else k_match<4, 3><<<lp.grid, kThreads, smem, st>>>(lp, kmax);
+    if (kmax > 8) e |= launch_ex(k_match<16, 2>, lp.grid, kThreads, smem, st, pct, lp, kmax);
+    else if (kmax > 4) e |= launch_ex(k_match<8, 2>, lp.grid, kThreads, smem, st, pct, lp, kmax);
+    else e |= launch_ex(k_match<4, 3>, lp.grid, kThreads, smem, st, pct, lp, kmax);
     if (ev_end) cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st);
     if (kernels) *kernels = nk;
-    return cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
+    return e == 0 && cudaPeekAtLastError() == cudaSuccess ? DFA_OK : DFA_ECUDA;
 }
 
 }  // namespace dfam
