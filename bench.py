@@ -235,7 +235,7 @@ def batched_leg(dm, dfas, datas, reps: int = 5):
 
 
 def serving_leg(dm, dfas, datas, rate_gbs: float, seconds: float = 2.0, budget: int = 2 << 30,
-                inflight: int = 4, seed: int = 5):
+                inflight: int = 8, seed: int = 5):
     """Poisson arrivals at `rate_gbs` of offered load drawn from the given tests
     (pinned host buffers); reports achieved GB/s and arrival->result latency."""
     import torch
@@ -339,7 +339,7 @@ def run_serve_config(args, dm, torch):
     rates = [("20k_req_s", 20000 * mean / 1e9)] + [("%.2fx" % f, f * cap) for f in (0.25, 0.5, 0.75, 1.0)]
     for name, gbs in rates:
         sv, done, sub = serving_leg(dm, dd, datas, gbs, seconds=args.serve_seconds,
-                                    budget=args.budget, inflight=4, seed=len(out) + 1)
+                                    budget=args.budget, inflight=args.inflight, seed=len(out) + 1)
         res_b = bl_res
         for c in done:   # every served result equals the same test in the batched launch
             assert (c[1], c[2], c[3]) == res_b[sub[c[0]]], "served result differs"
@@ -349,7 +349,8 @@ def run_serve_config(args, dm, torch):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
             "data": "synthetic",
             "config": {"workload": "serving_batched_mix", "pool_tests": len(datas),
-                       "budget_bytes": args.budget, "mean_request_bytes": int(mean)},
+                       "budget_bytes": args.budget, "mean_request_bytes": int(mean),
+                       "inflight": args.inflight},
             "serving": out, "batched_capacity_gbs": cap}
     print(json.dumps(line), flush=True)
 
@@ -369,6 +370,7 @@ def main():
     ap.add_argument("--tests", type=int, default=4096, help="batch/serve: number of tests")
     ap.add_argument("--max-len", type=int, default=64 << 20, help="batch/serve: longest test")
     ap.add_argument("--budget", type=int, default=40 << 30, help="serve: admission budget (bytes)")
+    ap.add_argument("--inflight", type=int, default=8, help="serve: batches in flight (streams)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--bytes", type=int, default=0, help="input size override (small profiling cases)")

@@ -355,8 +355,10 @@ typedef struct {
 /*
  * A serving loop on the current device: requests (dfa, host string) are
  * admitted while the bytes in flight stay within hbm_budget_bytes, grouped
- * into batches as they arrive and launched on max_inflight streams, so new
- * requests start while earlier batches still run (continuous batching).
+ * into batches as they arrive and launched on max_inflight streams (0 = 8,
+ * at most 64), so new requests start while earlier batches still run
+ * (continuous batching).  A batch takes at most hbm_budget_bytes /
+ * max_inflight bytes, so one batch's copies overlap another's matching.
  * DFAs must stay alive while requests on them are pending.
  */
 int dfa_server_create(uint64_t hbm_budget_bytes, uint32_t max_inflight, dfa_server_t **out);

@@ -431,7 +431,7 @@ def match_batch(dfas: Sequence[Dfa], tensors, stream=None, num_chunks: int = 0,
 class Server:
     """Continuous-batching request loop (dfa_server_t)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4):
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 8):
         h = ctypes.c_void_p()
         _check(lib().dfa_server_create(hbm_budget_bytes, max_inflight, ctypes.byref(h)),
                "dfa_server_create")

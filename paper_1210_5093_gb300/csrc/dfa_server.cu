@@ -273,7 +273,7 @@ extern "C" {
 int dfa_server_create(uint64_t budget, uint32_t max_inflight, dfa_server_t** out) {
     if (!out || budget == 0) return DFA_EINVAL;
     *out = nullptr;
-    if (max_inflight == 0) max_inflight = 4;
+    if (max_inflight == 0) max_inflight = 8;
     if (max_inflight > 64) max_inflight = 64;
     dfa_server_s* s = new (std::nothrow) dfa_server_s();
     if (!s) return DFA_ENOMEM;
