@@ -118,11 +118,19 @@ def lookups_per_launch(dm, d, dev, n: int, num_chunks: int = 0, lookahead: int =
     return W, float(sizes[1:].mean()) if P > 1 else 1.0
 
 
+def device_code_sha() -> str:
+    """sha256 prefix of the kernels' device code: dfa_kernels.cu above its host-side
+    section (launch helpers below it do not change what a launch reads or writes)."""
+    src = os.path.join(ROOT, "paper_1210_5093_gb300", "csrc", "dfa_kernels.cu")
+    text = open(src, "rb").read()
+    cut = text.find(b"// ------------------------------------------------------------ host side")
+    return hashlib.sha256(text[:cut] if cut >= 0 else text).hexdigest()[:16]
+
+
 def _traffic_record(workload: str):
     """DRAM bytes per match-kernel launch from the committed ncu summary, valid only
-    while the kernel source is unchanged."""
-    src = os.path.join(ROOT, "paper_1210_5093_gb300", "csrc", "dfa_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    while the kernels' device code is unchanged."""
+    sha = device_code_sha()
     p = os.path.join(ROOT, "profiles", "k_match_%s_traffic.json" % workload)
     if not os.path.exists(p):
         return None

@@ -1274,60 +1274,73 @@ uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint
     return smem_layout(table_cap, kmax, vcap, min_stage).total;
 }
 
-static int g_sm_count = -1, g_dev = -1;
-static uint32_t g_smem_optin = 0;
-static uint32_t g_smem_per_sm = 228u * 1024u;
+// Per-device properties the launches need; the kernel attributes are set once
+// per device when they are first read (thread-safe).
+struct DevProps {
+    bool ready = false;
+    uint32_t sms = 0;          // streaming multiprocessors
+    uint32_t smem_optin = 0;   // largest dynamic shared memory per CTA
+    uint32_t smem_per_sm = 0;  // shared memory per SM
+};
+constexpr int kMaxDevices = 64;
+static DevProps g_props[kMaxDevices];
+static std::mutex g_props_mu;
+
+static const DevProps* dev_props() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> g(g_props_mu);
+    DevProps& p = g_props[dev];
+    if (p.ready) return &p;
+    int sms = 0, optin = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        sms < 1 || optin < 1 || per_sm < 1)
+        return nullptr;
+    // k_lookahead's per-warp bitmap and set buffer for the largest DFA (4096 states)
+    const int la_max = kLaWarps * (4096 / 32 + 4096 / 2) * 4;
+    // The match kernels may take up to the opt-in maximum per launch: set once,
+    // so plans prepared in any order (batch parts, concurrent server batches)
+    // launch with whatever shared memory each needs.  The split between shared
+    // memory and L1 is chosen per launch (carveout_pct).
+    if (cudaFuncSetAttribute(k_lookahead, cudaFuncAttributeMaxDynamicSharedMemorySize, la_max) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_plan_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmallPlanSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_match<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_match<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_match<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+            cudaSuccess)
+        return nullptr;
+    p.sms = (uint32_t)sms;
+    p.smem_optin = (uint32_t)optin;
+    p.smem_per_sm = (uint32_t)per_sm;
+    p.ready = true;
+    return &p;
+}
 
 template <int KMAX, int MINB>
-static int grid_for(uint32_t smem, uint32_t* grid) {
-    if (smem > g_smem_optin) return DFA_ECUDA;
+static int grid_for(const DevProps& p, uint32_t smem, uint32_t* grid) {
+    if (smem > p.smem_optin) return DFA_ECUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<KMAX, MINB>, kThreads,
                                                       smem) != cudaSuccess ||
         per_sm < 1)
         return DFA_ECUDA;
-    *grid = (uint32_t)(g_sm_count * per_sm);
+    *grid = p.sms * (uint32_t)per_sm;
     return DFA_OK;
 }
 
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return DFA_ECUDA;
-    if (g_dev != dev) {
-        if (cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return DFA_ECUDA;
-        // k_lookahead's per-warp bitmap and set buffer for the largest DFA (4096 states)
-        const int la_max = kLaWarps * (4096 / 32 + 4096 / 2) * 4;
-        if (cudaFuncSetAttribute(k_lookahead, cudaFuncAttributeMaxDynamicSharedMemorySize, la_max) !=
-            cudaSuccess)
-            return DFA_ECUDA;
-        if (cudaFuncSetAttribute(k_plan_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmallPlanSmem) != cudaSuccess)
-            return DFA_ECUDA;
-        // The match kernels may take up to the opt-in maximum per launch: set
-        // once, so plans prepared in any order (batch parts, concurrent server
-        // batches) launch with whatever shared memory each needs.  The split
-        // between shared memory and L1 is chosen per launch (launch_match).
-        int optin = 0;
-        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            cudaFuncSetAttribute(k_match<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_match<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_match<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
-                cudaSuccess)
-            return DFA_ECUDA;
-        g_smem_optin = (uint32_t)optin;
-        int per_sm = 0;
-        if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ==
-                cudaSuccess &&
-            per_sm > 0)
-            g_smem_per_sm = (uint32_t)per_sm;
-        g_dev = dev;
-    }
-    if (kmax > 8) return grid_for<16, 2>(smem, grid);
-    if (kmax > 4) return grid_for<8, 2>(smem, grid);
-    return grid_for<4, 3>(smem, grid);
+    const DevProps* p = dev_props();
+    if (!p) return DFA_ECUDA;
+    if (kmax > 8) return grid_for<16, 2>(*p, smem, grid);
+    if (kmax > 4) return grid_for<8, 2>(*p, smem, grid);
+    return grid_for<4, 3>(*p, smem, grid);
 }
 
 // Eq. (8) over the segments of one string: seg_res[0] is the first
@@ -1364,9 +1377,11 @@ int launch_compose_segments(const dfa_result_t* seg_res, const uint16_t* maps, u
 // dynamic shared memory limit.  One value for all kernels of the launch
 // spares the SMs a reconfiguration between them.
 static uint32_t carveout_pct(const LaunchPlan& lp, uint32_t smem) {
-    const uint32_t per_sm = (lp.grid + (uint32_t)g_sm_count - 1) / (uint32_t)g_sm_count;
+    const DevProps* p = dev_props();
+    if (!p) return 100u;
+    const uint32_t per_sm = (lp.grid + p->sms - 1) / p->sms;
     const uint32_t need = std::max(per_sm * (smem + 1024u), kSmallPlanSmem + 1024u);
-    return std::min(100u, (need * 100u + g_smem_per_sm - 1) / g_smem_per_sm);
+    return std::min(100u, (need * 100u + p->smem_per_sm - 1) / p->smem_per_sm);
 }
 
 template <typename... Params, typename... Args>
