@@ -940,14 +940,22 @@ static int match_pipelined(const dfa_t* d, const uint8_t* str, const std::vector
     const size_t ns = seg.size();
     std::vector<Single> plan(ns);
     uint64_t len = 0, ws_need = 0;
+    for (uint64_t x : seg) len += x;
+    // every segment keeps the chunk length the whole string would get (the
+    // planner sizes chunk counts for a full GPU, which would cut the short
+    // early segments into needlessly short chunks)
+    Single whole;
+    int rc = plan_single(d, len, opts, &whole);
+    if (rc != DFA_OK) return rc;
+    dfa_match_opts_t so = opts ? *opts : dfa_match_opts_t{};
+    if (!opts) so.lookahead = 1;
     for (size_t i = 0; i < ns; ++i) {
-        int rc = plan_single(d, seg[i], opts, &plan[i]);
-        if (rc != DFA_OK) return rc;
-        len += seg[i];
+        const uint64_t p = (uint64_t)whole.lp.ptot * seg[i] / len;
+        so.num_chunks = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p, 1u << 30));
+        if ((rc = plan_single(d, seg[i], &so, &plan[i])) != DFA_OK) return rc;
         ws_need = std::max(ws_need, plan[i].ws.total);
     }
-    int rc = pipeline_resources(B, ns);
-    if (rc != DFA_OK) return rc;
+    if ((rc = pipeline_resources(B, ns)) != DFA_OK) return rc;
     const uint32_t stride = (d->h.qe + 1) & ~1u;
     const uint64_t res_off = 2 * ws_need, map_off = up(res_off + sizeof(dfa_result_t) * (ns + 1), 256);
     if ((rc = grow_dev(&B.str, &B.str_cap, len)) != DFA_OK) return rc;
