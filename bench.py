@@ -118,13 +118,20 @@ def lookups_per_launch(dm, d, dev, n: int, num_chunks: int = 0, lookahead: int =
     return W, float(sizes[1:].mean()) if P > 1 else 1.0
 
 
-def device_code_sha() -> str:
+def device_code_sha(text: bytes = None) -> str:
     """sha256 prefix of the kernels' device code: dfa_kernels.cu above its host-side
-    section (launch helpers below it do not change what a launch reads or writes)."""
-    src = os.path.join(ROOT, "paper_1210_5093_gb300", "csrc", "dfa_kernels.cu")
-    text = open(src, "rb").read()
+    section (launch helpers below it do not change what a launch reads or writes),
+    with comments and blank space dropped (they do not either)."""
+    import re
+    if text is None:
+        src = os.path.join(ROOT, "paper_1210_5093_gb300", "csrc", "dfa_kernels.cu")
+        text = open(src, "rb").read()
     cut = text.find(b"// ------------------------------------------------------------ host side")
-    return hashlib.sha256(text[:cut] if cut >= 0 else text).hexdigest()[:16]
+    code = (text[:cut] if cut >= 0 else text).decode()
+    code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+    code = re.sub(r"//[^\n]*", " ", code)
+    code = " ".join(code.split())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def _traffic_record(workload: str):

@@ -119,7 +119,7 @@ typedef struct {
  *                  or 0xFF for "not in Sigma"; NULL = identity (needs num_symbols == 256).
  * Limits: 1 <= num_states <= 4095 (a chunk's chains must fit one thread block),
  * 1 <= num_symbols <= 256.
- * Compilation (Algorithm 3 lines 1-7, done once): bytes with identical delta
+ * Compilation (the set computation of Algorithm 3, done once): bytes with identical delta
  * columns share a class; I_c (Eq. 11) and I_max (Eq. 12) are computed; the
  * class-major table (uint8 states if |Q|+1 <= 256, else uint16) is placed in
  * shared memory if it fits, otherwise read through L2.

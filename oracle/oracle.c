@@ -62,8 +62,8 @@ int oracle_run(uint32_t Q, uint32_t S, const int32_t *delta, uint32_t q0,
 }
 
 /*
- * States left out of every initial-state set.  Algorithm 3 (lines 1-7) drops
- * the error state q_e because a run that reached it never leaves it (Sec. 3,
+ * States left out of every initial-state set.  Algorithm 3 drops the error
+ * state q_e from its initial-state sets because a run that reached it never leaves it (Sec. 3,
  * Sec. 4.2).  For a DFA that is not minimal the same argument holds for every
  * state that loops on all symbols and is not accepting, so those are the
  * states excluded here: excluded[s] = 1 iff delta(s, a) == s for all a and
@@ -81,9 +81,9 @@ void oracle_excluded(uint32_t Q, uint32_t S, const int32_t *delta, const uint8_t
 
 /*
  * Eq. (11): I_sigma = { s : delta(x, sigma) = s for some x in Q }, minus the
- * excluded states (Algorithm 3, lines 1-6).  iset is S x (Q+1) flags,
- * iset[a*(Q+1)+s] = 1 iff s in I_a.  Returns I_max of Eq. (12) (the largest
- * cardinality, the reading of Algorithm 3 line 7).
+ * excluded states (Algorithm 3's initial-state sets).  iset is S x (Q+1) flags,
+ * iset[a*(Q+1)+s] = 1 iff s in I_a.  Returns I_max of Eq. (12): the largest
+ * cardinality (Algorithm 3's maximum over the sets, read as cardinalities).
  */
 uint32_t oracle_isets(uint32_t Q, uint32_t S, const int32_t *delta, const uint8_t *final_flags,
                       uint8_t *iset) {

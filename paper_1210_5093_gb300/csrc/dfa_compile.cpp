@@ -1,6 +1,6 @@
 // DFA compilation (done once per DFA, off the timed path).
 //
-// Algorithm 3, lines 1-7 of the paper computes the initial-state sets
+// The first part of Algorithm 3 computes the initial-state sets
 // I_sigma = { delta(x, sigma) : x in Q } \ {q_e} (Eq. 11) and
 // I_max = max_sigma |I_sigma| (Eq. 12).  Because I_max is a static property of
 // the DFA it may be computed off-line (Sec. 4.2); this file does it once at

@@ -4,11 +4,11 @@
 // four planning kernels (or k_plan_small, all of them in one CTA, for small
 // launches) and one persistent match kernel, all on one stream:
 //
-//   k_count        per chunk: test, reverse-lookahead class, thread slots, work  (Alg. 3 l.16, Eq. 11)
+//   k_count        per chunk: test, reverse-lookahead class, thread slots, work  (Alg. 3, Eq. 11)
 //   k_offsets      per-chunk slot offsets, CTA shares of the work, share bounds
 //   k_pack (x2)    greedy packing of each share into tiles, tile ranges
 //   k_match        persistent: stage chunks, advance every (chunk, state) chain,
-//                  compose the chunk maps, combine per test             (Alg. 3 l.8-20, Eqs. 8-9)
+//                  compose the chunk maps, combine per test             (Alg. 3, Eqs. 8-9)
 //
 // Layout of the work: chunk k of a test is matched from every state of its
 // initial-state set I_k (the image of its reverse-lookahead symbol's class).
@@ -253,7 +253,7 @@ __device__ __forceinline__ uint32_t cta_of_mid2(uint64_t mid2, uint64_t W, uint3
 // The reciprocal cta_of_mid2 takes (one real division per thread).
 __device__ __forceinline__ uint64_t share_recip(uint64_t W) { return W ? ~0ull / (2 * W) : 0; }
 
-// Per chunk g: owning test, reverse-lookahead class (Algorithm 3 line 16)
+// Per chunk g: owning test, reverse-lookahead class (Algorithm 3, Sec. 4.2)
 // and the thread slots it is charged: ceil(|I_k| / K), at least 2.  Writes
 // chunk_test, chunk_cls and the packing word; returns in cost[i] and work[i]
 // the slots and cost x chunk length (the lane-steps the chunk occupies, used
