@@ -14,6 +14,9 @@ It shares no code with ``paper_1210_5093_gb300`` and does not import it.
 * ``iset_word``  - Eq. (13) for one word of r reverse-lookahead symbols, in C.
 * ``isets_r``    - Eq. (13) for every word of length r, by enumeration
                    (exponential; small DFAs only).
+* ``boundary_starts`` - Sec. 4.2's boundary placement: each chunk start moved,
+                   within a bounded window, to the position whose reverse-
+                   lookahead symbol has the smallest initial-state set.
 
 Parity is pinned for every function here by tests/test_oracle_*.py (worked
 examples printed in the paper, closed-form languages, brute force over all
@@ -241,3 +244,53 @@ def chunk_starts(n: int, P: int, m: int) -> list:
 def l0(n: int, P: int, m: int, w: Optional[Sequence] = None) -> Fraction:
     w = [Fraction(1)] * P if w is None else [Fraction(x) for x in w]
     return Fraction(n) * m / (w[0] * m + sum(w[1:]))
+
+
+# ------------------------------------------------------------- Sec. 4.2 boundaries
+
+NOT_IN_SIGMA_COST = 65536  # larger than any initial-state set (|Q| <= 65535)
+
+
+def boundary_window(n: int, P: int, m: int, window: int, lookahead: int = 1) -> int:
+    """The window actually searched around each Eqs. (6)-(7) chunk start:
+    at most a quarter of floor(n / (m + P - 1)), the shortest chunk after the
+    first, so placed starts stay strictly increasing and no chunk grows by more
+    than half of that length.  Algorithm 2 (no lookahead symbol) and empty
+    chunks get no window."""
+    if lookahead == 0 or window == 0 or P <= 1:
+        return 0
+    return min(int(window), (n // (m + P - 1)) // 4)
+
+
+def boundary_starts(dfa: "Dfa", data, P: int, m: int, window: int, lookahead: int = 1) -> list:
+    """Sec. 4.2 ("Another possible optimization"): when the initial-state sets
+    differ much in size, divide the input at boundaries whose reverse-lookahead
+    symbol has a small set.  Reading taken here: start with the boundaries of
+    Eqs. (6)-(7); move the start S of every chunk k >= 1 to the position p in
+    [S - w, S + w] (w from boundary_window) that minimises, in this order, the
+    size |I_sigma| (Eq. 11) of the symbol sigma = Str[p - 1] before it, the
+    distance |p - S| and p itself.  A byte outside Sigma costs more than any
+    set.  The nominal start is a candidate, so no chunk starts after a symbol
+    with a larger set than Eqs. (6)-(7) gave it; the paper's concern that a
+    small-set symbol may be missing (a speed-down) is bounded by the window.
+    Returns the P+1 boundaries [0, ..., n]."""
+    buf = _as_u8(data)
+    n = len(buf)
+    starts = chunk_starts(n, P, m)
+    w = boundary_window(n, P, m, window, lookahead)
+    if w == 0:
+        return starts
+    flags, _ = dfa.isets()
+    size = flags.sum(axis=1).astype(np.int64)               # |I_sigma| for every symbol
+    out = list(starts)
+    for k in range(1, P):
+        S = starts[k]
+        sym = dfa.symbols(buf[S - w - 1:S + w])             # symbols before p = S-w .. S+w
+        best = None
+        for i, p in enumerate(range(S - w, S + w + 1)):
+            cost = int(size[sym[i]]) if sym[i] >= 0 else NOT_IN_SIGMA_COST
+            key = (cost, abs(p - S), p)
+            if best is None or key < best:
+                best = key
+        out[k] = best[2]
+    return out
