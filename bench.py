@@ -107,13 +107,18 @@ class Clocks:
         return out
 
 
-def lookups_per_launch(dm, d, dev, n: int, num_chunks: int = 0, lookahead: int = 1) -> tuple:
+def lookups_per_launch(dm, d, dev, n: int, num_chunks: int = 0, lookahead: int = 1,
+                       boundary_window: int = 0) -> tuple:
     """Algorithmic work of one launch (the second term of Eq. 16):
     W = L_0 + sum_{k>=1} L_k |I_k|.  |I_k| comes from the planning kernels
-    (dfa_plan_sets), the chunk lengths from the partition (dfa_partition)."""
-    sizes = d.plan_sets(dev, num_chunks=num_chunks, lookahead=lookahead).astype(np.int64)
+    (dfa_plan_sets), the chunk lengths from the chunk starts the launch uses
+    (dfa_plan_starts: Eqs. 6-7, or the Sec. 4.2 placement)."""
+    sizes = d.plan_sets(dev, num_chunks=num_chunks, lookahead=lookahead,
+                        boundary_window=boundary_window).astype(np.int64)
     P = len(sizes)
-    lens = np.diff(dm.partition(n, P, 1).astype(np.int64))
+    lens = np.diff(d.plan_starts(dev, num_chunks=num_chunks, lookahead=lookahead,
+                                 boundary_window=boundary_window).astype(np.int64))
+    assert len(lens) == P and int(lens.sum()) == n
     W = int((lens * sizes).sum())
     return W, float(sizes[1:].mean()) if P > 1 else 1.0
 
@@ -392,6 +397,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-mix", action="store_true", help="skip the batched and serving legs")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--boundary-window", type=int, default=0,
+                    help="Sec. 4.2 boundary placement window in bytes (0: Eqs. 6-7 starts)")
     ap.add_argument("--tuning", default="",
                     help="K,tiles_per_cta,ctas_per_sm instead of the autotuner (profiling runs)")
     args = ap.parse_args()
@@ -432,16 +439,19 @@ def main():
     n = len(w.data)
     dev = torch.from_numpy(w.data).cuda()
     tuning = None
+    bw = args.boundary_window
     if args.tuning:
         k, tpc, cps = (int(x) for x in args.tuning.split(","))
-        d.set_tuning(states_per_thread=k, tiles_per_cta=tpc, ctas_per_sm=cps)
+        d.set_tuning(states_per_thread=k, tiles_per_cta=tpc, ctas_per_sm=cps, boundary_window=bw)
         tuning = {"states_per_thread": k, "tiles_per_cta": tpc, "ctas_per_sm": cps, "fixed": True}
     elif not w.num_chunks and not args.no_tune:
-        t, _ = d.autotune(dev[: 1 << 30])  # the library's per-DFA tuner (on at most 1 GiB), before any timing
+        # the library's per-DFA tuner (on at most 1 GiB), before any timing
+        t, _ = d.autotune(dev[: 1 << 30], boundary_window=bw)
         tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
                   "ctas_per_sm": t.ctas_per_sm}
-    P = d.plan_chunks(n, num_chunks=w.num_chunks)
-    ws = torch.empty(d.workspace_size(n, num_chunks=w.num_chunks), dtype=torch.uint8, device="cuda")
+    P = d.plan_chunks(n, num_chunks=w.num_chunks, boundary_window=bw)
+    ws = torch.empty(d.workspace_size(n, num_chunks=w.num_chunks, boundary_window=bw),
+                     dtype=torch.uint8, device="cuda")
     out = torch.zeros(12, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
     kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -451,7 +461,8 @@ def main():
 
     def step(i=None, timed=False):
         ev = (kb[i], ke[i]) if timed else None
-        d.match_async(dev, out, ws, stream=stream, num_chunks=w.num_chunks, events=ev)
+        d.match_async(dev, out, ws, stream=stream, num_chunks=w.num_chunks, events=ev,
+                      boundary_window=bw)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -484,11 +495,11 @@ def main():
     # every kernel and the 12-byte result read back, per step
     pinned = torch.from_numpy(w.data).pin_memory()
     e2e_steps = max(3, min(10, args.steps))
-    d.match(pinned)
+    d.match(pinned, boundary_window=bw)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(e2e_steps):
-        d.match(pinned)
+        d.match(pinned, boundary_window=bw)
     e2e_s = (time.perf_counter() - te) / e2e_steps
     # context: this box's plain host-to-device copy rate (the pipelined host
     # path cannot run faster than the copies that feed it)
@@ -510,7 +521,7 @@ def main():
         hbm_peak, sm_max_mhz, peak_src = _peaks()
         props = torch.cuda.get_device_properties(local)
         nsm = props.multi_processor_count
-        W, mean_I = lookups_per_launch(dm, d, dev, n, w.num_chunks)
+        W, mean_I = lookups_per_launch(dm, d, dev, n, w.num_chunks, 1, bw)
         k_avg_s = statistics.mean(k_ms) / 1e3
         lookup_peak = nsm * 32 * sm_max_mhz * 1e6           # 32 shared-memory lanes per clock per SM
         achieved = W / k_avg_s
@@ -524,6 +535,9 @@ def main():
             "config": {"workload": w.name, "states": w.spec.num_states,
                        "classes": int(info.num_classes), "input_bytes": n, "chunks": int(P),
                        "lookahead": 1, "i_max": int(info.i_max), "gamma": round(info.gamma, 4),
+                       "chunk_starts": ("Sec. 4.2 placement within %d bytes of Eqs. 6-7" % bw
+                                        if bw else "Eqs. 6-7"),
+                       "boundary_window": bw, "mean_set": round(mean_I, 3),
                        "tuning": tuning,
                        "l2": "input (%d MiB) larger than L2 (129 MB); no flush needed" % (n >> 20)
                        if n > (129 << 20) else "input smaller than L2",
@@ -543,39 +557,52 @@ def main():
             "e2e": {"value": round(n * world / e2e_s / 1e9, 3), "unit": "GB/s",
                     "h2d_bytes_per_step": n, "d2h_bytes_per_step": 12,
                     "api": "dfa_match (pinned host buffer)", "h2d_copy_gbs": round(h2d_gbs, 1)},
-            "gpu_launches": d.num_kernels(n, num_chunks=w.num_chunks) * args.steps,
+            "gpu_launches": d.num_kernels(n, num_chunks=w.num_chunks, boundary_window=bw) * args.steps,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"]},
             "result": {"final_state": fs, "accept": acc, "status": st},
         }
         if not args.no_mix and args.workload in ("regex", "protein"):
-            # r-symbol reverse lookahead (Eq. 13): same input, smaller initial-state sets
-            la = {}
-            for r in (2, 4):
+            tune = not args.tuning and not args.no_tune
+
+            def leg(r, win, reps=5):
+                """One more configuration of the same test on the same input: its own
+                tuning record, `reps` timed steps (whole step and match kernel alone)."""
                 tr = None
-                if not args.tuning and not args.no_tune:
-                    t, _ = d.autotune(dev[: 1 << 30], lookahead=r)   # this depth's own tuning record
+                if tune:
+                    t, _ = d.autotune(dev[: 1 << 30], lookahead=r, boundary_window=win)
                     tr = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
                           "ctas_per_sm": t.ctas_per_sm}
-                kb2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                ke2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                for e in kb2 + ke2:
+                ev = [[torch.cuda.Event(enable_timing=True) for _ in range(reps)] for _ in range(4)]
+                for e in sum(ev, []):
                     e.record(stream)
+                ws2 = torch.empty(d.workspace_size(n, lookahead=r, boundary_window=win),
+                                  dtype=torch.uint8, device="cuda")
                 with torch.cuda.stream(stream):
-                    d.match_async(dev, out, ws2 := torch.empty(d.workspace_size(n, lookahead=r),
-                                  dtype=torch.uint8, device="cuda"), stream=stream, lookahead=r)
-                    for i in range(3):
-                        d.match_async(dev, out, ws2, stream=stream, lookahead=r, events=(kb2[i], ke2[i]))
+                    d.match_async(dev, out, ws2, stream=stream, lookahead=r, boundary_window=win)
+                    for i in range(reps):
+                        ev[2][i].record(stream)
+                        d.match_async(dev, out, ws2, stream=stream, lookahead=r, boundary_window=win,
+                                      events=(ev[0][i], ev[1][i]))
+                        ev[3][i].record(stream)
                 torch.cuda.synchronize()
-                assert dm.results_from(out)[0] == (fs, acc, st), "lookahead changed the answer"
-                kms = statistics.median(a.elapsed_time(b) for a, b in zip(kb2, ke2))
-                Wr, _ = lookups_per_launch(dm, d, dev, n, 0, r)
-                la["r%d" % r] = {"gbs": round(n / kms / 1e6, 3), "kernel_ms": round(kms, 3),
-                                 "lookups_per_byte": round(Wr / n, 3),
-                                 "lookup_roof_frac": round(Wr / (kms / 1e3) / lookup_peak, 4),
-                                 "tuning": tr}
+                assert dm.results_from(out)[0] == (fs, acc, st), "the answer changed"
+                kms = statistics.median(a.elapsed_time(b) for a, b in zip(ev[0], ev[1]))
+                sms = statistics.median(a.elapsed_time(b) for a, b in zip(ev[2], ev[3]))
+                Wr, mI = lookups_per_launch(dm, d, dev, n, 0, r, win)
                 del ws2
-            line["lookahead"] = la
+                return {"gbs": round(n / sms / 1e6, 3), "step_ms": round(sms, 4),
+                        "kernel_gbs": round(n / kms / 1e6, 3), "kernel_ms": round(kms, 4),
+                        "lookups_per_byte": round(Wr / n, 3), "mean_set": round(mI, 3),
+                        "lookup_roof_frac": round(Wr / (kms / 1e3) / lookup_peak, 4),
+                        "boundary_window": win, "tuning": tr}
+
+            # r-symbol reverse lookahead (Eq. 13): same input, smaller initial-state sets
+            line["lookahead"] = {"r%d" % r: leg(r, bw) for r in (2, 4)}
+            if bw:   # the chunk starts of Eqs. 6-7, for comparison
+                line["eqs_6_7"] = {"r1": leg(1, 0)}
+            else:    # Sec. 4.2 boundary placement
+                line["placement"] = {"r%d" % r: leg(r, 256) for r in (1, 4)}
         if not args.no_mix and args.workload == "regex":
             mix = _mixed_strings(w.spec, 11, 384, 256, 8 << 20)
             bl, res_b = batched_leg(dm, [d] * len(mix), mix)

@@ -101,7 +101,22 @@ typedef struct {
                               0 = Algorithm 2 (every chunk matched from all of Q),
                               2..8 = the r-symbol sets of Eq. (13), computed per
                               chunk on the device                                 */
-    uint32_t reserved;
+    uint32_t boundary_window; /* Sec. 4.2's boundary placement ("divide the input at
+                              boundaries with reverse lookahead symbols that have a
+                              small initial state set"): 0 = the chunk starts of
+                              Eqs. (6)-(7) (the default); w > 0 = on the device,
+                              each start S of a chunk k >= 1 moves to the position
+                              p in [S - w', S + w'] whose preceding byte has the
+                              smallest |I_class| (a byte outside Sigma counts as
+                              larger than any set), ties to the p nearest S, then
+                              to the smaller p.  w' = min(w, floor(len / (m + P -
+                              1)) / 4): a quarter of the shortest later chunk, so
+                              starts stay increasing.  Chunk k's set (and, for
+                              lookahead >= 2, its Eq. (13) set) is then taken at
+                              the placed start.  Ignored by Algorithm 2
+                              (lookahead 0).  At most 65536 (DFA_EINVAL above).
+                              The answer never depends on it (failure-freedom);
+                              the work sum_k L_k |I_k| usually drops.           */
     void *match_begin_event; /* optional cudaEvent_t recorded on the stream right before  */
     void *match_end_event;   /* ... and right after the match kernel (for timing it alone) */
 } dfa_match_opts_t;
@@ -170,12 +185,16 @@ int dfa_autotune(dfa_t *dfa, const uint8_t *dev_sample, uint64_t len, void *stre
  * dfa_get_tuning / dfa_set_tuning / dfa_autotune read and write, used for
  * lookahead 1) and may keep one record per other depth r = opts->lookahead
  * (0 = Algorithm 2, 2..8 = Eq. (13) sets): the sets shrink as r grows, so the
- * best chains per thread and tiles per CTA differ.  A depth without its own
- * record uses the base record.  These three calls read, write or autotune the
- * record of opts->lookahead (opts NULL = lookahead 1 = the base record).
- * dfa_autotune_opts times launches with that lookahead (k_lookahead
+ * best chains per thread and tiles per CTA differ.  Each depth r >= 1 also
+ * has a record for launches with Sec. 4.2 boundary placement
+ * (opts->boundary_window > 0), whose sets are smaller still.  A placed record
+ * that was never set reads as its depth's record, and a depth without its own
+ * record as the base record.  These three calls read, write or autotune the
+ * record of (opts->lookahead, opts->boundary_window > 0) (opts NULL =
+ * lookahead 1 without placement = the base record).  dfa_autotune_opts times
+ * launches with that lookahead and window (k_lookahead, k_boundaries
  * included).  Errors: as dfa_get_tuning / dfa_set_tuning / dfa_autotune, and
- * DFA_EINVAL for a lookahead above 8.
+ * DFA_EINVAL for a lookahead above 8 or a window above 65536.
  */
 int dfa_get_tuning_opts(const dfa_t *dfa, const dfa_match_opts_t *opts, dfa_tuning_t *out);
 int dfa_set_tuning_opts(dfa_t *dfa, const dfa_match_opts_t *opts, const dfa_tuning_t *tuning);
@@ -225,8 +244,21 @@ int dfa_match(const dfa_t *dfa, const uint8_t *str, uint64_t len, const dfa_matc
               dfa_result_t *out);
 
 /* Number of chunks P the planner uses for a single test of len bytes
- * (opts->num_chunks when given); the partition is then dfa_partition(len, P, m). */
+ * (opts->num_chunks when given); the partition is then dfa_partition(len, P, m),
+ * or, with opts->boundary_window, the placed starts of dfa_plan_starts. */
 int dfa_plan_chunks(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts, uint32_t *P);
+
+/*
+ * Inspection: the chunk boundaries a single test of dev_str (device, len
+ * bytes) uses: starts[0] = 0, starts[k] = the start of chunk k, starts[P] =
+ * len (P + 1 entries; at most cap written; *P receives the chunk count).
+ * Without a placement window these are Eqs. (6)-(7) and nothing runs on the
+ * device; with opts->boundary_window the placement kernel runs on dev_str
+ * (Sec. 4.2) and its starts are copied back (temporary workspace, device
+ * synchronised).  Errors: DFA_EINVAL, DFA_ENOMEM, DFA_ECUDA, DFA_EHOSTONLY.
+ */
+int dfa_plan_starts(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
+                    const dfa_match_opts_t *opts, uint64_t *starts, uint32_t cap, uint32_t *P);
 
 /*
  * Inspection: run only the planning kernels of a single test on dev_str and
@@ -240,8 +272,8 @@ int dfa_plan_sets(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
 
 /* Kernel launches one dfa_match_async / dfa_match call issues for (dfa, len,
  * opts): the planning kernels (one fused kernel for plans of at most 2048
- * chunks, else four), k_lookahead when opts->lookahead >= 2, and the match
- * kernel. */
+ * chunks, else four), k_boundaries when a placement window applies,
+ * k_lookahead when opts->lookahead >= 2, and the match kernel. */
 int dfa_match_num_kernels(const dfa_t *dfa, uint64_t len, const dfa_match_opts_t *opts,
                           uint32_t *n);
 

@@ -53,7 +53,7 @@ class Tuning(ctypes.Structure):
 
 class MatchOpts(ctypes.Structure):
     _fields_ = [("num_chunks", ctypes.c_uint32), ("multiplicity", ctypes.c_uint32),
-                ("lookahead", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("lookahead", ctypes.c_uint32), ("boundary_window", ctypes.c_uint32),
                 ("match_begin_event", ctypes.c_void_p), ("match_end_event", ctypes.c_void_p)]
 
 
@@ -89,6 +89,7 @@ SIGNATURES = {
     "dfa_plan_chunks": (_I, [_P, _U64, _P, _P]),
     "dfa_match_num_kernels": (_I, [_P, _U64, _P, _P]),
     "dfa_plan_sets": (_I, [_P, _P, _U64, _P, _P, _U32, _P]),
+    "dfa_plan_starts": (_I, [_P, _P, _U64, _P, _P, _U32, _P]),
     "dfa_debug_chunk_maps": (_I, [_P, _P, _U64, _P, _P, _U32, _P, _P]),
     "dfa_match_workspace_size": (_I, [_P, _U64, _P, _P]),
     "dfa_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
@@ -135,9 +136,11 @@ def _check(rc: int, what: str):
         raise DfaError(rc, what)
 
 
-def _opts(num_chunks=0, multiplicity=0, lookahead=1, events=None) -> MatchOpts:
+def _opts(num_chunks=0, multiplicity=0, lookahead=1, events=None, boundary_window=0) -> MatchOpts:
+    """boundary_window: Sec. 4.2 placement of the chunk starts (0: Eqs. 6-7)."""
     ev = (None, None) if events is None else (events[0].cuda_event, events[1].cuda_event)
-    return MatchOpts(int(num_chunks), int(multiplicity), int(lookahead), 0, ev[0], ev[1])
+    return MatchOpts(int(num_chunks), int(multiplicity), int(lookahead), int(boundary_window),
+                     ev[0], ev[1])
 
 
 def partition(n: int, P: int, m: int = 1) -> np.ndarray:
@@ -216,34 +219,35 @@ class Dfa:
         _check(lib().dfa_info(self._h, ctypes.byref(out)), "dfa_info")
         return out
 
-    def tuning(self, lookahead: int = 1) -> Tuning:
-        """The tuning record used for launches with this lookahead (1: the base record)."""
+    def tuning(self, lookahead: int = 1, boundary_window: int = 0) -> Tuning:
+        """The tuning record used for launches with this lookahead (1: the base
+        record) and, with boundary_window > 0, Sec. 4.2 placement."""
         t = Tuning()
-        o = _opts(lookahead=lookahead)
+        o = _opts(lookahead=lookahead, boundary_window=boundary_window)
         _check(lib().dfa_get_tuning_opts(self._h, ctypes.byref(o), ctypes.byref(t)),
                "dfa_get_tuning_opts")
         return t
 
     def set_tuning(self, states_per_thread: int = 0, tiles_per_cta: int = 0,
                    min_chunk_bytes: int = 0, batch_chunk_bytes: int = 0, ctas_per_sm: int = 0,
-                   host_segment_bytes: int = 0, lookahead: int = 1):
+                   host_segment_bytes: int = 0, lookahead: int = 1, boundary_window: int = 0):
         """host_segment_bytes: first segment of dfa_match's copy/match pipeline for
         host input (0 = automatic, 0xFFFFFFFF = copy the whole string first).
         lookahead: the depth whose record is set (1: the base record)."""
         t = Tuning(states_per_thread, tiles_per_cta, min_chunk_bytes, batch_chunk_bytes, ctas_per_sm,
                    host_segment_bytes)
-        o = _opts(lookahead=lookahead)
+        o = _opts(lookahead=lookahead, boundary_window=boundary_window)
         _check(lib().dfa_set_tuning_opts(self._h, ctypes.byref(o), ctypes.byref(t)),
                "dfa_set_tuning_opts")
 
-    def autotune(self, dev_sample, stream=None, lookahead: int = 1):
+    def autotune(self, dev_sample, stream=None, lookahead: int = 1, boundary_window: int = 0):
         """Time the candidate tunings on a device sample (launches with this
-        lookahead) and keep the fastest in that lookahead's record.
+        lookahead and placement window) and keep the fastest in that record.
         Returns (Tuning, best_ms)."""
         t = Tuning()
         ms = ctypes.c_double()
         n = dev_sample.numel()
-        o = _opts(lookahead=lookahead)
+        o = _opts(lookahead=lookahead, boundary_window=boundary_window)
         _check(lib().dfa_autotune_opts(self._h, dev_sample.data_ptr() if n else None, n,
                                        ctypes.byref(o), _stream_ptr(stream), ctypes.byref(t),
                                        ctypes.byref(ms)),
@@ -264,11 +268,11 @@ class Dfa:
 
     # -------------------------------------------------------------- matching
     def match(self, data, num_chunks: int = 0, multiplicity: int = 0, lookahead: int = 1,
-              events=None):
+              events=None, boundary_window: int = 0):
         """Synchronous test.  data: bytes / numpy uint8 / a (pinned) CPU tensor, or a
         CUDA uint8 tensor.  Returns (status, final_state, accept)."""
         res = Result()
-        o = _opts(num_chunks, multiplicity, lookahead, events)
+        o = _opts(num_chunks, multiplicity, lookahead, events, boundary_window)
         if hasattr(data, "data_ptr"):
             ptr, n, keep = data.data_ptr(), data.numel(), data
         else:
@@ -285,24 +289,26 @@ class Dfa:
         return OK, int(res.final_state), bool(res.accept)
 
     def plan_chunks(self, n: int, num_chunks: int = 0, multiplicity: int = 0,
-                    lookahead: int = 1) -> int:
+                    lookahead: int = 1, boundary_window: int = 0) -> int:
         out = ctypes.c_uint32()
-        o = _opts(num_chunks, multiplicity, lookahead)
+        o = _opts(num_chunks, multiplicity, lookahead, None, boundary_window)
         _check(lib().dfa_plan_chunks(self._h, n, ctypes.byref(o), ctypes.byref(out)),
                "dfa_plan_chunks")
         return int(out.value)
 
-    def num_kernels(self, n: int, num_chunks: int = 0, lookahead: int = 1) -> int:
+    def num_kernels(self, n: int, num_chunks: int = 0, lookahead: int = 1,
+                    boundary_window: int = 0) -> int:
         out = ctypes.c_uint32()
-        o = _opts(num_chunks, 0, lookahead)
+        o = _opts(num_chunks, 0, lookahead, None, boundary_window)
         _check(lib().dfa_match_num_kernels(self._h, n, ctypes.byref(o), ctypes.byref(out)),
                "dfa_match_num_kernels")
         return int(out.value)
 
-    def chunk_maps(self, dev_data, num_chunks: int = 0, lookahead: int = 1):
+    def chunk_maps(self, dev_data, num_chunks: int = 0, lookahead: int = 1,
+                   boundary_window: int = 0):
         """(L maps [P, |Q|+1] uint16, final_state): the chunk maps of Sec. 4.1 as the
         match kernel computed them (identity outside each chunk's I_k)."""
-        o = _opts(num_chunks, 0, lookahead)
+        o = _opts(num_chunks, 0, lookahead, None, boundary_window)
         n = dev_data.numel()
         P = ctypes.c_uint32()
         ptr = dev_data.data_ptr() if n else None
@@ -316,9 +322,9 @@ class Dfa:
         return out, int(fs.value)
 
     def plan_sets(self, dev_data, num_chunks: int = 0, multiplicity: int = 0,
-                  lookahead: int = 1) -> np.ndarray:
+                  lookahead: int = 1, boundary_window: int = 0) -> np.ndarray:
         """|I_k| of every chunk of a single test on dev_data (planning kernels only)."""
-        o = _opts(num_chunks, multiplicity, lookahead)
+        o = _opts(num_chunks, multiplicity, lookahead, None, boundary_window)
         n = dev_data.numel()
         P = ctypes.c_uint32()
         _check(lib().dfa_plan_sets(self._h, dev_data.data_ptr() if n else None, n, ctypes.byref(o),
@@ -328,21 +334,37 @@ class Dfa:
                                    out.ctypes.data, P.value, ctypes.byref(P)), "dfa_plan_sets")
         return out[: P.value]
 
+    def plan_starts(self, dev_data, num_chunks: int = 0, multiplicity: int = 0,
+                    lookahead: int = 1, boundary_window: int = 0) -> np.ndarray:
+        """Chunk boundaries [0, start_1, ..., start_{P-1}, n] of a single test on
+        dev_data: Eqs. (6)-(7), or the Sec. 4.2 placement with boundary_window."""
+        o = _opts(num_chunks, multiplicity, lookahead, None, boundary_window)
+        n = dev_data.numel()
+        ptr = dev_data.data_ptr() if n else None
+        P = ctypes.c_uint32()
+        _check(lib().dfa_plan_starts(self._h, ptr, n, ctypes.byref(o), None, 0, ctypes.byref(P)),
+               "dfa_plan_starts")
+        out = np.zeros(P.value + 1, dtype=np.uint64)
+        _check(lib().dfa_plan_starts(self._h, ptr, n, ctypes.byref(o), out.ctypes.data, P.value + 1,
+                                     ctypes.byref(P)), "dfa_plan_starts")
+        return out
+
     def workspace_size(self, n: int, num_chunks: int = 0, multiplicity: int = 0,
-                       lookahead: int = 1) -> int:
+                       lookahead: int = 1, boundary_window: int = 0) -> int:
         out = ctypes.c_uint64()
-        o = _opts(num_chunks, multiplicity, lookahead)
+        o = _opts(num_chunks, multiplicity, lookahead, None, boundary_window)
         _check(lib().dfa_match_workspace_size(self._h, n, ctypes.byref(o), ctypes.byref(out)),
                "dfa_match_workspace_size")
         return int(out.value)
 
     def match_async(self, dev_data, dev_out, workspace, stream=None, num_chunks: int = 0,
-                    multiplicity: int = 0, lookahead: int = 1, events=None):
+                    multiplicity: int = 0, lookahead: int = 1, events=None,
+                    boundary_window: int = 0):
         """Enqueue a test on `stream` (torch stream; default: current).  dev_data: CUDA
         uint8 tensor; dev_out: CUDA uint8 tensor of >= 12 bytes; workspace: CUDA uint8
         tensor of >= workspace_size() bytes; events: optional (begin, end) torch.cuda.Event
         pair recorded around the match kernel."""
-        o = _opts(num_chunks, multiplicity, lookahead, events)
+        o = _opts(num_chunks, multiplicity, lookahead, events, boundary_window)
         n = dev_data.numel()
         rc = lib().dfa_match_async(self._h, dev_data.data_ptr() if n else None, n, ctypes.byref(o),
                                    dev_out.data_ptr(), workspace.data_ptr(), workspace.numel(),
@@ -350,10 +372,10 @@ class Dfa:
         _check(rc, "dfa_match_async")
 
     def match_noalloc(self, dev_data, dev_out, stream=None, num_chunks: int = 0,
-                      multiplicity: int = 0, lookahead: int = 1):
+                      multiplicity: int = 0, lookahead: int = 1, boundary_window: int = 0):
         """Enqueue a test that uses the library's fixed scratch array instead of a
         workspace (see dfa_match_noalloc: calls sharing a device must not overlap)."""
-        o = _opts(num_chunks, multiplicity, lookahead)
+        o = _opts(num_chunks, multiplicity, lookahead, None, boundary_window)
         n = dev_data.numel()
         rc = lib().dfa_match_noalloc(self._h, dev_data.data_ptr() if n else None, n,
                                      ctypes.byref(o), dev_out.data_ptr(), _stream_ptr(stream))
@@ -374,14 +396,14 @@ class Batch:
     many times as one persistent launch (optionally replayed from a CUDA graph)."""
 
     def __init__(self, dfas: Sequence[Dfa], tensors, num_chunks: int = 0, multiplicity: int = 0,
-                 lookahead: int = 1):
+                 lookahead: int = 1, boundary_window: int = 0):
         self._dfas = list(dfas)
         self._tensors = list(tensors)
         n = len(self._tensors)
         dp = _ptr_array([d.handle.value for d in self._dfas])
         sp = _ptr_array([t.data_ptr() if t.numel() else 0 for t in self._tensors])
         lens = np.array([t.numel() for t in self._tensors], dtype=np.uint64)
-        o = _opts(num_chunks, multiplicity, lookahead)
+        o = _opts(num_chunks, multiplicity, lookahead, None, boundary_window)
         h = ctypes.c_void_p()
         _check(lib().dfa_batch_prepare(n, dp, sp, lens.ctypes.data, ctypes.byref(o),
                                        ctypes.byref(h)), "dfa_batch_prepare")
@@ -414,7 +436,7 @@ class Batch:
 
 
 def match_batch(dfas: Sequence[Dfa], tensors, stream=None, num_chunks: int = 0,
-                multiplicity: int = 0, lookahead: int = 1):
+                multiplicity: int = 0, lookahead: int = 1, boundary_window: int = 0):
     """One-shot batched test through dfa_match_batch; returns (final, accept, status) tuples."""
     torch = _torch()
     n = len(tensors)
@@ -422,7 +444,7 @@ def match_batch(dfas: Sequence[Dfa], tensors, stream=None, num_chunks: int = 0,
     dp = _ptr_array([d.handle.value for d in dfas])
     sp = _ptr_array([t.data_ptr() if t.numel() else 0 for t in tensors])
     lens = np.array([t.numel() for t in tensors], dtype=np.uint64)
-    o = _opts(num_chunks, multiplicity, lookahead)
+    o = _opts(num_chunks, multiplicity, lookahead, None, boundary_window)
     _check(lib().dfa_match_batch(n, dp, sp, lens.ctypes.data, ctypes.byref(o), out.data_ptr(),
                                  _stream_ptr(stream)), "dfa_match_batch")
     return results_from(out)

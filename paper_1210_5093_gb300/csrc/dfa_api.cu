@@ -18,7 +18,7 @@ uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint
                           uint32_t* stage_bytes, uint32_t target);
 uint32_t match_target_ctas(uint32_t kmax, uint32_t want);
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
-uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn);
+uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn, bool bnd);
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
                 uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr,
                 bool plan_only = false);
@@ -36,7 +36,7 @@ inline uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
 WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t ptot, uint32_t nblk,
                    uint32_t grid, uint32_t stride, bool inline_desc, bool dyn = false,
-                   uint64_t set_entries = 0) {
+                   uint64_t set_entries = 0, bool bnd = false) {
     WsLayout w;
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) { uint64_t r = o; o = up(o + bytes, 256); return r; };
@@ -62,6 +62,7 @@ WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t pt
     w.seg_vals = take(2ull * stride * (grid + ntests));
     w.set_size = take(dyn ? 4ull * ptot : 0);
     w.sets = take(dyn ? 2ull * set_entries : 0);
+    w.starts = take(bnd ? 8ull * ptot : 0);
     w.total = o;
     return w;
 }
@@ -88,18 +89,42 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
     lp.seg_vals = reinterpret_cast<uint16_t*>(base + w.seg_vals);
     lp.set_size = reinterpret_cast<uint32_t*>(base + w.set_size);
     lp.sets = reinterpret_cast<uint16_t*>(base + w.sets);
+    lp.starts = reinterpret_cast<uint64_t*>(base + w.starts);
 }
 
 // Reverse-lookahead symbols requested by opts: 1 (Algorithm 3) by default,
 // 0 for Algorithm 2, up to kMaxLookahead for Eq. (13).
 inline uint32_t opts_lookahead(const dfa_match_opts_t* o) { return o ? o->lookahead : 1u; }
+// Sec. 4.2 placement window requested by opts (0: the starts of Eqs. 6-7).
+inline uint32_t opts_window(const dfa_match_opts_t* o) { return o ? o->boundary_window : 0u; }
+// The tuning slot of a call: its lookahead depth, placed or not.  Algorithm 2
+// has no lookahead symbol to place by, so it always takes the unplaced slot.
+inline uint32_t opts_slot(const dfa_match_opts_t* o) {
+    const uint32_t r = opts_lookahead(o);
+    return tuning_slot(r, r != 0 && opts_window(o) != 0);
+}
+inline bool opts_valid(const dfa_match_opts_t* o) {
+    return opts_lookahead(o) <= kMaxLookahead && opts_window(o) <= kMaxBoundaryWindow;
+}
+
+// The window a test of n bytes in P chunks (multiplicity m) actually searches:
+// at most a quarter of floor(n / (m + P - 1)), the shortest chunk after the
+// first, so the window lies inside the string and placed starts stay strictly
+// increasing; none for Algorithm 2 or a single chunk.
+uint32_t test_window(const dfa_match_opts_t* o, uint64_t n, uint32_t P, uint32_t m) {
+    const uint32_t w = opts_window(o);
+    if (w == 0 || opts_lookahead(o) == 0 || P <= 1) return 0;
+    const uint64_t quarter = n / ((uint64_t)m + P - 1) / 4;
+    return (uint32_t)std::min<uint64_t>(w, quarter);
+}
 inline uint32_t seg_stride_for(uint32_t qe_max) { return (qe_max + 1) & ~1u; }
 
-// Launch-specific copy of a DFA's device descriptor.  K is raised when the
-// largest set the launch matches would not fit one tile.
-DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
+// Launch-specific copy of a DFA's device descriptor for a tuning slot.  K is
+// raised when the largest set the launch matches would not fit one tile.
+DevDfa launch_desc(const dfa_t* d, uint32_t slot) {
     DevDfa x = d->dev;
-    const uint32_t tk = d->tuning_for(lookahead).states_per_thread;
+    const uint32_t lookahead = slot_lookahead(slot);
+    const uint32_t tk = d->tuning_for(slot).states_per_thread;
     x.K = tk ? tk : d->h.K;
     const uint32_t vmax = lookahead ? std::max(d->h.imax, 1u) : d->h.qe;
     while ((vmax + x.K - 1) / x.K > (uint32_t)kThreads / 2 && x.K < 16) x.K *= 2;
@@ -113,7 +138,7 @@ DevDfa launch_desc(const dfa_t* d, uint32_t lookahead) {
 // a launch holding little input gets shorter chunks and so more parallelism.
 uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_opts_t* o,
                      bool batched, uint64_t batch_cap) {
-    const dfa_tuning_t& tu = d->tuning_for(opts_lookahead(o));
+    const dfa_tuning_t& tu = d->tuning_for(opts_slot(o));
     uint64_t P;
     if (o && o->num_chunks) {
         P = o->num_chunks;
@@ -122,15 +147,20 @@ uint32_t plan_chunks(const dfa_t* d, uint64_t n, uint32_t grid, const dfa_match_
         if (batch_cap) L = std::min(L, batch_cap);
         P = (n + L - 1) / L;
     } else {
-        // enough lane tasks for kTilesPerCta tiles on every CTA, chunks >= kMinChunk
-        double mean_cost = 0;
+        // enough lane tasks for kTilesPerCta tiles on every CTA, chunks >= kMinChunk;
+        // a chunk costs its set's thread slots: the mean over the classes, or with
+        // Sec. 4.2 placement the smallest set (the one the placement looks for)
+        double mean_cost = 0, min_cost = 1e30;
         const HostDfa& h = d->h;
         for (uint32_t c = 0; c < h.C; ++c) {
             uint32_t sz = h.iset_off[c + 1] - h.iset_off[c];
             const uint32_t K = tu.states_per_thread ? tu.states_per_thread : h.K;
-            mean_cost += std::max((sz + K - 1) / K, 2u);
+            const double cost = std::max((sz + K - 1) / K, 2u);
+            mean_cost += cost;
+            min_cost = std::min(min_cost, cost);
         }
         mean_cost = h.C ? mean_cost / h.C : 2.0;
+        if (h.C && opts_slot(o) > kMaxLookahead) mean_cost = min_cost;
         const uint32_t tpc = tu.tiles_per_cta ? tu.tiles_per_cta : kTilesPerCta;
         double want = (double)grid * kThreads * tpc * 0.9 / mean_cost;
         uint64_t by_len = n / (tu.min_chunk_bytes ? tu.min_chunk_bytes : kMinChunk);
@@ -146,8 +176,8 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
             const uint64_t* lens, const dfa_match_opts_t* opts, bool batched, Prepared* out,
             const uint32_t* out_ids) {
     if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
-    const uint32_t lookahead = opts_lookahead(opts);
-    if (lookahead > kMaxLookahead) return DFA_EINVAL;
+    if (!opts_valid(opts)) return DFA_EINVAL;
+    const uint32_t lookahead = opts_lookahead(opts), slot = opts_slot(opts);
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     Prepared p;
     // group tests by DFA (stable), unique DFAs in first-seen order
@@ -165,7 +195,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         }
     }
     for (const dfa_t* d : uniq) {
-        DevDfa x = launch_desc(d, lookahead);
+        DevDfa x = launch_desc(d, slot);
         if (uniq.size() > 1) {
             // One launch has one kernel variant and one shared-memory layout,
             // sized for its largest K and largest shared-memory table.  In a
@@ -214,6 +244,8 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         t.qinv = recip64((uint64_t)m + t.P - 1);
         t.chunk_base = (uint32_t)chunks;
         t.lookahead = lookahead;
+        t.window = test_window(opts, t.n, t.P, m);
+        p.bnd |= t.window ? 1u : 0u;
         t.out = out_ids ? out_ids[i] : i;
         if (p.groups.empty() || p.groups.back().dfa != t.dfa) {
             if (!p.groups.empty()) {
@@ -242,7 +274,8 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
     }
     p.dyn = lookahead >= 2 ? 1u : 0u;
     p.ws = ws_layout((uint32_t)p.dfas.size(), count, (uint32_t)p.groups.size(), p.ptot, p.nblk,
-                     p.grid, seg_stride_for(p.qe_max), false, p.dyn != 0, p.set_entries);
+                     p.grid, seg_stride_for(p.qe_max), false, p.dyn != 0, p.set_entries,
+                     p.bnd != 0);
     *out = std::move(p);
     return DFA_OK;
 }
@@ -259,6 +292,7 @@ void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out
     lp.vcap = p.vcap;
     lp.qe_max = p.qe_max;
     lp.dyn = p.dyn;
+    lp.bnd = p.bnd;
     lp.stage_bytes = p.stage;
     lp.dfas = reinterpret_cast<const DevDfa*>(ws + p.ws.dfas);
     lp.tests = reinterpret_cast<const DevTest*>(ws + p.ws.tests);
@@ -308,15 +342,15 @@ int launch_single(const Single& s, void* stream, void* ev_begin, void* ev_end) {
 int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Single* s) {
     if (!d) return DFA_EINVAL;
     if (!d->on_device) return DFA_EHOSTONLY;
-    const uint32_t lookahead = opts_lookahead(opts);
-    if (lookahead > kMaxLookahead) return DFA_EINVAL;
+    if (!opts_valid(opts)) return DFA_EINVAL;
+    const uint32_t lookahead = opts_lookahead(opts), slot = opts_slot(opts);
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
-    DevDfa x = launch_desc(d, lookahead);
+    DevDfa x = launch_desc(d, slot);
     const uint32_t tcap = x.placement == kSmem ? (uint32_t)up(x.table_bytes, 16) : 0u;
     s->kmax = x.K;
     uint32_t stage = 0;
     s->smem = match_smem_bytes(tcap, x.K, x.vcap, stage_esz(x.stage_fmt), &stage,
-                               match_target_ctas(x.K, d->tuning_for(lookahead).ctas_per_sm));
+                               match_target_ctas(x.K, d->tuning_for(slot).ctas_per_sm));
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
@@ -334,7 +368,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.stage_bytes = stage;
     lp.qe_max = x.qe;
     lp.dyn = lookahead >= 2 ? 1u : 0u;
-    lp.dfas = d->dev_desc_for(lookahead);
+    lp.dfas = d->dev_desc_for(slot);
     lp.tests = nullptr;
     lp.groups = nullptr;
     lp.test1.str = nullptr;
@@ -346,6 +380,8 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.test1.chunk_base = 0;
     lp.test1.group = 0;
     lp.test1.lookahead = lookahead;
+    lp.test1.window = test_window(opts, len, P, m);
+    lp.bnd = lp.test1.window ? 1u : 0u;
     lp.test1.out = 0;
     lp.group1.first_chunk = 0;
     lp.group1.end_chunk = P;
@@ -354,7 +390,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.group1.set_stride = std::max(d->h.imax, 1u);
     lp.group1.set_base = 0;
     s->ws = ws_layout(1, 1, 1, P, lp.nblk, grid, lp.seg_stride, true, lp.dyn != 0,
-                      (uint64_t)P * lp.group1.set_stride);
+                      (uint64_t)P * lp.group1.set_stride, lp.bnd != 0);
     return DFA_OK;
 }
 
@@ -369,15 +405,15 @@ int prepare_parts(uint32_t count, const dfa_t* const* dfas, const uint8_t* const
                   const uint64_t* lens, const dfa_match_opts_t* opts, std::vector<Prepared>* parts,
                   std::vector<uint64_t>* ws_off, uint64_t* ws_total) {
     if (count == 0 || !dfas || !strs || !lens) return DFA_EINVAL;
-    const uint32_t lookahead = opts_lookahead(opts);
-    if (lookahead > kMaxLookahead) return DFA_EINVAL;
+    if (!opts_valid(opts)) return DFA_EINVAL;
+    const uint32_t slot = opts_slot(opts);
     std::vector<uint32_t> ids[2];
     const dfa_t* first = dfas[0];
     bool several = false;
     for (uint32_t i = 0; i < count; ++i) {
         if (!dfas[i]) return DFA_EINVAL;
         several |= dfas[i] != first;
-        const DevDfa x = launch_desc(dfas[i], lookahead);
+        const DevDfa x = launch_desc(dfas[i], slot);
         const bool smem = x.placement == kSmem && x.table_bytes <= kBatchSmemTable;
         ids[smem ? 0 : 1].push_back(i);
     }
@@ -417,14 +453,14 @@ using namespace dfam;
 
 // ------------------------------------------------------------------ dfa_t
 
-const DevDfa* dfa_s::dev_desc_for(uint32_t lookahead) const { return dev_desc + lookahead; }
+const DevDfa* dfa_s::dev_desc_for(uint32_t slot) const { return dev_desc + slot; }
 
-// Uploads the launch descriptors of every lookahead depth (their K follows
-// the depth's tuning record).
+// Uploads the launch descriptors of every tuning slot (their K follows the
+// slot's tuning record).
 static int upload_descs(dfa_t* d) {
     if (!d->dev_desc) return DFA_OK;  // a host-only DFA
-    DevDfa descs[kMaxLookahead + 1];
-    for (uint32_t r = 0; r <= kMaxLookahead; ++r) descs[r] = launch_desc(d, r);
+    DevDfa descs[kTuningSlots];
+    for (uint32_t r = 0; r < kTuningSlots; ++r) descs[r] = launch_desc(d, r);
     return cudaMemcpy(d->dev_desc, descs, sizeof descs, cudaMemcpyHostToDevice) == cudaSuccess
                ? DFA_OK
                : DFA_ECUDA;
@@ -470,7 +506,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         }
         uint64_t o = 0;
         auto take = [&](uint64_t bytes) { uint64_t r = o; o = up(o + bytes, 256); return r; };
-        const uint64_t o_desc = take((kMaxLookahead + 1) * sizeof(DevDfa));
+        const uint64_t o_desc = take(kTuningSlots * sizeof(DevDfa));
         const uint64_t o_table = take(h.table.size());
         const uint64_t o_b16 = take(512), o_b32 = take(1024), o_bc = take(512);
         const uint64_t o_ioff = take(4 * h.iset_off.size()), o_iset = take(2 * h.iset.size());
@@ -556,17 +592,17 @@ int dfa_info(const dfa_t* d, dfa_info_t* o) {
     return DFA_OK;
 }
 
-// Tuning record of lookahead depth r: the base record for r == 1 (and for
-// depths without their own record when read).
+// Tuning record of a slot (lookahead depth, placed or not): the base record
+// for depth 1 unplaced (and for slots without their own record when read).
 static int get_tuning_r(const dfa_t* d, uint32_t r, dfa_tuning_t* out) {
-    if (!d || !out || r > kMaxLookahead) return DFA_EINVAL;
+    if (!d || !out || r >= kTuningSlots) return DFA_EINVAL;
     *out = d->tuning_for(r);
     if (!out->states_per_thread) out->states_per_thread = d->h.K;
     return DFA_OK;
 }
 
 static int set_tuning_r(dfa_t* d, uint32_t r, const dfa_tuning_t* t) {
-    if (!d || !t || r > kMaxLookahead) return DFA_EINVAL;
+    if (!d || !t || r >= kTuningSlots) return DFA_EINVAL;
     const uint32_t K = t->states_per_thread ? t->states_per_thread : d->h.K;
     if (K != 2 && K != 4 && K != 8 && K != 16) return DFA_EINVAL;
     if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) return DFA_EINVAL;
@@ -583,17 +619,20 @@ static int set_tuning_r(dfa_t* d, uint32_t r, const dfa_tuning_t* t) {
     return upload_descs(d);
 }
 
-// Times every candidate tuning on a device sample with lookahead r and keeps
-// the fastest in r's record.
-static int autotune_r(dfa_t* d, uint32_t r, const uint8_t* dev_sample, uint64_t len, void* stream,
-                      dfa_tuning_t* chosen, double* best_ms) {
-    if (!d || (len && !dev_sample) || r > kMaxLookahead) return DFA_EINVAL;
+// Times every candidate tuning on a device sample with the lookahead and
+// placement window of `base` (NULL: lookahead 1, no placement) and keeps the
+// fastest in that slot's record.
+static int autotune_r(dfa_t* d, const dfa_match_opts_t* base, const uint8_t* dev_sample,
+                      uint64_t len, void* stream, dfa_tuning_t* chosen, double* best_ms) {
+    if (!d || (len && !dev_sample) || !opts_valid(base)) return DFA_EINVAL;
     if (!d->on_device) return DFA_EHOSTONLY;
+    const uint32_t r = opts_slot(base);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     dfa_tuning_t saved;
     get_tuning_r(d, r, &saved);
     dfa_match_opts_t o{};
-    o.lookahead = r;
+    o.lookahead = opts_lookahead(base);
+    o.boundary_window = opts_window(base);
     std::vector<dfa_tuning_t> cands;
     for (uint32_t K : {2u, 4u, 8u, 16u}) {
         if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) continue;
@@ -706,21 +745,23 @@ int dfa_set_tuning(dfa_t* d, const dfa_tuning_t* t) { return set_tuning_r(d, 1, 
 
 int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream,
                  dfa_tuning_t* chosen, double* best_ms) {
-    return autotune_r(d, 1, dev_sample, len, stream, chosen, best_ms);
+    return autotune_r(d, nullptr, dev_sample, len, stream, chosen, best_ms);
 }
 
 int dfa_get_tuning_opts(const dfa_t* d, const dfa_match_opts_t* opts, dfa_tuning_t* out) {
-    return get_tuning_r(d, opts_lookahead(opts), out);
+    if (!opts_valid(opts)) return DFA_EINVAL;
+    return get_tuning_r(d, opts_slot(opts), out);
 }
 
 int dfa_set_tuning_opts(dfa_t* d, const dfa_match_opts_t* opts, const dfa_tuning_t* t) {
-    return set_tuning_r(d, opts_lookahead(opts), t);
+    if (!opts_valid(opts)) return DFA_EINVAL;
+    return set_tuning_r(d, opts_slot(opts), t);
 }
 
 int dfa_autotune_opts(dfa_t* d, const uint8_t* dev_sample, uint64_t len,
                       const dfa_match_opts_t* opts, void* stream, dfa_tuning_t* chosen,
                       double* best_ms) {
-    return autotune_r(d, opts_lookahead(opts), dev_sample, len, stream, chosen, best_ms);
+    return autotune_r(d, opts, dev_sample, len, stream, chosen, best_ms);
 }
 
 int dfa_class_of_bytes(const dfa_t* d, uint16_t* out) {
@@ -791,7 +832,7 @@ int dfa_match_num_kernels(const dfa_t* d, uint64_t len, const dfa_match_opts_t* 
     Single s;
     int rc = plan_single(d, len, opts, &s);
     if (rc != DFA_OK) return rc;
-    *n = launch_kernel_count(s.lp.ptot, s.lp.grid, s.lp.dyn != 0);
+    *n = launch_kernel_count(s.lp.ptot, s.lp.grid, s.lp.dyn != 0, s.lp.bnd != 0);
     return DFA_OK;
 }
 
@@ -824,6 +865,37 @@ int dfa_plan_sets(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
     const HostDfa& h = d->h;
     for (uint32_t k = 0; k < n; ++k)
         sizes[k] = cls[k] == dyn_set(h.C) ? dyn[k] : h.iset_off[cls[k] + 1] - h.iset_off[cls[k]];
+    return DFA_OK;
+}
+
+int dfa_plan_starts(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
+                    const dfa_match_opts_t* opts, uint64_t* starts, uint32_t cap, uint32_t* P) {
+    if (!P || (len && !dev_str)) return DFA_EINVAL;
+    Single s;
+    int rc = plan_single(d, len, opts, &s);
+    if (rc != DFA_OK) return rc;
+    *P = s.lp.ptot;
+    if (!starts || cap == 0) return DFA_OK;
+    const uint32_t P1 = s.lp.ptot + 1, n = std::min(cap, P1);
+    std::vector<uint64_t> placed;
+    if (s.lp.bnd) {
+        uint8_t* ws = nullptr;
+        if (cudaMalloc(&ws, s.ws.total) != cudaSuccess) { cudaGetLastError(); return DFA_ENOMEM; }
+        s.lp.test1.str = dev_str;
+        bind(s.lp, ws, s.ws);
+        s.lp.results = nullptr;
+        rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr, nullptr, nullptr, true);
+        placed.resize(s.lp.ptot);
+        if (rc == DFA_OK &&
+            cudaMemcpy(placed.data(), s.lp.starts, 8ull * s.lp.ptot, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = DFA_ECUDA;
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = DFA_ECUDA;
+        cudaFree(ws);
+        if (rc != DFA_OK) return rc;
+    }
+    const DevTest& t = s.lp.test1;
+    for (uint32_t k = 0; k < n; ++k)
+        starts[k] = (k == 0) ? 0 : (k >= t.P ? len : (t.window ? placed[k] : chunk_start(len, t.P, t.m, k)));
     return DFA_OK;
 }
 
@@ -1151,7 +1223,7 @@ int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) 
 int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
     if (!b || !n) return DFA_EINVAL;
     uint32_t k = 0;
-    for (const Prepared& p : b->parts) k += launch_kernel_count(p.ptot, p.grid, p.dyn != 0);
+    for (const Prepared& p : b->parts) k += launch_kernel_count(p.ptot, p.grid, p.dyn != 0, p.bnd != 0);
     *n = k;
     return DFA_OK;
 }

@@ -19,8 +19,18 @@ constexpr int kMaxSegLen = 2048;         // longest staged segment per chunk (po
 constexpr uint16_t kNone16 = 0xFFFF;     // "not a member" in pos tables / invalid byte
 constexpr uint32_t kNone32 = 0xFFFFFFFFu;
 constexpr uint32_t kSmemTableMax = 112 * 1024;  // tables larger than this are read through L2
-constexpr uint32_t kMaxStates = 4095;
-constexpr uint32_t kMaxLookahead = 8;    // reverse-lookahead symbols r of Eq. (13)    // |Q| limit: a chunk's chains (|I| <= |Q|+1) fit one tile at K=16
+constexpr uint32_t kMaxStates = 4095;       // |Q| limit: a chunk's chains (|I| <= |Q|+1) fit one tile at K=16
+constexpr uint32_t kMaxLookahead = 8;    // reverse-lookahead symbols r of Eq. (13)
+constexpr uint32_t kMaxBoundaryWindow = 65536;  // largest Sec. 4.2 placement window (bytes)
+
+// Tuning records and launch descriptors exist per lookahead depth r, once for
+// the chunk starts of Eqs. (6)-(7) and once for starts placed by Sec. 4.2
+// (the placed sets are far smaller, so the best K and tiles differ).
+constexpr uint32_t kTuningSlots = 2 * (kMaxLookahead + 1);
+inline uint32_t tuning_slot(uint32_t lookahead, bool placed) {
+    return lookahead + (placed ? kMaxLookahead + 1 : 0u);
+}
+inline uint32_t slot_lookahead(uint32_t slot) { return slot % (kMaxLookahead + 1); }
 
 enum Placement : uint32_t { kSmem = 0, kGlobal = 1 };
 
@@ -80,7 +90,8 @@ struct DevTest {
     uint32_t lookahead;   // 1: Algorithm 3, 0: Algorithm 2 (all states)
     uint32_t out;         // index of its result in the caller's output array
     uint32_t flags;       // kTestCont, kTestMap
-    uint64_t pad_;
+    uint32_t window;      // Sec. 4.2 placement window actually searched (0: Eqs. 6-7 starts)
+    uint32_t pad_;
 };
 static_assert(sizeof(DevTest) == 64, "DevTest layout");
 
@@ -153,6 +164,8 @@ struct LaunchPlan {
     uint16_t* sets;             // lookahead-set arena (r >= 2), see DevGroup
     uint32_t* set_size;         // [ptot] |I| of each chunk computed by k_lookahead
     uint32_t dyn;               // 1 if some test uses r >= 2 lookahead symbols
+    uint32_t bnd;               // 1 if some test places its chunk starts (Sec. 4.2)
+    uint64_t* starts;           // [ptot] start of every chunk k >= 1 of a placing test
     uint16_t* dbg_maps;         // optional [ptot * qe_max]: chunk maps L_k (identity pre-filled)
     uint32_t qe_max;            // largest |Q|+1 of the launch's DFAs
     dfa_result_t* results;      // [ntests] in the caller's order (DevTest::out)
@@ -166,7 +179,8 @@ struct LaunchPlan {
 // Workspace carve-up of one launch (byte offsets into the device workspace).
 struct WsLayout {
     uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, wk, bsum, bsumw, tile_first,
-        ccta, share, ntiles, num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets, total;
+        ccta, share, ntiles, num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets,
+        starts, total;
 };
 
 // A batch planned on the host: descriptors, sizes and the workspace layout.
@@ -175,7 +189,7 @@ struct Prepared {
     std::vector<DevTest> tests;
     std::vector<DevGroup> groups;
     uint32_t ptot = 0, nblk = 0, grid = 0, kmax = 2, vcap = 1, table_cap = 0, smem = 0, stage = 0;
-    uint32_t qe_max = 1, dyn = 0;
+    uint32_t qe_max = 1, dyn = 0, bnd = 0;
     uint64_t set_entries = 0;
     WsLayout ws{};
 };
@@ -244,17 +258,21 @@ struct dfa_s {
     void* dev_block = nullptr;       // one allocation holding every device array
     uint64_t dev_bytes = 0;
     dfam::DevDfa dev;                // pointers into dev_block
-    // device descriptors for launches with lookahead r = 0 .. kMaxLookahead
-    // (index r), each with the K of that lookahead's tuning
+    // device descriptors for launches of every tuning slot (lookahead r = 0 ..
+    // kMaxLookahead, with and without Sec. 4.2 placement; dfam::tuning_slot),
+    // each with the K of that slot's tuning
     dfam::DevDfa* dev_desc = nullptr;
-    const dfam::DevDfa* dev_desc_for(uint32_t lookahead) const;
+    const dfam::DevDfa* dev_desc_for(uint32_t slot) const;
     dfa_tuning_t tuning{};           // base tuning record (dfa_set_tuning / dfa_autotune)
-    // records for one lookahead depth (dfa_set_tuning_opts / dfa_autotune_opts);
-    // a depth without its own record uses the base record
-    dfa_tuning_t tuning_r[dfam::kMaxLookahead + 1]{};
-    bool has_tuning_r[dfam::kMaxLookahead + 1]{};
-    const dfa_tuning_t& tuning_for(uint32_t lookahead) const {
-        return lookahead <= dfam::kMaxLookahead && has_tuning_r[lookahead] ? tuning_r[lookahead]
-                                                                          : tuning;
+    // records of one slot (dfa_set_tuning_opts / dfa_autotune_opts); a placed
+    // slot without its own record uses its depth's record, a depth without
+    // its own record the base record
+    dfa_tuning_t tuning_r[dfam::kTuningSlots]{};
+    bool has_tuning_r[dfam::kTuningSlots]{};
+    const dfa_tuning_t& tuning_for(uint32_t slot) const {
+        if (slot < dfam::kTuningSlots && has_tuning_r[slot]) return tuning_r[slot];
+        if (slot > dfam::kMaxLookahead && slot < dfam::kTuningSlots)
+            return tuning_for(slot - (dfam::kMaxLookahead + 1));
+        return tuning;
     }
 };

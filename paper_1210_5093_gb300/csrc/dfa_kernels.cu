@@ -136,6 +136,14 @@ __device__ __forceinline__ uint32_t find_test(const LaunchPlan& lp, uint32_t g) 
     return lo;
 }
 
+// Start of chunk k of test t: placed by k_boundaries (Sec. 4.2) when the test
+// has a placement window, else Eqs. (6)-(7).
+__device__ __forceinline__ uint64_t cstart(const LaunchPlan& lp, const DevTest& t, uint32_t k) {
+    if (k == 0) return 0;
+    if (k >= t.P) return t.n;
+    return t.window ? lp.starts[t.chunk_base + k] : dstart(t, k);
+}
+
 // Readable bytes of the string before position st of test t (unbounded for
 // a continuation segment, whose predecessor is in the same device buffer).
 __device__ __forceinline__ uint64_t bytes_before(const DevTest& t, uint64_t st) {
@@ -143,6 +151,46 @@ __device__ __forceinline__ uint64_t bytes_before(const DevTest& t, uint64_t st) 
 }
 
 constexpr int kLaWarps = 8;
+constexpr int kBndWarps = 8;
+
+// Boundary placement (Sec. 4.2: divide the input at boundaries whose reverse-
+// lookahead symbol has a small initial-state set), one warp per chunk k >= 1
+// of a test with a window w: among the positions p in [S - w, S + w] around
+// the Eqs. (6)-(7) start S, chunk k starts at the one whose preceding byte's
+// class has the smallest |I_class| (a byte outside Sigma costs more than any
+// set), then the one nearest S, then the smaller p.  The host keeps w at most
+// a quarter of the shortest later chunk, so the window lies inside the string
+// and placed starts stay increasing.  Each lane scores every 32nd candidate
+// (coalesced byte reads, one byte_plan load each); a warp minimum picks p.
+__global__ void __launch_bounds__(kBndWarps * 32) k_boundaries(LaunchPlan lp) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t g = blockIdx.x * kBndWarps + (threadIdx.x >> 5);
+    if (g >= lp.ptot) return;  // warp-uniform
+    const DevTest t = test_at(lp, find_test(lp, g));
+    const uint32_t k = g - t.chunk_base;
+    if (t.window == 0 || k == 0) return;
+    const uint64_t S = dstart(t, k), w = t.window;
+    const uint32_t* bp = lp.dfas[t.dfa].byte_plan;
+    const uint8_t* before = t.str - 1;  // before[p] = Str[p - 1]
+    // key: |I| (bits 18-34), distance (bits 1-17), past S (bit 0); lower is better
+    uint64_t best = ~0ull;
+    for (uint64_t p = S - w + (uint64_t)lane; p <= S + w; p += 32) {
+        const uint32_t v = __ldg(bp + __ldg(before + p));
+        const uint64_t cost = v == kNone32 ? 0x10000u : (v & 0xFFFFu);
+        const uint64_t dist = p < S ? S - p : p - S;
+        const uint64_t key = (cost << 18) | (dist << 1) | (p > S ? 1u : 0u);
+        best = key < best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, best, o);
+        best = y < best ? y : best;
+    }
+    if (lane == 0) {
+        const uint64_t dist = (best >> 1) & 0x1FFFFu;
+        lp.starts[g] = (best & 1u) ? S + dist : S - dist;
+    }
+}
 
 // r-symbol reverse lookahead (Eq. 13), one warp per chunk: with sigma_1..sigma_j
 // the j = min(r, Start(k)) bytes before the chunk, I = delta*(Q, sigma_1..sigma_j)
@@ -163,7 +211,7 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
     const DevTest t = test_at(lp, ti);
     if (t.lookahead < 2) return;
     const DevDfa& d = lp.dfas[t.dfa];
-    const uint64_t st = dstart(t, g - t.chunk_base);
+    const uint64_t st = cstart(lp, t, g - t.chunk_base);
     const uint64_t avail = bytes_before(t, st);
     const uint32_t j = (uint32_t)(avail < t.lookahead ? avail : t.lookahead);
     if (j < 2) return;
@@ -281,8 +329,8 @@ __device__ __forceinline__ void chunk_count_n(const LaunchPlan& lp, uint32_t g0,
         K[i] = __ldg(&d->K);
         bp[i] = (const uint32_t*)__ldg((const unsigned long long*)&d->byte_plan);
         const uint32_t k = g - t.chunk_base;
-        st[i] = ok ? dstart(t, k) : 0;
-        en[i] = ok ? dstart(t, k + 1) : 0;
+        st[i] = ok ? cstart(lp, t, k) : 0;
+        en[i] = ok ? cstart(lp, t, k + 1) : 0;
         const uint64_t avail = bytes_before(t, st[i]);
         b[i] = (ok && avail && t.lookahead) ? (uint32_t)__ldg(t.str + ((int64_t)st[i] - 1)) : kNoByte;
         // Eq. 13 sets (r >= 2) were sized by k_lookahead
@@ -1120,7 +1168,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             const uint32_t te = lp.chunk_test[g];
             const DevTest tt = test_at(lp, te);
             const uint32_t k = g - tt.chunk_base;
-            const uint64_t st = dstart(tt, k), en = dstart(tt, k + 1);
+            const uint64_t st = cstart(lp, tt, k), en = cstart(lp, tt, k + 1);
             const uint32_t cls = lp.chunk_cls[g];
             ChunkMeta m;
             uint32_t size;
@@ -1400,12 +1448,14 @@ static cudaError_t launch_ex(void (*kernel)(Params...), uint32_t grid, uint32_t 
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn) {
-    return (ptot <= kSmallPlan && grid <= kSmallShares ? 2u : 5u) + (dyn ? 1u : 0u);
+uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn, bool bnd) {
+    return (ptot <= kSmallPlan && grid <= kSmallShares ? 2u : 5u) + (dyn ? 1u : 0u) +
+           (bnd ? 1u : 0u);
 }
 
 // Issue the whole launch on `st`: memsets of the per-test counters, the
-// planning kernels (k_lookahead only for r >= 2) and the match kernel.
+// planning kernels (k_boundaries only for tests with a placement window,
+// k_lookahead only for r >= 2) and the match kernel.
 // With plan_only the match kernel is skipped.
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
                 uint32_t* kernels, void* ev_begin, void* ev_end, bool plan_only) {
@@ -1416,9 +1466,12 @@ int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t
     if ((!small || lp.dyn) &&
         cudaMemsetAsync(lp.test_err, 0, sizeof(uint32_t) * lp.ntests * 2, st) != cudaSuccess)
         return DFA_ECUDA;
-    uint32_t nk = launch_kernel_count(lp.ptot, lp.grid, lp.dyn != 0);
+    uint32_t nk = launch_kernel_count(lp.ptot, lp.grid, lp.dyn != 0, lp.bnd != 0);
     const uint32_t pct = carveout_pct(lp, smem);
     int e = 0;  // launch errors (cudaError_t values OR-ed: nonzero = failed)
+    if (lp.bnd)
+        e |= launch_ex(k_boundaries, (lp.ptot + kBndWarps - 1) / kBndWarps, kBndWarps * 32, 0, st,
+                       pct, lp);
     if (lp.dyn) {
         const uint32_t qe_words = (lp.qe_max + 31) / 32, set_words = (lp.vcap + 1) / 2;
         const uint32_t la_smem = kLaWarps * (qe_words + set_words) * 4;

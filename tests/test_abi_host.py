@@ -131,6 +131,9 @@ def test_compile_rejects_bad_input(dm):
     with pytest.raises(dm.DfaError) as e:
         d.match(b"ab")
     assert e.value.status == dm.EHOSTONLY
+    with pytest.raises(dm.DfaError) as e:      # placement needs the device image too
+        d.match(b"ab", boundary_window=16)
+    assert e.value.status == dm.EHOSTONLY
 
 
 @pytest.mark.parametrize("n", [0, 1, 36, 12345, 4 << 20, 10**10 + 7])
