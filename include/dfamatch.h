@@ -164,7 +164,7 @@ int dfa_set_tuning(dfa_t *dfa, const dfa_tuning_t *tuning);
 /*
  * Autotuner: times single-test launches of the device string dev_sample
  * (len bytes) for every allowed K in {2, 4, 8, 16}, tiles-per-CTA in
- * {4, 8, 16} and, for K <= 4, 2 or 3 CTAs per SM, plus shortest chunks of
+ * {1, 2, 4, 8, 16} and, for K <= 4, 2 or 3 CTAs per SM, plus shortest chunks of
  * 2 and 8 KiB where the default shortest chunk bounds the chunk count
  * (median of 3 timed launches each, CUDA events on `stream`),
  * keeps the fastest as the DFA's tuning record (of the candidates within 1%

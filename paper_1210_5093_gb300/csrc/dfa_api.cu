@@ -636,7 +636,7 @@ static int autotune_r(dfa_t* d, const dfa_match_opts_t* base, const uint8_t* dev
     std::vector<dfa_tuning_t> cands;
     for (uint32_t K : {2u, 4u, 8u, 16u}) {
         if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) continue;
-        for (uint32_t tpc : {4u, 8u, 16u}) {
+        for (uint32_t tpc : {1u, 2u, 4u, 8u, 16u}) {
             for (uint32_t ctas : {2u, 3u}) {
                 if (ctas == 3 && K > 4) continue;
                 dfa_tuning_t t = saved;

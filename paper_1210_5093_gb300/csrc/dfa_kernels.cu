@@ -1209,11 +1209,16 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             c.active = c.r < (int)meta[lo].cnt;
         }
         const uint32_t esz = stage_esz(d.stage_fmt);
-        // positions per chunk per segment: a multiple of 16 (8-bit stream) or 8,
-        // as many as the stage buffer holds for this tile's chunks
+        // positions per chunk per segment: a multiple of 16, at most what the
+        // stage buffer holds for this tile's chunks; the segments then share the
+        // longest chunk evenly, so the last one is not mostly identity padding
         const int quant = 16;
         int S = (int)(lp.stage_bytes / ((uint32_t)nch * esz)) / quant * quant;
         S = S < quant ? quant : (S > kMaxSegLen ? kMaxSegLen : S);
+        if (maxlen > 0) {
+            const uint32_t nseg = (maxlen + (uint32_t)S - 1) / (uint32_t)S;
+            S = (int)(((maxlen + nseg - 1) / nseg + quant - 1) / quant * quant);
+        }
         c.S = S;
         c.stage_bytes = lp.stage_bytes;
         c.tb = sa(sm + L.table);
