@@ -5,7 +5,10 @@ folded to 32 classes (gamma in 0.02-0.47), matched against 1 GiB of seeded
 Zipf(1.1) printable text with 0.1% planted accepted words.  One step is one
 whole membership test (planning kernels + match kernel, i.e. every step of the
 hot path) on device-resident input.  The input is larger than L2, so every
-step streams it from HBM.
+step streams it from HBM.  Chunk starts are placed as Sec. 4.2 proposes: each
+start of Eqs. (6)-(7) moves, within --boundary-window bytes, to the position
+whose reverse-lookahead symbol has the smallest initial-state set (0 keeps
+Eqs. 6-7; the line reports that configuration beside the headline).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload regex|plain|protein]
                     [--impl ours|reference]
@@ -139,11 +142,13 @@ def device_code_sha(text: bytes = None) -> str:
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-def _traffic_record(workload: str):
-    """DRAM bytes per match-kernel launch from the committed ncu summary, valid only
-    while the kernels' device code is unchanged."""
+def _traffic_record(workload: str, window: int = 0):
+    """DRAM bytes per match-kernel launch from the committed ncu summary of this
+    workload and placement window, valid only while the kernels' device code is
+    unchanged."""
     sha = device_code_sha()
-    p = os.path.join(ROOT, "profiles", "k_match_%s_traffic.json" % workload)
+    name = workload + ("_w%d" % window if window else "")
+    p = os.path.join(ROOT, "profiles", "k_match_%s_traffic.json" % name)
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -205,15 +210,16 @@ def _mixed_strings(spec, seed: int, count: int, lo: int, hi: int):
     return [gen.batch_text(seed * 1000003 + i, spec, int(n)) for i, n in enumerate(lens)]
 
 
-def batched_leg(dm, dfas, datas, reps: int = 5):
+def batched_leg(dm, dfas, datas, reps: int = 5, window: int = 0):
     """One persistent graph-replayed launch over all tests vs the plain path
-    (one dfa_match_async per string, back to back on one stream).  Device-resident."""
+    (one dfa_match_async per string, back to back on one stream).  Device-resident.
+    Both paths use the same Sec. 4.2 placement window."""
     import torch
     tens = [torch.from_numpy(x).cuda() for x in datas]
     total = sum(len(x) for x in datas)
     stream = torch.cuda.Stream()
     out = torch.zeros(12 * len(tens), dtype=torch.uint8, device="cuda")
-    b = dm.Batch(dfas, tens)
+    b = dm.Batch(dfas, tens, boundary_window=window)
     with torch.cuda.stream(stream):
         for _ in range(2):
             b.launch(out, stream=stream, graph=True)
@@ -228,13 +234,13 @@ def batched_leg(dm, dfas, datas, reps: int = 5):
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3 / reps
     # plain path: per-string launches with one reusable workspace
-    wsz = max(d.workspace_size(t.numel()) for d, t in zip(dfas, tens))
+    wsz = max(d.workspace_size(t.numel(), boundary_window=window) for d, t in zip(dfas, tens))
     ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
     outs = torch.zeros(12 * len(tens), dtype=torch.uint8, device="cuda")
 
     def plain():
         for i, (d, t) in enumerate(zip(dfas, tens)):
-            d.match_async(t, outs[12 * i:12 * i + 12], ws, stream=stream)
+            d.match_async(t, outs[12 * i:12 * i + 12], ws, stream=stream, boundary_window=window)
     with torch.cuda.stream(stream):
         plain()
     torch.cuda.synchronize()
@@ -255,7 +261,7 @@ def batched_leg(dm, dfas, datas, reps: int = 5):
 
 
 def serving_leg(dm, dfas, datas, rate_gbs: float, seconds: float = 2.0, budget: int = 2 << 30,
-                inflight: int = 8, seed: int = 5):
+                inflight: int = 8, seed: int = 5, window: int = 0):
     """Poisson arrivals at `rate_gbs` of offered load drawn from the given tests
     (pinned host buffers); reports achieved GB/s and arrival->result latency."""
     import torch
@@ -267,7 +273,7 @@ def serving_leg(dm, dfas, datas, rate_gbs: float, seconds: float = 2.0, budget: 
     n = max(20, int(lam * seconds))
     gaps = -np.log(1.0 - gen.unit(gen.draws(gen.key(seed, 99), n))) / lam
     picks = gen.below(gen.draws(gen.key(seed, 98), n), len(datas)).astype(np.int64)
-    srv = dm.Server(budget, max_inflight=inflight)
+    srv = dm.Server(budget, max_inflight=inflight, boundary_window=window)
     t0 = time.perf_counter()
     t_next = t0
     sub = {}
@@ -325,9 +331,10 @@ def run_batch_config(args, dm, torch):
     if not args.no_tune:
         for k, (s, d) in enumerate(zip(specs, dfas)):
             sample = torch.from_numpy(gen.batch_text(7 + k, s, 16 << 20)).cuda()
-            d.autotune(sample)
+            d.autotune(sample, boundary_window=args.boundary_window)
             del sample
-    bl, res = batched_leg(dm, [dfas[p] for p in picks], datas, reps=args.steps)
+    bl, res = batched_leg(dm, [dfas[p] for p in picks], datas, reps=args.steps,
+                          window=args.boundary_window)
     ok = True
     if not args.no_cpu:  # spot-check against the oracle (bounded)
         import oracle
@@ -340,7 +347,8 @@ def run_batch_config(args, dm, torch):
             "warmup": 2, "ms_per_step": bl["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u16", "data": "synthetic",
             "config": {"workload": "batched_64dfa_%dtests" % ntests, "tests": ntests,
-                       "input_bytes": total, "max_len": args.max_len, "autotuned": not args.no_tune},
+                       "input_bytes": total, "max_len": args.max_len, "autotuned": not args.no_tune,
+                       "boundary_window": args.boundary_window},
             "batched": bl, "oracle_spot_check": ok,
             "setup_s": round(time.perf_counter() - t_setup, 1)}
     print(json.dumps(line), flush=True)
@@ -359,7 +367,8 @@ def run_serve_config(args, dm, torch):
     rates = [("20k_req_s", 20000 * mean / 1e9)] + [("%.2fx" % f, f * cap) for f in (0.25, 0.5, 0.75, 1.0)]
     for name, gbs in rates:
         sv, done, sub = serving_leg(dm, dd, datas, gbs, seconds=args.serve_seconds,
-                                    budget=args.budget, inflight=args.inflight, seed=len(out) + 1)
+                                    budget=args.budget, inflight=args.inflight, seed=len(out) + 1,
+                                    window=args.boundary_window)
         res_b = bl_res
         for c in done:   # every served result equals the same test in the batched launch
             assert (c[1], c[2], c[3]) == res_b[sub[c[0]]], "served result differs"
@@ -370,7 +379,7 @@ def run_serve_config(args, dm, torch):
             "data": "synthetic",
             "config": {"workload": "serving_batched_mix", "pool_tests": len(datas),
                        "budget_bytes": args.budget, "mean_request_bytes": int(mean),
-                       "inflight": args.inflight},
+                       "inflight": args.inflight, "boundary_window": args.boundary_window},
             "serving": out, "batched_capacity_gbs": cap}
     print(json.dumps(line), flush=True)
 
@@ -397,8 +406,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-mix", action="store_true", help="skip the batched and serving legs")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
-    ap.add_argument("--boundary-window", type=int, default=0,
-                    help="Sec. 4.2 boundary placement window in bytes (0: Eqs. 6-7 starts)")
+    ap.add_argument("--boundary-window", type=int, default=256,
+                    help="Sec. 4.2 boundary placement window in bytes (0: the starts of Eqs. 6-7)")
     ap.add_argument("--tuning", default="",
                     help="K,tiles_per_cta,ctas_per_sm instead of the autotuner (profiling runs)")
     args = ap.parse_args()
@@ -526,7 +535,7 @@ def main():
         lookup_peak = nsm * 32 * sm_max_mhz * 1e6           # 32 shared-memory lanes per clock per SM
         achieved = W / k_avg_s
         info = d.info()
-        traffic = _traffic_record(w.name)
+        traffic = _traffic_record(w.name, bw)
         line = {
             "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
@@ -605,9 +614,9 @@ def main():
                 line["placement"] = {"r%d" % r: leg(r, 256) for r in (1, 4)}
         if not args.no_mix and args.workload == "regex":
             mix = _mixed_strings(w.spec, 11, 384, 256, 8 << 20)
-            bl, res_b = batched_leg(dm, [d] * len(mix), mix)
+            bl, res_b = batched_leg(dm, [d] * len(mix), mix, window=bw)
             line["batched"] = dict(bl, workload="regex512 DFA, 384 strings, lengths log-uniform 256 B - 8 MiB")
-            sv, done, sub = serving_leg(dm, [d] * len(mix), mix, 0.5 * bl["gbs"])
+            sv, done, sub = serving_leg(dm, [d] * len(mix), mix, 0.5 * bl["gbs"], window=bw)
             for c in done:          # every served result equals the same test in the batch
                 assert (c[1], c[2], c[3]) == res_b[sub[c[0]]], "served result differs"
             line["serving"] = dict(sv, workload="same 384 strings, Poisson arrivals at half the batched rate")

@@ -394,6 +394,12 @@ typedef struct {
  * DFAs must stay alive while requests on them are pending.
  */
 int dfa_server_create(uint64_t hbm_budget_bytes, uint32_t max_inflight, dfa_server_t **out);
+/* Planning options of the batches formed from now on: opts->lookahead (Algorithm
+ * 2/3, Eq. 13) and opts->boundary_window (Sec. 4.2 placement); NULL restores the
+ * default (lookahead 1, no placement).  num_chunks, multiplicity and the events
+ * must be 0 (they are per test, the server plans per batch).  The answers never
+ * depend on it.  Errors: DFA_EINVAL. */
+int dfa_server_set_opts(dfa_server_t *srv, const dfa_match_opts_t *opts);
 /* Copies str (host memory) into a pinned staging buffer and queues it.
  * Errors: DFA_EBUDGET (len > budget), DFA_EAGAIN, DFA_EINVAL, DFA_ENOMEM. */
 int dfa_server_submit(dfa_server_t *srv, const dfa_t *dfa, const uint8_t *str, uint64_t len,

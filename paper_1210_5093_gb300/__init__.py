@@ -104,6 +104,7 @@ SIGNATURES = {
     "dfa_batch_destroy": (None, [_P]),
     "dfa_strerror": (ctypes.c_char_p, [_I]),
     "dfa_server_create": (_I, [_U64, _U32, _P]),
+    "dfa_server_set_opts": (_I, [_P, _P]),
     "dfa_server_submit": (_I, [_P, _P, _P, _U64, _P]),
     "dfa_server_poll": (_I, [_P, _P, _U32, _P]),
     "dfa_server_drain": (_I, [_P, ctypes.c_double]),
@@ -453,12 +454,20 @@ def match_batch(dfas: Sequence[Dfa], tensors, stream=None, num_chunks: int = 0,
 class Server:
     """Continuous-batching request loop (dfa_server_t)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 8):
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 8, lookahead: int = 1,
+                 boundary_window: int = 0):
         h = ctypes.c_void_p()
         _check(lib().dfa_server_create(hbm_budget_bytes, max_inflight, ctypes.byref(h)),
                "dfa_server_create")
         self._h = h
         self._keep = {}
+        if lookahead != 1 or boundary_window:
+            self.set_opts(lookahead, boundary_window)
+
+    def set_opts(self, lookahead: int = 1, boundary_window: int = 0):
+        """Lookahead depth and Sec. 4.2 placement window of the batches formed from now on."""
+        o = _opts(lookahead=lookahead, boundary_window=boundary_window)
+        _check(lib().dfa_server_set_opts(self._h, ctypes.byref(o)), "dfa_server_set_opts")
 
     def submit(self, dfa: Dfa, host_data: np.ndarray) -> int:
         """host_data must stay alive until its completion is polled (kept here)."""

@@ -112,6 +112,7 @@ struct dfa_server_s {
     uint64_t next_ticket = 1;
     dfa_server_stats_t st{};
     int fatal = DFA_OK;
+    dfa_match_opts_t opts{};  // lookahead and placement window of every batch (under mu)
 
     void run();
     bool reap();
@@ -169,8 +170,10 @@ bool dfa_server_s::launch_one() {
         if (!s.busy) { slot = &s; break; }
     if (!slot) return false;
     std::vector<Req> batch;
+    dfa_match_opts_t bo;
     {
         std::lock_guard<std::mutex> g(mu);
+        bo = opts;
         // admission in arrival order while the arena has room; one batch takes
         // at most budget / slots bytes, so that every slot can be in flight and
         // one batch's copies overlap another's matching
@@ -203,7 +206,7 @@ bool dfa_server_s::launch_one() {
     std::vector<dfam::Prepared> parts;
     std::vector<uint64_t> ws_off;
     uint64_t ws_total = 0;
-    int rc = dfam::prepare_parts(n, dfas.data(), strs.data(), lens.data(), nullptr, &parts, &ws_off,
+    int rc = dfam::prepare_parts(n, dfas.data(), strs.data(), lens.data(), &bo, &parts, &ws_off,
                                  &ws_total);
     // device: [part workspaces | results]; pinned host: [results | descriptor staging per part]
     const uint64_t out_off = (ws_total + 255) & ~255ull;
@@ -284,6 +287,7 @@ int dfa_server_create(uint64_t budget, uint32_t max_inflight, dfa_server_t** out
         return DFA_ENOMEM;
     }
     s->budget = budget;
+    s->opts.lookahead = 1;
     s->arena.reset(budget);
     s->slots.resize(max_inflight);
     for (Slot& sl : s->slots) {
@@ -301,6 +305,23 @@ int dfa_server_create(uint64_t budget, uint32_t max_inflight, dfa_server_t** out
     }
     s->worker = std::thread([s] { s->run(); });
     *out = s;
+    return DFA_OK;
+}
+
+int dfa_server_set_opts(dfa_server_t* s, const dfa_match_opts_t* opts) {
+    if (!s) return DFA_EINVAL;
+    dfa_match_opts_t o{};
+    o.lookahead = 1;
+    if (opts) {
+        if (opts->num_chunks || opts->multiplicity || opts->match_begin_event ||
+            opts->match_end_event || opts->lookahead > dfam::kMaxLookahead ||
+            opts->boundary_window > dfam::kMaxBoundaryWindow)
+            return DFA_EINVAL;
+        o.lookahead = opts->lookahead;
+        o.boundary_window = opts->boundary_window;
+    }
+    std::lock_guard<std::mutex> g(s->mu);
+    s->opts = o;
     return DFA_OK;
 }
 

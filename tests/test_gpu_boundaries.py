@@ -190,3 +190,32 @@ def test_placed_tuning_records_and_kernel_count(dm):
     with pytest.raises(dm.DfaError) as e:
         d.match(dev, boundary_window=65537)
     assert e.value.status == dm.EINVAL
+
+
+def test_served_with_placement_equal_oracle(dm):
+    """The serving loop plans its batches with the placement window it was given."""
+    import torch
+    w = gen.regex_workload(8, 2 << 20)
+    d = dm.Dfa.from_spec(w.spec)
+    od = oracle.Dfa.from_spec(w.spec)
+    lens = [0, 5, 700, 9000, 100_000, 1 << 20, 2 << 20]
+    datas = [np.ascontiguousarray(w.data[:n]) for n in lens]
+    want = [od.run(x) for x in datas]
+    srv = dm.Server(1 << 28, max_inflight=4, boundary_window=256)
+    tickets = {}
+    for rep in range(3):
+        for i, x in enumerate(datas):
+            host = torch.from_numpy(x).pin_memory() if len(x) else x
+            tickets[srv.submit(d, host)] = i
+    srv.drain(120.0)
+    done = srv.poll(1024)
+    assert len(done) == len(tickets)
+    for c in done:
+        st, fs, acc = want[tickets[c[0]]]
+        assert c[3] == st
+        if st == 0:
+            assert (c[1], c[2]) == (fs, acc)
+    with pytest.raises(dm.DfaError) as e:
+        srv.set_opts(boundary_window=70000)
+    assert e.value.status == dm.EINVAL
+    srv.close()
