@@ -616,10 +616,13 @@ def main():
             mix = _mixed_strings(w.spec, 11, 384, 256, 8 << 20)
             bl, res_b = batched_leg(dm, [d] * len(mix), mix, window=bw)
             line["batched"] = dict(bl, workload="regex512 DFA, 384 strings, lengths log-uniform 256 B - 8 MiB")
-            sv, done, sub = serving_leg(dm, [d] * len(mix), mix, 0.5 * bl["gbs"], window=bw)
+            # a quarter of the batched rate: about 100k requests/s, which the host-side
+            # loop sustains (the full sweep up to 1.0x is --workload serve)
+            sv, done, sub = serving_leg(dm, [d] * len(mix), mix, 0.25 * bl["gbs"], window=bw)
             for c in done:          # every served result equals the same test in the batch
                 assert (c[1], c[2], c[3]) == res_b[sub[c[0]]], "served result differs"
-            line["serving"] = dict(sv, workload="same 384 strings, Poisson arrivals at half the batched rate")
+            line["serving"] = dict(sv, workload="same 384 strings, Poisson arrivals at a quarter "
+                                                "of the batched rate")
         if not args.no_cpu:
             v, nbytes, reps = cpu_oracle_gbs(w.spec, w.data)
             line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": 1,
