@@ -173,7 +173,8 @@ int dfa_set_tuning(dfa_t *dfa, const dfa_tuning_t *tuning);
  * *chosen and its time in *best_ms (either may be NULL).  The batched chunk
  * length is set to the chosen single-test chunk length, clamped to
  * [8 KiB, 64 KiB].  Launches of several DFAs (batches, the server) use each
- * DFA's compiler K capped at 8 rather than the tuned K: one kernel variant
+ * DFA's compiler K (from its mean set size; with Sec. 4.2 placement, from its
+ * smallest set) capped at 8 rather than the tuned K: one kernel variant
  * serves the whole launch.
  * Allocates a temporary workspace; synchronises the stream.
  */

@@ -208,7 +208,16 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
                 x.placement = kGlobal;
                 x.stage_fmt = kOff32;
             }
-            uint32_t K = std::min(d->h.K0, kBatchKMax);
+            // With Sec. 4.2 placement the chunks start after the symbols of the
+            // smallest sets, so K follows the smallest set instead of the mean.
+            uint32_t K0 = d->h.K0;
+            if (slot > kMaxLookahead && d->h.C) {
+                uint32_t smallest = ~0u;
+                for (uint32_t c = 0; c < d->h.C; ++c)
+                    smallest = std::min(smallest, d->h.iset_off[c + 1] - d->h.iset_off[c]);
+                K0 = k_for_set_size(std::max(1u, smallest));
+            }
+            uint32_t K = std::min(K0, kBatchKMax);
             while ((x.vcap + K - 1) / K > (uint32_t)kThreads / 2) K *= 2;
             x.K = K;
         }

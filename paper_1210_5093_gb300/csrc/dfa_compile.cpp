@@ -154,7 +154,7 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
     // States per thread: enough chains per thread for latency hiding, few
     // enough that the padding of the last thread of a chunk stays small.
     double mean = std::max(1.0, h.mean_iset);
-    h.K = mean >= 48 ? 8 : (mean >= 12 ? 4 : 2);
+    h.K = k_for_set_size(mean);
     // a chunk's chains must fit in one tile: ceil(I_max/K) <= kThreads/2
     // (launches of Algorithm 2, which match all of Q, raise K further)
     while ((std::max(h.imax, 1u) + h.K - 1) / h.K > (uint32_t)kThreads / 2 && h.K < 16) h.K *= 2;

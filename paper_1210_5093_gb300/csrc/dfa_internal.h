@@ -34,6 +34,10 @@ inline uint32_t slot_lookahead(uint32_t slot) { return slot % (kMaxLookahead + 1
 
 enum Placement : uint32_t { kSmem = 0, kGlobal = 1 };
 
+// Chains per thread the compiler picks for chunks whose sets have about
+// `size` states (before the tile-fit rule raises it for I_max).
+inline uint32_t k_for_set_size(double size) { return size >= 48 ? 8u : (size >= 12 ? 4u : 2u); }
+
 // ------------------------------------------------------- device DFA image
 // Everything the kernels read about one DFA.  Pointers are device pointers.
 struct DevDfa {
