@@ -101,9 +101,9 @@ typedef struct {
                               0 = Algorithm 2 (every chunk matched from all of Q),
                               2..8 = the r-symbol sets of Eq. (13), computed per
                               chunk on the device                                 */
-    uint32_t boundary_window; /* Sec. 4.2's boundary placement ("divide the input at
-                              boundaries with reverse lookahead symbols that have a
-                              small initial state set"): 0 = the chunk starts of
+    uint32_t boundary_window; /* Sec. 4.2's boundary placement (chunks cut right
+                              after symbols whose initial-state set is small, an
+                              optimization the paper suggests): 0 = the chunk starts of
                               Eqs. (6)-(7) (the default); w > 0 = on the device,
                               each start S of a chunk k >= 1 moves to the position
                               p in [S - w', S + w'] whose preceding byte has the

@@ -263,9 +263,8 @@ def boundary_window(n: int, P: int, m: int, window: int, lookahead: int = 1) -> 
 
 
 def boundary_starts(dfa: "Dfa", data, P: int, m: int, window: int, lookahead: int = 1) -> list:
-    """Sec. 4.2 ("Another possible optimization"): when the initial-state sets
-    differ much in size, divide the input at boundaries whose reverse-lookahead
-    symbol has a small set.  Reading taken here: start with the boundaries of
+    """Sec. 4.2 suggests, when the initial-state sets differ much in size, cutting
+    the input right after symbols whose set is small.  Reading taken here: start with the boundaries of
     Eqs. (6)-(7); move the start S of every chunk k >= 1 to the position p in
     [S - w, S + w] (w from boundary_window) that minimises, in this order, the
     size |I_sigma| (Eq. 11) of the symbol sigma = Str[p - 1] before it, the

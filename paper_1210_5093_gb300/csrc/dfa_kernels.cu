@@ -153,8 +153,8 @@ __device__ __forceinline__ uint64_t bytes_before(const DevTest& t, uint64_t st) 
 constexpr int kLaWarps = 8;
 constexpr int kBndWarps = 8;
 
-// Boundary placement (Sec. 4.2: divide the input at boundaries whose reverse-
-// lookahead symbol has a small initial-state set), one warp per chunk k >= 1
+// Boundary placement (Sec. 4.2 suggests cutting the input right after symbols
+// with small initial-state sets), one warp per chunk k >= 1
 // of a test with a window w: among the positions p in [S - w, S + w] around
 // the Eqs. (6)-(7) start S, chunk k starts at the one whose preceding byte's
 // class has the smallest |I_class| (a byte outside Sigma costs more than any

@@ -1,5 +1,5 @@
-"""Pins the oracle's boundary placement (Sec. 4.2: divide the input at
-boundaries whose reverse-lookahead symbol has a small initial-state set) to
+"""Pins the oracle's boundary placement (Sec. 4.2's suggestion: cut the input
+right after symbols whose initial-state set is small) to
 cases whose answer is fixed by construction, and to properties that any
 correct placement has:
 
