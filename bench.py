@@ -409,7 +409,8 @@ def main():
     ap.add_argument("--boundary-window", type=int, default=256,
                     help="Sec. 4.2 boundary placement window in bytes (0: the starts of Eqs. 6-7)")
     ap.add_argument("--tuning", default="",
-                    help="K,tiles_per_cta,ctas_per_sm instead of the autotuner (profiling runs)")
+                    help="K,tiles_per_cta,ctas_per_sm[,grid_waves] instead of the autotuner "
+                         "(profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -450,14 +451,16 @@ def main():
     tuning = None
     bw = args.boundary_window
     if args.tuning:
-        k, tpc, cps = (int(x) for x in args.tuning.split(","))
-        d.set_tuning(states_per_thread=k, tiles_per_cta=tpc, ctas_per_sm=cps, boundary_window=bw)
-        tuning = {"states_per_thread": k, "tiles_per_cta": tpc, "ctas_per_sm": cps, "fixed": True}
+        k, tpc, cps, *gw = (int(x) for x in args.tuning.split(","))
+        d.set_tuning(states_per_thread=k, tiles_per_cta=tpc, ctas_per_sm=cps, boundary_window=bw,
+                     grid_waves=gw[0] if gw else 0)
+        tuning = {"states_per_thread": k, "tiles_per_cta": tpc, "ctas_per_sm": cps,
+                  "grid_waves": gw[0] if gw else 1, "fixed": True}
     elif not w.num_chunks and not args.no_tune:
         # the library's per-DFA tuner (on at most 1 GiB), before any timing
         t, _ = d.autotune(dev[: 1 << 30], boundary_window=bw)
         tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
-                  "ctas_per_sm": t.ctas_per_sm}
+                  "ctas_per_sm": t.ctas_per_sm, "grid_waves": max(1, t.grid_waves)}
     P = d.plan_chunks(n, num_chunks=w.num_chunks, boundary_window=bw)
     ws = torch.empty(d.workspace_size(n, num_chunks=w.num_chunks, boundary_window=bw),
                      dtype=torch.uint8, device="cuda")
@@ -581,7 +584,7 @@ def main():
                 if tune:
                     t, _ = d.autotune(dev[: 1 << 30], lookahead=r, boundary_window=win)
                     tr = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
-                          "ctas_per_sm": t.ctas_per_sm}
+                          "ctas_per_sm": t.ctas_per_sm, "grid_waves": max(1, t.grid_waves)}
                 ev = [[torch.cuda.Event(enable_timing=True) for _ in range(reps)] for _ in range(4)]
                 for e in sum(ev, []):
                     e.record(stream)

@@ -89,6 +89,13 @@ typedef struct {
                                    double); 0 = automatic (len/32 clamped to
                                    [16 MiB, 256 MiB]), 0xFFFFFFFF = copy the whole
                                    string before matching                              */
+    uint32_t grid_waves;        /* single tests: match-kernel CTAs as a multiple (1-4) of
+                                   those that fit the GPU at once (0 = 1, one resident
+                                   wave).  The work and chunks stay the same; each CTA
+                                   takes 1/waves of a resident CTA's share, and the
+                                   hardware starts the next CTA wherever one finished,
+                                   which evens out SMs that run at different speeds.
+                                   Safe because no CTA waits for another.              */
 } dfa_tuning_t;
 
 /* Optional per-call planning overrides; pass NULL for the defaults. */

@@ -48,7 +48,8 @@ class Info(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("states_per_thread", ctypes.c_uint32), ("tiles_per_cta", ctypes.c_uint32),
                 ("min_chunk_bytes", ctypes.c_uint32), ("batch_chunk_bytes", ctypes.c_uint32),
-                ("ctas_per_sm", ctypes.c_uint32), ("host_segment_bytes", ctypes.c_uint32)]
+                ("ctas_per_sm", ctypes.c_uint32), ("host_segment_bytes", ctypes.c_uint32),
+                ("grid_waves", ctypes.c_uint32)]
 
 
 class MatchOpts(ctypes.Structure):
@@ -231,12 +232,13 @@ class Dfa:
 
     def set_tuning(self, states_per_thread: int = 0, tiles_per_cta: int = 0,
                    min_chunk_bytes: int = 0, batch_chunk_bytes: int = 0, ctas_per_sm: int = 0,
-                   host_segment_bytes: int = 0, lookahead: int = 1, boundary_window: int = 0):
+                   host_segment_bytes: int = 0, lookahead: int = 1, boundary_window: int = 0,
+                   grid_waves: int = 0):
         """host_segment_bytes: first segment of dfa_match's copy/match pipeline for
         host input (0 = automatic, 0xFFFFFFFF = copy the whole string first).
         lookahead: the depth whose record is set (1: the base record)."""
         t = Tuning(states_per_thread, tiles_per_cta, min_chunk_bytes, batch_chunk_bytes, ctas_per_sm,
-                   host_segment_bytes)
+                   host_segment_bytes, grid_waves)
         o = _opts(lookahead=lookahead, boundary_window=boundary_window)
         _check(lib().dfa_set_tuning_opts(self._h, ctypes.byref(o), ctypes.byref(t)),
                "dfa_set_tuning_opts")

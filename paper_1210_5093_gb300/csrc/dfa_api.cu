@@ -31,6 +31,7 @@ constexpr uint64_t kBatchChunk = 8192;     // default chunk length for batched t
 constexpr uint64_t kBatchChunksTarget = 65536;  // chunks a batched launch aims for at least
 constexpr uint64_t kBatchChunkMin = 2048;       // shortest batched chunk
 constexpr uint64_t kMaxChunk = 1ull << 31; // chunk lengths are 32-bit on the device
+constexpr uint32_t kMaxWaves = 4;          // largest dfa_tuning_t.grid_waves
 
 inline uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -363,14 +364,20 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
+    // chunks are planned for one resident wave; more waves only cut the same
+    // work into more, smaller CTA shares
     const uint32_t P = plan_chunks(d, len, grid, opts, false, 0);
+    const uint32_t gw = d->tuning_for(slot).grid_waves;
+    const uint32_t waves = gw ? std::min(gw, kMaxWaves) : 1u;
     LaunchPlan& lp = s->lp;
     std::memset(&lp, 0, sizeof lp);
     lp.ntests = 1;
     lp.ngroups = 1;
     lp.ptot = P;
     lp.nblk = (P + 1023) / 1024;
-    lp.grid = grid;
+    lp.grid = grid * waves;
+    lp.waves = waves;
+    grid = lp.grid;
     lp.seg_stride = seg_stride_for(x.qe);
     lp.smem_table_cap = tcap;
     lp.vcap = x.vcap;
@@ -615,6 +622,7 @@ static int set_tuning_r(dfa_t* d, uint32_t r, const dfa_tuning_t* t) {
     const uint32_t K = t->states_per_thread ? t->states_per_thread : d->h.K;
     if (K != 2 && K != 4 && K != 8 && K != 16) return DFA_EINVAL;
     if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) return DFA_EINVAL;
+    if (t->grid_waves > kMaxWaves) return DFA_EINVAL;
     dfa_tuning_t v = *t;
     v.states_per_thread = K;
     if (r == 1) {
@@ -652,7 +660,15 @@ static int autotune_r(dfa_t* d, const dfa_match_opts_t* base, const uint8_t* dev
                 t.states_per_thread = K;
                 t.tiles_per_cta = tpc;
                 t.ctas_per_sm = ctas;
+                t.grid_waves = 1;
                 cands.push_back(t);
+                // more, smaller CTA shares over the same chunks (each CTA still
+                // gets at least one full tile)
+                for (uint32_t w : {2u, 4u}) {
+                    if (w > tpc || tpc > 4) continue;
+                    t.grid_waves = w;
+                    cands.push_back(t);
+                }
             }
         }
     }

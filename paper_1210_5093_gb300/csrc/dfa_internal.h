@@ -141,6 +141,7 @@ struct LaunchPlan {
     const DevGroup* groups;
     uint32_t ntests, ngroups, ptot, nblk;
     uint32_t grid;              // CTAs of the match kernel
+    uint32_t waves;             // grid / CTAs that fit the GPU at once (0 or 1: one wave)
     uint32_t seg_stride;        // entries per segment map
     uint32_t smem_table_cap;    // bytes reserved for a shared-memory table
     uint32_t vcap;              // entries reserved for the running map

@@ -1432,7 +1432,8 @@ int launch_compose_segments(const dfa_result_t* seg_res, const uint16_t* maps, u
 static uint32_t carveout_pct(const LaunchPlan& lp, uint32_t smem) {
     const DevProps* p = dev_props();
     if (!p) return 100u;
-    const uint32_t per_sm = (lp.grid + p->sms - 1) / p->sms;
+    const uint32_t resident = lp.waves > 1 ? lp.grid / lp.waves : lp.grid;
+    const uint32_t per_sm = (resident + p->sms - 1) / p->sms;
     const uint32_t need = std::max(per_sm * (smem + 1024u), kSmallPlanSmem + 1024u);
     return std::min(100u, (need * 100u + p->smem_per_sm - 1) / p->smem_per_sm);
 }

@@ -219,3 +219,28 @@ def test_served_with_placement_equal_oracle(dm):
         srv.set_opts(boundary_window=70000)
     assert e.value.status == dm.EINVAL
     srv.close()
+
+
+@pytest.mark.parametrize("window", [0, 256])
+def test_grid_waves_equal_oracle(dm, window):
+    """More CTAs than fit at once (tuning grid_waves 2 or 4: the same chunks cut
+    into more, smaller CTA shares, scheduled as earlier CTAs finish) give the
+    same answers and the same chunks."""
+    w = gen.regex_workload(6, (16 << 20) + 999)
+    d = dm.Dfa.from_spec(w.spec)
+    dev = _dev(w.data)
+    want = oracle.Dfa.from_spec(w.spec).run(w.data)
+    n = dev.numel()
+    base = None
+    for waves in (1, 2, 4):
+        d.set_tuning(states_per_thread=2, tiles_per_cta=4, ctas_per_sm=2, grid_waves=waves,
+                     boundary_window=window)
+        assert d.tuning(boundary_window=window).grid_waves == waves
+        P = d.plan_chunks(n, boundary_window=window)
+        base = P if base is None else base
+        assert P == base                      # waves do not change the chunks
+        for r in (1, 4):
+            assert d.match(dev, lookahead=r, boundary_window=window) == want, (waves, r)
+    with pytest.raises(dm.DfaError) as e:
+        d.set_tuning(grid_waves=5, boundary_window=window)
+    assert e.value.status == dm.EINVAL
