@@ -233,7 +233,8 @@ int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t *starts);
  * Synchronous membership test.  str may be a host or a device pointer
  * (detected with cudaPointerGetAttributes).  Host input of at least two
  * first-segment lengths (dfa_tuning_t.host_segment_bytes) is copied and
- * matched as a pipeline when opts sets neither num_chunks nor multiplicity:
+ * matched as a pipeline when opts sets neither num_chunks nor multiplicity
+ * (segments double in length up to an eighth of the string):
  * each segment is copied on a library-owned copy stream and matched, once its
  * copy has landed, as its own launch on one of two library-owned compute
  * streams (so consecutive launches overlap).  Every segment after the first

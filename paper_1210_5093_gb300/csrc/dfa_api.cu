@@ -967,16 +967,18 @@ struct SyncBuffers {
 static SyncBuffers g_sync[64];
 
 // Segment lengths of the pipelined host path.  The first segment is short,
-// so little copy time is exposed before the first launch; each later one
-// doubles, since the copy engine moves bytes faster than the match kernel
-// consumes them and the next copy still ends under the current match.  A
-// remainder shorter than half the next length joins the last segment.
+// so little copy time is exposed before the first launch.  Later ones double
+// (fewer launches while the matching is slower than the copies) up to an
+// eighth of the string: the last segment's match starts only once its copy
+// has landed, so its length bounds the match time left exposed at the end.
+// A remainder shorter than half the next length joins the last segment.
 // Returns false when the input is too short to pipeline.
 static bool host_segments(uint64_t len, uint32_t first_bytes, std::vector<uint64_t>* seg) {
     constexpr uint64_t kMin = 16ull << 20, kMax = 256ull << 20;
     if (first_bytes == 0xFFFFFFFFu) return false;
     uint64_t first = first_bytes ? first_bytes : std::min(kMax, std::max(kMin, len / 32));
     if (first < 4096 || len < 2 * first) return false;
+    const uint64_t cap = std::max(first, len / 8);
     seg->clear();
     uint64_t pos = 0, next = first;
     while (pos < len) {
@@ -984,7 +986,7 @@ static bool host_segments(uint64_t len, uint32_t first_bytes, std::vector<uint64
         if (len - pos - take < next / 2) take = len - pos;
         seg->push_back(take);
         pos += take;
-        next *= 2;
+        next = std::min(next * 2, cap);
     }
     return seg->size() > 1;
 }

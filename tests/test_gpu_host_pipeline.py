@@ -27,8 +27,10 @@ def dm():
 
 
 def _segments(n, first):
-    """The segment lengths the library uses (doubling; a short remainder joins
-    the last segment), restated to place bytes at the boundaries."""
+    """The segment lengths the library uses (doubling up to an eighth of the
+    string; a short remainder joins the last segment), restated to place bytes
+    at the boundaries."""
+    cap = max(first, n // 8)
     out, pos, nxt = [], 0, first
     while pos < n:
         take = min(nxt, n - pos)
@@ -36,7 +38,7 @@ def _segments(n, first):
             take = n - pos
         out.append(take)
         pos += take
-        nxt *= 2
+        nxt = min(nxt * 2, cap)
     return out
 
 
