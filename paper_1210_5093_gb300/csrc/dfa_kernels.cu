@@ -4,6 +4,9 @@
 // four planning kernels (or k_plan_small, all of them in one CTA, for small
 // launches) and one persistent match kernel, all on one stream:
 //
+//   k_boundaries   (placement only) moves each chunk start within a window to
+//                  just after the symbol with the smallest initial set (Sec. 4.2)
+//   k_lookahead    (r >= 2 only) per chunk: the Eq. 13 set of r symbols
 //   k_count        per chunk: test, reverse-lookahead class, thread slots, work  (Alg. 3, Eq. 11)
 //   k_offsets      per-chunk slot offsets, CTA shares of the work, share bounds
 //   k_pack (x2)    greedy packing of each share into tiles, tile ranges
@@ -153,13 +156,13 @@ __device__ __forceinline__ uint64_t bytes_before(const DevTest& t, uint64_t st) 
 constexpr int kLaWarps = 8;
 constexpr int kBndWarps = 8;
 
-// Boundary placement (Sec. 4.2 suggests cutting the input right after symbols
-// with small initial-state sets), one warp per chunk k >= 1
-// of a test with a window w: among the positions p in [S - w, S + w] around
-// the Eqs. (6)-(7) start S, chunk k starts at the one whose preceding byte's
-// class has the smallest |I_class| (a byte outside Sigma costs more than any
-// set), then the one nearest S, then the smaller p.  The host keeps w at most
-// a quarter of the shortest later chunk, so the window lies inside the string
+// Boundary placement, which Sec. 4.2 suggests: cut the input right after
+// symbols with small initial-state sets.  One warp per chunk k >= 1 of a test
+// with a window w: among the positions p in [S - w, S + w] around the
+// Eqs. (6)-(7) start S, chunk k starts at the one whose preceding byte's class
+// has the smallest |I_class| (a byte outside Sigma costs more than any set),
+// then the one nearest S, then the smaller p.  The host keeps w at most a
+// quarter of the shortest later chunk, so the window lies inside the string
 // and placed starts stay increasing.  Each lane scores every 32nd candidate
 // (coalesced byte reads, one byte_plan load each); a warp minimum picks p.
 __global__ void __launch_bounds__(kBndWarps * 32) k_boundaries(LaunchPlan lp) {
