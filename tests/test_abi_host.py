@@ -142,3 +142,24 @@ def test_compile_rejects_bad_input(dm):
 def test_partition_matches_oracle(dm, n, P, m):
     got = dm.partition(n, P, m).tolist()
     assert got == oracle.chunk_starts(n, P, m)
+
+
+@pytest.mark.parametrize("which", ["reject", "accept"])
+def test_compile_excluded_states_by_hand(dm, which):
+    """The product's compiler leaves out the same states as the oracle on the
+    hand-built DFAs whose sets are written out in test_oracle_pins: a
+    non-accepting absorbing state besides q_e is excluded, an accepting
+    absorbing state and a state that loops on one symbol only are kept."""
+    from tests.test_oracle_pins import ABSORB_ACCEPT, ABSORB_REJECT
+    d = ABSORB_REJECT if which == "reject" else ABSORB_ACCEPT
+    m = np.array([i if i < d["num_symbols"] else 0xFF for i in range(256)], dtype=np.uint8)
+    spec = gen.DfaSpec(d["num_states"], d["num_symbols"], np.array(d["delta"], dtype=np.int32),
+                       d["q0"], np.array(d["finals"], dtype=np.uint32), m)
+    dd, info = _compare_isets(dm, spec)
+    cls = dd.class_of_bytes()
+    if which == "reject":
+        assert info.num_excluded == 2 and info.i_max == 2
+        assert dd.iset(int(cls[0])) == [0, 1] and dd.iset(int(cls[1])) == [3]
+    else:
+        assert info.num_excluded == 1 and info.i_max == 2
+        assert dd.iset(int(cls[0])) == [1, 2] and dd.iset(int(cls[1])) == [0, 1]

@@ -248,3 +248,84 @@ def test_partition_exact_and_tiles(n, P, m):
     # closed integer form of Eqs. (6) and (10) with w = 1
     for k in range(1, P):
         assert r[k][0] == (n * (m + k - 1)) // (m + P - 1)
+
+
+# ---------------------------------------------------------------- excluded states
+# Algorithm 3 leaves the error state q_e out of every initial-state set; the
+# oracle's reading extends that to every non-accepting state that loops on all
+# symbols (a run that reaches one never leaves it and is rejected) and keeps
+# accepting absorbing states.  The two DFAs below are built by hand so that
+# each plausible variant of the rule gives different sets: "exclude only q_e"
+# puts q2 of ABSORB_REJECT into I_a; "also exclude accepting absorbing states"
+# drops q1 of ABSORB_ACCEPT from I_a and I_b; "exclude states that loop on
+# some symbol" drops q2 of ABSORB_ACCEPT from I_a.  Expected sets are written
+# out from Eq. (11) by hand: I_sigma = image of delta(., sigma) over Q + {q_e},
+# minus the excluded states.
+
+# symbols a = 0, b = 1; -1 = q_e (state 4 here, state 3 below)
+ABSORB_REJECT = dict(num_states=4, num_symbols=2, q0=0, finals=[3], delta=[
+    [1, 2],    # q0: a -> q1, b -> q2
+    [1, 3],    # q1: a -> q1, b -> q3
+    [2, 2],    # q2: non-accepting, loops on a and b (absorbing, not q_e)
+    [0, -1],   # q3: accepting; b -> q_e
+])
+ABSORB_ACCEPT = dict(num_states=3, num_symbols=2, q0=0, finals=[1], delta=[
+    [1, 0],    # q0: a -> q1, b -> q0
+    [1, 1],    # q1: accepting and absorbing
+    [2, 0],    # q2: loops on a only
+])
+
+
+def _hand_dfa(d):
+    return oracle.Dfa(d["num_states"], d["num_symbols"], np.array(d["delta"], dtype=np.int32),
+                      d["q0"], d["finals"], None if d["num_symbols"] == 256 else
+                      np.array([i if i < d["num_symbols"] else 0xFF for i in range(256)],
+                               dtype=np.uint8))
+
+
+def test_excluded_non_accepting_absorbing_state_besides_qe():
+    o = _hand_dfa(ABSORB_REJECT)
+    # q2 loops on every symbol and is not accepting; q_e (index 4) is the paper's error state
+    assert o.excluded().tolist() == [False, False, True, False, True]
+    flags, imax = o.isets()
+    # I_a: q0->q1, q1->q1, q2->q2, q3->q0, q_e->q_e  = {q0, q1, q2, q_e} minus {q2, q_e}
+    assert np.nonzero(flags[0])[0].tolist() == [0, 1]
+    # I_b: q0->q2, q1->q3, q2->q2, q3->q_e, q_e->q_e = {q2, q3, q_e} minus {q2, q_e}
+    assert np.nonzero(flags[1])[0].tolist() == [3]
+    assert imax == 2
+
+
+def test_excluded_keeps_accepting_absorbing_and_partial_loops():
+    o = _hand_dfa(ABSORB_ACCEPT)
+    # only q_e (index 3, unreachable here) is excluded: q1 is absorbing but
+    # accepting, q2 loops on a but leaves on b
+    assert o.excluded().tolist() == [False, False, False, True]
+    flags, imax = o.isets()
+    # I_a: q0->q1, q1->q1, q2->q2, q_e->q_e = {q1, q2, q_e} minus {q_e}
+    assert np.nonzero(flags[0])[0].tolist() == [1, 2]
+    # I_b: q0->q0, q1->q1, q2->q0, q_e->q_e = {q0, q1, q_e} minus {q_e}
+    assert np.nonzero(flags[1])[0].tolist() == [0, 1]
+    assert imax == 2
+
+
+@pytest.mark.parametrize("which", ["reject", "accept"])
+def test_excluded_states_keep_every_chunking_exact(which):
+    """Excluding absorbing states never changes the answer (their identity
+    entries in L_k are already right): every chunking of every string of
+    length <= 7 equals Algorithm 1, and Algorithm 1 equals backward
+    propagation of F."""
+    d = ABSORB_REJECT if which == "reject" else ABSORB_ACCEPT
+    o = _hand_dfa(d)
+    spec = gen.DfaSpec(d["num_states"], d["num_symbols"], np.array(d["delta"], dtype=np.int32),
+                       d["q0"], np.array(d["finals"], dtype=np.uint32), o.map)
+    for L in range(0, 8):
+        words = _all_words(2, L)
+        want = _backward_accepts(spec, words)
+        for w, acc in zip(words, want):
+            data = np.array(w, dtype=np.uint8)
+            st, fs, a = o.run(data)
+            assert st == 0 and a == bool(acc)
+            for cuts in itertools.combinations(range(1, L), min(2, max(0, L - 1))):
+                starts = [0, *cuts, L]
+                st2, fs2, a2, _ = o.chunked(data, starts)
+                assert (st2, fs2, a2) == (st, fs, a), (w, starts)
