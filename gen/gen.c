@@ -60,14 +60,21 @@ static void run_uniform(job_t *j) {
     for (uint64_t i = j->lo; i < j->hi; ++i) j->out[i] = (uint8_t)(draw(j->key, i) >> 56);
 }
 
+/* The first index a with r < cdf[a], found from a per-bucket starting index
+ * (bucket = top 12 bits of r) and a short forward scan: the same index the
+ * plain binary search gives, without its unpredictable branches. */
+#define CAT_BUCKET_BITS 12
 static void run_categorical(job_t *j) {
+    uint16_t first[1u << CAT_BUCKET_BITS];
+    for (uint32_t bkt = 0, a = 0; bkt < (1u << CAT_BUCKET_BITS); ++bkt) {
+        const uint64_t lo = (uint64_t)bkt << (32 - CAT_BUCKET_BITS);
+        while (a + 1 < (uint32_t)j->k && lo >= j->cdf[a]) ++a;
+        first[bkt] = (uint16_t)a;
+    }
     for (uint64_t i = j->lo; i < j->hi; ++i) {
         uint64_t r = draw(j->key, i) >> 32; /* uniform in [0, 2^32) */
-        int a = 0, b = j->k - 1;             /* first index with r < cdf[idx] */
-        while (a < b) {
-            int mid = (a + b) >> 1;
-            if (r < j->cdf[mid]) b = mid; else a = mid + 1;
-        }
+        uint32_t a = first[r >> (32 - CAT_BUCKET_BITS)];
+        while (a + 1 < (uint32_t)j->k && r >= j->cdf[a]) ++a;
         j->out[i] = j->syms[a];
     }
 }
