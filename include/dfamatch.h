@@ -334,9 +334,14 @@ int dfa_match_async(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
  * scratch that must start at zero are cleared on the stream by each call.
  * All calls on a device share the one array, which keeps the last call's
  * contents: calls whose work overlaps on the GPU (other streams, or another
- * host thread) race and give wrong results; order them on one stream.  The
- * first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture.
+ * host thread) race and give wrong results; order them on one stream.  Each
+ * call made outside stream capture looks up the array's device address on the
+ * current device (cheap after the first time), so a cudaDeviceReset between
+ * calls, which reloads the library's device code at a new address, is
+ * harmless; a call made while `stream` is being captured uses the address
+ * found by the last call outside capture on that device.  So make the first
+ * call on each device, and the first call after a device reset, before any
+ * stream capture (during capture without one: DFA_ECUDA).
  */
 int dfa_match_noalloc(const dfa_t *dfa, const uint8_t *dev_str, uint64_t len,
                       const dfa_match_opts_t *opts, dfa_result_t *dev_out, void *stream);
@@ -345,7 +350,11 @@ uint64_t dfa_noalloc_scratch_bytes(void);
 
 /*
  * Batched membership tests: count independent tests (dfas[i], strs[i],
- * lens[i]) run in one persistent launch (plus four small planning launches).
+ * lens[i]), each computed by the same method as dfa_match (Algorithm 3 on its
+ * own partition, Eqs. 6-7, combined by Eqs. 8-9), run in one persistent
+ * launch (plus four small planning launches).  Several tests may share one
+ * string under different DFAs, the paper's use of one symbol-index input by
+ * several DFAs (Sec. 5).
  * dfas may repeat (tests are grouped by DFA); strs are device pointers;
  * results go to dev_out[0..count) (device).  Host arrays are read before
  * the call returns; strings must stay valid until the stream reaches the end
@@ -409,7 +418,12 @@ int dfa_server_create(uint64_t hbm_budget_bytes, uint32_t max_inflight, dfa_serv
  * must be 0 (they are per test, the server plans per batch).  The answers never
  * depend on it.  Errors: DFA_EINVAL. */
 int dfa_server_set_opts(dfa_server_t *srv, const dfa_match_opts_t *opts);
-/* Copies str (host memory) into a pinned staging buffer and queues it.
+/* Queues the test (dfa, str): str is host memory of len bytes that the server
+ * copies to the device when it forms the request's batch, so it must stay valid
+ * and unchanged until the request's completion has been polled.  The copy is
+ * asynchronous (and overlaps other batches' matching) only when str is pinned
+ * host memory (cudaHostAlloc / cudaHostRegister); from pageable memory it is
+ * synchronous.  *ticket receives the request's id.
  * Errors: DFA_EBUDGET (len > budget), DFA_EAGAIN, DFA_EINVAL, DFA_ENOMEM. */
 int dfa_server_submit(dfa_server_t *srv, const dfa_t *dfa, const uint8_t *str, uint64_t len,
                       uint64_t *ticket);

@@ -20,19 +20,28 @@ namespace {
 constexpr uint64_t kScratchBytes = 16ull << 20;  // 16 MiB per device
 
 // Shared by every call on a device; only host code needs its address, which
-// is looked up once per device (the array's host-side name is not a device
-// address and must never be passed to a kernel).
+// it looks up with cudaGetSymbolAddress (the array's host-side name is not a
+// device address and must never be passed to a kernel).
 static __device__ __align__(256) uint8_t g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint8_t* g_ptr[kMaxDevices] = {};
 
-int scratch_ptr(uint8_t** out) {
+// The array's device address on the current device.  Outside stream capture
+// it is looked up again on every call (a device reset reloads the module at a
+// new address, so a cached one could be stale); while `stream` is being
+// captured the address from the last lookup on this device is used.
+int scratch_ptr(void* stream, uint8_t** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DFA_ECUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return DFA_ECUDA;
+    }
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -40,6 +49,7 @@ int scratch_ptr(uint8_t** out) {
         }
         g_ptr[dev] = static_cast<uint8_t*>(p);
     }
+    if (!g_ptr[dev]) return DFA_ECUDA;
     *out = g_ptr[dev];
     return DFA_OK;
 }
@@ -56,7 +66,7 @@ extern "C" int dfa_match_noalloc(const dfa_t* dfa, const uint8_t* dev_str, uint6
     if (rc != DFA_OK) return rc;
     if (s.ws.total > kScratchBytes) return DFA_ENOSPACE;
     uint8_t* base = nullptr;
-    if ((rc = scratch_ptr(&base)) != DFA_OK) return rc;
+    if ((rc = scratch_ptr(stream, &base)) != DFA_OK) return rc;
     s.lp.test1.str = dev_str;
     dfam::bind(s.lp, base, s.ws);
     s.lp.results = dev_out;

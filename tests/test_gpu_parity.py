@@ -210,34 +210,73 @@ def test_batch_matches_oracle_and_graph_replay(dm):
         assert (fs, acc) == res[i][:2] or st != 0
 
 
-@pytest.mark.slow
-def test_regex_full_size_1GiB(dm):
+@pytest.fixture(scope="module")
+def regex_1gib():
+    """The benchmark's regex workload at full size, on the device, with the
+    oracle's answer (Algorithm 1 on the whole GiB, computed once)."""
     import torch
     w = gen.regex_workload(2, 1 << 30)
-    d = dm.Dfa.from_spec(w.spec)
     dev = torch.from_numpy(w.data).cuda()
-    ws = torch.empty(d.workspace_size(dev.numel()), dtype=torch.uint8, device="cuda")
+    return w, dev, _expect(w.spec, w.data)
+
+
+@pytest.fixture(scope="module")
+def protein_10gb():
+    import torch
+    w = gen.protein_workload(3, 10 * 10**9)
+    dev = torch.from_numpy(w.data).cuda()
+    return w, dev, _expect(w.spec, w.data)
+
+
+def _async_answer(dm, d, dev, **kw):
+    import torch
+    ws = torch.empty(d.workspace_size(dev.numel(), **kw), dtype=torch.uint8, device="cuda")
     out = torch.zeros(12, dtype=torch.uint8, device="cuda")
-    d.match_async(dev, out, ws)
+    d.match_async(dev, out, ws, **kw)
     torch.cuda.synchronize()
     (fs, acc, st), = dm.results_from(out)
-    est, efs, eacc = _expect(w.spec, w.data)
-    assert (st, fs, acc) == (0, efs, eacc)
+    return (st, fs, acc) if st == 0 else (st, None, None)
 
 
 @pytest.mark.slow
-def test_protein_full_size_10GB(dm):
-    import torch
-    w = gen.protein_workload(3, 10 * 10**9)
+@pytest.mark.parametrize("tuning", ["default", "autotuned", "fixed_2_2_2"])
+@pytest.mark.parametrize("window", [0, 256])
+def test_regex_full_size_1GiB(dm, regex_1gib, tuning, window):
+    """The benchmarked configurations at the size they are timed: the starts of
+    Eqs. 6-7 (the headline) and Sec. 4.2 placement within 256 bytes, under the
+    library defaults, the autotuner's pick on this input, and K = 2 with 2
+    tiles and 2 CTAs per SM."""
+    w, dev, want = regex_1gib
     d = dm.Dfa.from_spec(w.spec)
-    dev = torch.from_numpy(w.data).cuda()
-    ws = torch.empty(d.workspace_size(dev.numel()), dtype=torch.uint8, device="cuda")
-    out = torch.zeros(12, dtype=torch.uint8, device="cuda")
-    d.match_async(dev, out, ws)
-    torch.cuda.synchronize()
-    (fs, acc, st), = dm.results_from(out)
-    est, efs, eacc = _expect(w.spec, w.data)
-    assert (st, fs, acc) == (0, efs, eacc)
+    if tuning == "autotuned":
+        d.autotune(dev, boundary_window=window)
+    elif tuning == "fixed_2_2_2":
+        d.set_tuning(states_per_thread=2, tiles_per_cta=2, ctas_per_sm=2, boundary_window=window)
+    assert _async_answer(dm, d, dev, boundary_window=window) == want
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("window", [0, 256])
+def test_regex_full_size_1GiB_pinned_host_pipeline(dm, regex_1gib, window):
+    """dfa_match on a pinned 1 GiB host buffer: the segmented copy/match
+    pipeline the end-to-end figure times, twice in a row."""
+    w, dev, want = regex_1gib
+    import torch
+    d = dm.Dfa.from_spec(w.spec)
+    pinned = torch.from_numpy(w.data).pin_memory()
+    for _ in range(2):
+        assert d.match(pinned, boundary_window=window) == want
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tuning,window", [("default", 0), ("autotuned", 0), ("default", 256),
+                                           ("autotuned", 256)])
+def test_protein_full_size_10GB(dm, protein_10gb, tuning, window):
+    w, dev, want = protein_10gb
+    d = dm.Dfa.from_spec(w.spec)
+    if tuning == "autotuned":
+        d.autotune(dev[: 1 << 30], boundary_window=window)
+    assert _async_answer(dm, d, dev, boundary_window=window) == want
 
 
 def _expected_set_sizes(spec, data, P, r):

@@ -1,14 +1,16 @@
 """dfa_match_noalloc: the entry point for callers that cannot allocate device
 memory (no cudaMalloc and no workspace of their own to pass).  It runs the same
 kernels with their scratch in a fixed device array inside the library, so its
-answers must equal dfa_match_async's, call after call, even though every call
-reuses (and leaves behind) the previous call's scratch contents.
+answers must equal dfa_match_async's and the oracle's (Algorithm 1), call after
+call, even though every call reuses (and leaves behind) the previous call's
+scratch contents.
 
 This file is collected last so that a run that stops at the first failure has
 already run every other test; it also passes on its own in a fresh process."""
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -52,11 +54,14 @@ def test_noalloc_matches_async_on_consecutive_calls(dm):
     calls = [(d_regex, dev_regex, {}),
              (d_plain, dev_plain, {"num_chunks": plain.num_chunks}),
              (d_regex, dev_regex[: (5 << 20) + 3], {"num_chunks": 4097})]
+    specs = {id(d_regex): regex.spec, id(d_plain): plain.spec}
     for d, dev, kw in calls:
         want = _via_async(dm, d, dev, **kw)
         got = _via_noalloc(dm, d, dev, **kw)
         assert got == want, (got, want, kw)          # bit-exact: final state, accept, status
         assert got[2] == dm.OK
+        st, fs, acc = oracle.Dfa.from_spec(specs[id(d)]).run(dev.cpu().numpy())
+        assert (got[2], got[0], got[1]) == (st, fs, acc), (got, kw)
 
 
 def test_noalloc_rejects_plans_beyond_the_array(dm):
