@@ -35,9 +35,13 @@ constexpr uint32_t kMaxWaves = 4;          // largest dfa_tuning_t.grid_waves
 
 inline uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+// Entries per running-map array of one CTA when a launch's maps live in global
+// memory (vcap > kSmemVcap), else 0.
+inline uint32_t vmap_stride_for(uint32_t vcap) { return vcap > kSmemVcap ? (vcap + 7u) & ~7u : 0u; }
+
 WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t ptot, uint32_t nblk,
                    uint32_t grid, uint32_t stride, bool inline_desc, bool dyn = false,
-                   uint64_t set_entries = 0, bool bnd = false) {
+                   uint64_t set_entries = 0, bool bnd = false, uint32_t vcap = 0) {
     WsLayout w;
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) { uint64_t r = o; o = up(o + bytes, 256); return r; };
@@ -64,6 +68,7 @@ WsLayout ws_layout(uint32_t ndfa, uint32_t ntests, uint32_t ngroups, uint32_t pt
     w.set_size = take(dyn ? 4ull * ptot : 0);
     w.sets = take(dyn ? 2ull * set_entries : 0);
     w.starts = take(bnd ? 8ull * ptot : 0);
+    w.big_maps = take(2ull * 2 * vmap_stride_for(vcap) * grid);
     w.total = o;
     return w;
 }
@@ -91,6 +96,7 @@ void bind(LaunchPlan& lp, uint8_t* base, const WsLayout& w) {
     lp.set_size = reinterpret_cast<uint32_t*>(base + w.set_size);
     lp.sets = reinterpret_cast<uint16_t*>(base + w.sets);
     lp.starts = reinterpret_cast<uint64_t*>(base + w.starts);
+    lp.big_maps = reinterpret_cast<uint16_t*>(base + w.big_maps);
 }
 
 // Reverse-lookahead symbols requested by opts: 1 (Algorithm 3) by default,
@@ -106,6 +112,16 @@ inline uint32_t opts_slot(const dfa_match_opts_t* o) {
 }
 inline bool opts_valid(const dfa_match_opts_t* o) {
     return opts_lookahead(o) <= kMaxLookahead && opts_window(o) <= kMaxBoundaryWindow;
+}
+// The sets of Eq. (13) (r >= 2) are computed per chunk for DFAs of at most
+// kMaxSmallQe states (q_e included).
+inline bool lookahead_ok(const dfa_t* d, const dfa_match_opts_t* o) {
+    return opts_lookahead(o) < 2 || d->h.qe <= kMaxSmallQe;
+}
+// Chains per thread a tuning may use: every chunk's chains fit one tile at K,
+// or K = 16 (larger sets then run in several passes over their chunk).
+inline bool k_allowed(const dfa_t* d, uint32_t K) {
+    return K == 16 || (std::max(d->h.imax, 1u) + K - 1) / K <= (uint32_t)kThreads / 2;
 }
 
 // The window a test of n bytes in P chunks (multiplicity m) actually searches:
@@ -189,7 +205,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         if (!d) return DFA_EINVAL;
         if (!d->on_device) return DFA_EHOSTONLY;
         if (lens[i] && !strs[i]) return DFA_EINVAL;
-        if (!lookahead && d->h.qe > 4096) return DFA_EINVAL;
+        if (!lookahead_ok(d, opts)) return DFA_EINVAL;
         if (!idx.count(d)) {
             idx[d] = (uint32_t)uniq.size();
             uniq.push_back(d);
@@ -219,7 +235,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
                 K0 = k_for_set_size(std::max(1u, smallest));
             }
             uint32_t K = std::min(K0, kBatchKMax);
-            while ((x.vcap + K - 1) / K > (uint32_t)kThreads / 2) K *= 2;
+            while ((x.vcap + K - 1) / K > (uint32_t)kThreads / 2 && K < 16) K *= 2;
             x.K = K;
         }
         p.dfas.push_back(x);
@@ -285,7 +301,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
     p.dyn = lookahead >= 2 ? 1u : 0u;
     p.ws = ws_layout((uint32_t)p.dfas.size(), count, (uint32_t)p.groups.size(), p.ptot, p.nblk,
                      p.grid, seg_stride_for(p.qe_max), false, p.dyn != 0, p.set_entries,
-                     p.bnd != 0);
+                     p.bnd != 0, p.vcap);
     *out = std::move(p);
     return DFA_OK;
 }
@@ -300,6 +316,7 @@ void fill_plan(const Prepared& p, LaunchPlan& lp, uint8_t* ws, dfa_result_t* out
     lp.seg_stride = seg_stride_for(p.qe_max);
     lp.smem_table_cap = p.table_cap;
     lp.vcap = p.vcap;
+    lp.vmap_stride = vmap_stride_for(p.vcap);
     lp.qe_max = p.qe_max;
     lp.dyn = p.dyn;
     lp.bnd = p.bnd;
@@ -352,7 +369,7 @@ int launch_single(const Single& s, void* stream, void* ev_begin, void* ev_end) {
 int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Single* s) {
     if (!d) return DFA_EINVAL;
     if (!d->on_device) return DFA_EHOSTONLY;
-    if (!opts_valid(opts)) return DFA_EINVAL;
+    if (!opts_valid(opts) || !lookahead_ok(d, opts)) return DFA_EINVAL;
     const uint32_t lookahead = opts_lookahead(opts), slot = opts_slot(opts);
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     DevDfa x = launch_desc(d, slot);
@@ -381,6 +398,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.seg_stride = seg_stride_for(x.qe);
     lp.smem_table_cap = tcap;
     lp.vcap = x.vcap;
+    lp.vmap_stride = vmap_stride_for(x.vcap);
     lp.stage_bytes = stage;
     lp.qe_max = x.qe;
     lp.dyn = lookahead >= 2 ? 1u : 0u;
@@ -406,7 +424,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.group1.set_stride = std::max(d->h.imax, 1u);
     lp.group1.set_base = 0;
     s->ws = ws_layout(1, 1, 1, P, lp.nblk, grid, lp.seg_stride, true, lp.dyn != 0,
-                      (uint64_t)P * lp.group1.set_stride, lp.bnd != 0);
+                      (uint64_t)P * lp.group1.set_stride, lp.bnd != 0, x.vcap);
     return DFA_OK;
 }
 
@@ -621,7 +639,7 @@ static int set_tuning_r(dfa_t* d, uint32_t r, const dfa_tuning_t* t) {
     if (!d || !t || r >= kTuningSlots) return DFA_EINVAL;
     const uint32_t K = t->states_per_thread ? t->states_per_thread : d->h.K;
     if (K != 2 && K != 4 && K != 8 && K != 16) return DFA_EINVAL;
-    if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) return DFA_EINVAL;
+    if (!k_allowed(d, K)) return DFA_EINVAL;
     if (t->grid_waves > kMaxWaves) return DFA_EINVAL;
     dfa_tuning_t v = *t;
     v.states_per_thread = K;
@@ -641,7 +659,7 @@ static int set_tuning_r(dfa_t* d, uint32_t r, const dfa_tuning_t* t) {
 // fastest in that slot's record.
 static int autotune_r(dfa_t* d, const dfa_match_opts_t* base, const uint8_t* dev_sample,
                       uint64_t len, void* stream, dfa_tuning_t* chosen, double* best_ms) {
-    if (!d || (len && !dev_sample) || !opts_valid(base)) return DFA_EINVAL;
+    if (!d || (len && !dev_sample) || !opts_valid(base) || !lookahead_ok(d, base)) return DFA_EINVAL;
     if (!d->on_device) return DFA_EHOSTONLY;
     const uint32_t r = opts_slot(base);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -652,7 +670,7 @@ static int autotune_r(dfa_t* d, const dfa_match_opts_t* base, const uint8_t* dev
     o.boundary_window = opts_window(base);
     std::vector<dfa_tuning_t> cands;
     for (uint32_t K : {2u, 4u, 8u, 16u}) {
-        if ((std::max(d->h.imax, 1u) + K - 1) / K > (uint32_t)kThreads / 2) continue;
+        if (!k_allowed(d, K)) continue;
         for (uint32_t tpc : {1u, 2u, 4u, 8u, 16u}) {
             for (uint32_t ctas : {2u, 3u}) {
                 if (ctas == 3 && K > 4) continue;
@@ -1117,7 +1135,7 @@ int dfa_match(const dfa_t* d, const uint8_t* str, uint64_t len, const dfa_match_
     std::lock_guard<std::mutex> lock(B.mu);
     std::vector<uint64_t> seg;
     if (len && !on_dev && !(opts && (opts->num_chunks || opts->multiplicity)) &&
-        host_segments(len, d->tuning.host_segment_bytes, &seg))
+        d->h.qe <= kMaxSmallQe && host_segments(len, d->tuning.host_segment_bytes, &seg))
         return match_pipelined(d, str, seg, opts, B, out);
     const uint8_t* use = str;
     if (len && !on_dev) {

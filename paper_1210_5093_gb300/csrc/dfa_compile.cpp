@@ -124,8 +124,9 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
             h.pos[(size_t)c * qe + h.iset[i]] = (uint16_t)(i - h.iset_off[c]);
 
     // Table image: class-major, entries pre-scaled by the entry size; row C = identity.
-    h.sb = qe <= 256 ? 1 : 2;
-    const uint32_t align = h.sb == 1 ? 4 : 2;  // rows start on a 4-byte boundary
+    // 16-bit entries hold 2 * state, so above 32768 states (q_e included) they are 32-bit.
+    h.sb = qe <= 256 ? 1 : (qe <= 32768 ? 2 : 4);
+    const uint32_t align = 4 / h.sb;  // rows start on a 4-byte boundary
     h.qpad = (qe + align - 1) / align * align;
     const uint64_t tbytes = (uint64_t)(C + 1) * h.qpad * h.sb;
     h.table.assign(tbytes, 0);
@@ -134,8 +135,7 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
             uint32_t nxt = q < qe ? (c < C ? cols[c][q] : q) : 0;
             uint64_t at = ((uint64_t)c * h.qpad + q) * h.sb;
             uint32_t v = nxt * h.sb;
-            if (h.sb == 1) h.table[at] = (uint8_t)v;
-            else { h.table[at] = (uint8_t)(v & 0xFF); h.table[at + 1] = (uint8_t)(v >> 8); }
+            for (uint32_t i = 0; i < h.sb; ++i) h.table[at + i] = (uint8_t)(v >> (8 * i));
         }
     // Shared-memory placement needs a table that leaves room for the rest of
     // the CTA's shared memory, and a way to address its rows from the staged
@@ -155,11 +155,12 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
     // enough that the padding of the last thread of a chunk stays small.
     double mean = std::max(1.0, h.mean_iset);
     h.K = k_for_set_size(mean);
-    // a chunk's chains must fit in one tile: ceil(I_max/K) <= kThreads/2
-    // (launches of Algorithm 2, which match all of Q, raise K further)
+    // a chunk's chains should fit in one tile, ceil(I_max/K) <= kThreads/2, up
+    // to K = 16 (launches of Algorithm 2, which match all of Q, raise K
+    // further); a chunk with more chains than a tile holds runs its chains in
+    // several passes over the chunk (large DFAs)
     while ((std::max(h.imax, 1u) + h.K - 1) / h.K > (uint32_t)kThreads / 2 && h.K < 16) h.K *= 2;
     h.K0 = h.K;
-    if ((qe + 15) / 16 > (uint32_t)kThreads / 2) return DFA_EINVAL;
     *out = std::move(h);
     return DFA_OK;
 }

@@ -19,7 +19,14 @@ constexpr int kMaxSegLen = 2048;         // longest staged segment per chunk (po
 constexpr uint16_t kNone16 = 0xFFFF;     // "not a member" in pos tables / invalid byte
 constexpr uint32_t kNone32 = 0xFFFFFFFFu;
 constexpr uint32_t kSmemTableMax = 112 * 1024;  // tables larger than this are read through L2
-constexpr uint32_t kMaxStates = 4095;       // |Q| limit: a chunk's chains (|I| <= |Q|+1) fit one tile at K=16
+constexpr uint32_t kMaxStates = 65534;      // |Q| limit: states and q_e are 16-bit ids, 0xFFFF reserved
+// Launches whose largest set (the capacity of a running state map) exceeds
+// this keep each CTA's running map in global memory instead of shared memory.
+constexpr uint32_t kSmemVcap = 4096;
+// Largest |Q|+1 for the sets of Eq. (13) computed per chunk (k_lookahead keeps a
+// bitmap over Q and a set buffer per warp in shared memory) and for the map
+// tests of the pipelined host path (one register per state per thread).
+constexpr uint32_t kMaxSmallQe = 4096;
 constexpr uint32_t kMaxLookahead = 8;    // reverse-lookahead symbols r of Eq. (13)
 constexpr uint32_t kMaxBoundaryWindow = 65536;  // largest Sec. 4.2 placement window (bytes)
 
@@ -41,7 +48,7 @@ inline uint32_t k_for_set_size(double size) { return size >= 48 ? 8u : (size >= 
 // ------------------------------------------------------- device DFA image
 // Everything the kernels read about one DFA.  Pointers are device pointers.
 struct DevDfa {
-    const uint8_t* table;        // (C+1) rows x qpad entries of sb bytes; entry = next_state*sb;
+    const uint8_t* table;        // (C+1) rows x qpad entries of sb bytes (1, 2 or 4); entry = next_state*sb;
                                  // row C is the identity row used to pad chunk tails
     const uint16_t* byte_off16;  // [256] byte -> row byte offset c*qpad*sb (kNone16: not in Sigma)
     const uint32_t* byte_off32;  // [256] same, 32-bit (global placement)
@@ -55,7 +62,7 @@ struct DevDfa {
     uint32_t qe;                 // states incl. q_e
     uint32_t qpad;               // row stride (entries)
     uint32_t C;                  // classes (without the start set)
-    uint32_t sb;                 // bytes per table entry (1 or 2)
+    uint32_t sb;                 // bytes per table entry (1, 2, or 4 when |Q|+1 > 32768)
     uint32_t placement;          // Placement
     uint32_t table_bytes;        // (C+1)*qpad*sb
     uint32_t q0;
@@ -172,6 +179,8 @@ struct LaunchPlan {
     uint32_t bnd;               // 1 if some test places its chunk starts (Sec. 4.2)
     uint64_t* starts;           // [ptot] start of every chunk k >= 1 of a placing test
     uint16_t* dbg_maps;         // optional [ptot * qe_max]: chunk maps L_k (identity pre-filled)
+    uint16_t* big_maps;         // vcap > kSmemVcap: [grid][2][vmap_stride] running map and its domain
+    uint32_t vmap_stride;       // entries per running-map array in big_maps
     uint32_t qe_max;            // largest |Q|+1 of the launch's DFAs
     dfa_result_t* results;      // [ntests] in the caller's order (DevTest::out)
     uint16_t* maps;             // map tests: their state maps, map_stride entries each
@@ -185,7 +194,7 @@ struct LaunchPlan {
 struct WsLayout {
     uint64_t dfas, tests, groups, chunk_test, chunk_cls, cost, off, wk, bsum, bsumw, tile_first,
         ccta, share, ntiles, num_tiles, test_err, first_cta, last_cta, seg_hdr, seg_vals, set_size, sets,
-        starts, total;
+        starts, big_maps, total;
 };
 
 // A batch planned on the host: descriptors, sizes and the workspace layout.

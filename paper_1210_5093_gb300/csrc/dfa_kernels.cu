@@ -65,6 +65,11 @@ __device__ __forceinline__ uint32_t ldg_u16(const uint8_t* p) {
     asm volatile("ld.global.nc.u16 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
+__device__ __forceinline__ uint32_t ldg_u32(const uint8_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
 
 // floor(x / q) given qinv = floor((2^64 - 1) / q): the multiply-high estimate
 // is at most 2 below the quotient (division by an invariant integer).
@@ -242,7 +247,9 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
         const uint8_t* row = d.table + (size_t)c * d.qpad * d.sb;
         for (uint32_t x = lane; x < n; x += 32) {
             const uint32_t s = buf[x];
-            const uint32_t nx = d.sb == 1 ? row[s] : (uint32_t)(reinterpret_cast<const uint16_t*>(row)[s] >> 1);
+            const uint32_t nx = d.sb == 1 ? row[s]
+                                : (d.sb == 2 ? (uint32_t)(reinterpret_cast<const uint16_t*>(row)[s] >> 1)
+                                             : reinterpret_cast<const uint32_t*>(row)[s] >> 2);
             if (!d.excluded[nx]) atomicOr(bm + (nx >> 5), 1u << (nx & 31));
         }
         __syncwarp();
@@ -278,11 +285,12 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
     if (lane == 0) lp.set_size[g] = n;
 }
 
-// Per-chunk packing word: thread slots (bits 0-9; at most kThreads / 2, as
-// the compiler keeps ceil(|I| / K) <= 256) and kOpensTile, set when the chunk
-// starts a new DFA group or the share of a new CTA.
+// Per-chunk packing word: thread slots (bits 0-19: ceil(|I| / K) <= 32768)
+// and kOpensTile, set when the chunk starts a new DFA group or the share of a
+// new CTA.  A chunk with more slots than a CTA has threads fills a tile of its
+// own and runs its chains in several passes.
 constexpr uint32_t kOpensTile = 1u << 20;
-__device__ __forceinline__ uint32_t word_cost(uint32_t w) { return w & 0x3FFu; }
+__device__ __forceinline__ uint32_t word_cost(uint32_t w) { return w & 0xFFFFFu; }
 
 // CTA shares.  The launch's work W (lane-steps: thread slots x chunk length,
 // summed over its chunks) is cut into G equal shares, one per CTA of the
@@ -668,8 +676,11 @@ struct ChunkMeta {
 static_assert(sizeof(ChunkMeta) == 40, "ChunkMeta layout");
 
 // Shared-memory carve-up of k_match (byte offsets, all 16-byte aligned).
+// Launches with sets larger than kSmemVcap keep the running map and its
+// domain in global memory (LaunchPlan::big_maps) and hold here only one flag
+// bit per map entry, used while a chunk's chains run in several passes.
 struct SmemLayout {
-    uint32_t table, boff, stage, lmap, linit, vmap, vdom, meta, misc, desc, total;
+    uint32_t table, boff, stage, lmap, linit, vmap, vdom, vflag, meta, misc, desc, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -682,9 +693,11 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t table_cap, uint32_t k
     L.stage = L.boff + 1024;
     L.lmap = L.stage + 2 * stage_bytes;
     L.linit = L.lmap + align16(kThreads * kmax * 2);
+    const bool big = vcap > kSmemVcap;
     L.vmap = L.linit + align16(kThreads * kmax * 2);
-    L.vdom = L.vmap + align16(vcap * 2);
-    L.meta = L.vdom + align16(vcap * 2);
+    L.vdom = L.vmap + (big ? 0u : align16(vcap * 2));
+    L.vflag = L.vdom + (big ? 0u : align16(vcap * 2));
+    L.meta = L.vflag + (big ? align16((vcap + 31) / 32 * 4) : 0u);
     L.misc = L.meta + kMaxChunksPerTile * sizeof(ChunkMeta);
     L.desc = L.misc + 64;
     L.total = L.desc + align16(sizeof(DevDfa));
@@ -744,7 +757,8 @@ __device__ __forceinline__ void run_global(uint32_t (&s)[K], const uint8_t* tbl,
         for (int h = 0; h < 4; ++h) {
             const uint8_t* row = tbl + words[h];
 #pragma unroll
-            for (int u = 0; u < K; ++u) s[u] = SB == 1 ? ldg_u8(row + s[u]) : ldg_u16(row + s[u]);
+            for (int u = 0; u < K; ++u)
+                s[u] = SB == 1 ? ldg_u8(row + s[u]) : (SB == 2 ? ldg_u16(row + s[u]) : ldg_u32(row + s[u]));
         }
     }
 }
@@ -883,7 +897,7 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
                             uint16_t* dbg_maps, uint32_t dbg_stride, uint32_t g0) {
     uint32_t s[K];
     const uint32_t fmt = d.stage_fmt;
-    const uint32_t sh = d.sb == 2 ? 1 : 0;
+    const uint32_t sh = d.sb == 4 ? 2 : (d.sb == 2 ? 1 : 0);
     if (c.active) {
         const ChunkMeta m = meta[c.ci];
         const uint32_t size = m.size;
@@ -920,7 +934,8 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
                 else run_smem<K, 2>(s, c.tb, my, c.S);
             } else {
                 if (d.sb == 1) run_global<K, 1>(s, c.gtbl, my, c.S);
-                else run_global<K, 2>(s, c.gtbl, my, c.S);
+                else if (d.sb == 2) run_global<K, 2>(s, c.gtbl, my, c.S);
+                else run_global<K, 4>(s, c.gtbl, my, c.S);
             }
         }
         // the next segment stages into the other buffer, so one barrier per segment suffices
@@ -960,7 +975,7 @@ __device__ __forceinline__ void stage_seg_maps(const LaunchPlan& lp, uint32_t t,
     }
 }
 
-constexpr uint32_t kMapStatesPerThread = (kMaxStates + 1 + kThreads - 1) / kThreads;
+constexpr uint32_t kMapStatesPerThread = (kMaxSmallQe + kThreads - 1) / kThreads;
 
 // Map test: compose the whole segment maps (Eq. 9) for every state at once;
 // thread x follows states x, x + kThreads, ... through the maps in order.
@@ -968,6 +983,15 @@ __device__ void combine_test_map(const LaunchPlan& lp, uint32_t t, const DevTest
                                  const DevDfa& d, uint32_t b0, uint32_t nseg, uint32_t* sm,
                                  uint32_t per, uint32_t words) {
     const uint32_t qe = d.qe;
+    if (qe > kMapStatesPerThread * kThreads) {  // the host never pipelines such DFAs
+        if (threadIdx.x == 0) {
+            dfa_result_t r{};
+            r.status = DFA_EINVAL;
+            lp.results[tt.out] = r;
+        }
+        __syncthreads();
+        return;
+    }
     uint32_t cur[kMapStatesPerThread];
 #pragma unroll
     for (uint32_t i = 0; i < kMapStatesPerThread; ++i) cur[i] = threadIdx.x + i * kThreads;
@@ -1024,7 +1048,17 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
         return;
     }
     if (threadIdx.x == 0) *cell = cont ? lp.results[tt.out].final_state : d.q0;
-    for (uint32_t i0 = 0; i0 < nseg; i0 += per) {
+    if (per == 0 && threadIdx.x == 0) {
+        // maps larger than the staging buffer: thread 0 reads them in place
+        uint32_t s = *cell;
+        for (uint32_t j = 0; j < nseg; ++j) {
+            const uint32_t cb = b0 + j;
+            if (__ldcg(lp.cta_range + 2 * cb) == __ldcg(lp.cta_range + 2 * cb + 1)) continue;
+            s = __ldcg(lp.seg_vals + (size_t)(cb + t) * lp.seg_stride + s);
+        }
+        *cell = s;
+    }
+    for (uint32_t i0 = 0; i0 < nseg && per; i0 += per) {
         const uint32_t nb = min(per, nseg - i0);
         __syncthreads();
         stage_seg_maps(lp, t, b0, i0, nb, words, sm);
@@ -1059,8 +1093,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
     const SmemLayout L = smem_layout(lp.smem_table_cap, kmax, lp.vcap, lp.stage_bytes);
     ChunkMeta* meta = reinterpret_cast<ChunkMeta*>(sm + L.meta);
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + L.misc);
-    uint16_t* vmap = reinterpret_cast<uint16_t*>(sm + L.vmap);
-    uint16_t* vdom = reinterpret_cast<uint16_t*>(sm + L.vdom);
+    // the running map and its domain: shared memory, or this CTA's slice of
+    // big_maps when the launch's sets are larger than kSmemVcap
+    uint16_t* vmap = lp.vmap_stride ? lp.big_maps + (size_t)blockIdx.x * 2 * lp.vmap_stride
+                                    : reinterpret_cast<uint16_t*>(sm + L.vmap);
+    uint16_t* vdom = lp.vmap_stride ? vmap + lp.vmap_stride : reinterpret_cast<uint16_t*>(sm + L.vdom);
+    uint32_t* vflag = reinterpret_cast<uint32_t*>(sm + L.vflag);
     const uint16_t* lmap = reinterpret_cast<const uint16_t*>(sm + L.lmap);
     const uint16_t* linit = reinterpret_cast<const uint16_t*>(sm + L.linit);
     const int tid = threadIdx.x;
@@ -1199,9 +1237,21 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
         __syncthreads();
         const uint32_t maxlen = misc[M_MAXLEN];
 
-        // my chunk: last ci with toff <= tid
+        // A tile is either a run of chunks whose chains fit its threads, or one
+        // chunk with more chains than that (large DFAs): the chunk's chains then
+        // run in passes of kThreads threads, each pass re-staging the chunk.
+        const uint32_t cnt0 = meta[0].cnt;
+        const uint32_t passes = (nch == 1 && cnt0 > (uint32_t)kThreads)
+                                    ? (cnt0 + kThreads - 1) / kThreads : 1u;
+        bool fresh = false;  // the multi-pass chunk opened a new segment (CTA-uniform)
+        for (uint32_t pass = 0; pass < passes; ++pass) {
         TileCtx c;
-        {
+        if (passes > 1) {
+            c.ci = 0;
+            c.r = tid + (int)(pass * kThreads);
+            c.active = c.r < (int)cnt0;
+        } else {
+            // my chunk: last ci with toff <= tid
             int lo = 0, hi = nch - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
@@ -1241,6 +1291,49 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             tile_chains<(KMAX >= 16 ? 8 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         else tile_chains<KMAX>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         __syncthreads();
+
+        if (passes > 1) {
+            // Eq. (9) for one pass of a multi-pass chunk: the pass holds the chains
+            // of I_k[lo, hi) (tile-local slot x - lo).  Every entry of the running
+            // map is composed with the chunk exactly once, by the pass that holds
+            // its entering state's slot (vflag marks it done); excluded states
+            // (no slot) stay fixed.
+            const ChunkMeta m = meta[0];
+            const uint32_t lo = pass * (uint32_t)kThreads * d.K;
+            const uint32_t hi = min((uint32_t)m.size, lo + (uint32_t)kThreads * d.K);
+            if (pass == 0 && (int)m.test != cur_test) {
+                if (cur_test >= 0) end_segment();
+                cur_test = (int)m.test;
+                seg_first = gA;
+                seg_n = 0;
+                seg_cls = m.cls;
+                nD = m.size;
+                fresh = true;
+            }
+            if (fresh) {
+                for (uint32_t x = lo + tid; x < hi; x += kThreads) {
+                    vmap[x] = lmap[x - lo];
+                    vdom[x] = linit[x - lo];
+                }
+            } else {
+                const uint16_t* pos = d.pos + (size_t)m.cls * d.qe;
+                for (uint32_t x = tid; x < nD; x += kThreads) {
+                    if ((vflag[x >> 5] >> (x & 31)) & 1u) continue;
+                    const uint32_t p = __ldg(pos + vmap[x]);
+                    if (p != kNone16 && p >= lo && p < hi) {
+                        vmap[x] = lmap[p - lo];
+                        atomicOr(vflag + (x >> 5), 1u << (x & 31));
+                    }
+                }
+            }
+            __syncthreads();
+            if (pass + 1 == passes) {
+                ++seg_n;
+                for (uint32_t w = tid; w < (nD + 31) / 32; w += kThreads) vflag[w] = 0;
+            }
+            __syncthreads();
+            continue;
+        }
 
         // Compose the tile's chunk maps, in order, into the running map of each
         // test (Eq. 9).  Thread x owns entries x, x+kThreads, ... of the running map.
@@ -1282,6 +1375,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             ++seg_n;
         }
         __syncthreads();
+        }  // passes
     }
     if (cur_test >= 0) end_segment();
 }

@@ -163,3 +163,24 @@ def test_compile_excluded_states_by_hand(dm, which):
     else:
         assert info.num_excluded == 1 and info.i_max == 2
         assert dd.iset(int(cls[0])) == [1, 2] and dd.iset(int(cls[1])) == [0, 1]
+
+
+def test_compile_large_dfas_and_the_state_limit(dm):
+    """|Q| up to 65534 compiles (q_e is state 65534; ids are 16-bit with
+    0xFFFF reserved), with 32-bit table entries above 32767 states; 65535 is
+    rejected.  The I-sets of a 5000-state DFA equal the oracle's."""
+    m = np.full(256, 0xFF, dtype=np.uint8)
+    m[97:101] = np.arange(4)
+    spec = gen.random_dfa(5, 5000, 4, num_finals=3, missing=0.05, byte_to_symbol=m)
+    d, info = _compare_isets(dm, spec)
+    assert info.state_bytes == 2
+    m2 = np.full(256, 0xFF, dtype=np.uint8)
+    m2[97:99] = np.arange(2)
+    big = gen.random_dfa(6, 65534, 2, num_finals=1, byte_to_symbol=m2)
+    d = dm.Dfa.from_spec(big, host_only=True)
+    info = d.info()
+    assert info.num_states_ext == 65535 and info.state_bytes == 4 and info.placement == 1
+    too_big = np.zeros((65535, 2), dtype=np.int32)
+    with pytest.raises(dm.DfaError) as e:
+        dm.Dfa(65535, 2, too_big, 0, [1], m2, host_only=True)
+    assert e.value.status == dm.EINVAL

@@ -419,8 +419,9 @@ def test_l2_placed_tables(dm, kind):
 
 
 def test_largest_dfa_and_k16(dm):
-    """|Q| = 4095 (the limit), a dense 20-letter alphabet so I_max is large
-    and the planner needs K = 16 to fit a chunk into one tile."""
+    """|Q| = 4095 (the largest DFA whose running maps stay in shared memory), a
+    dense 20-letter alphabet so I_max is large and the planner needs K = 16 to
+    fit a chunk into one tile."""
     spec = gen.class_dfa(91, 4095, 20, 0.3, 0.9, 40, "protein")
     d = dm.Dfa.from_spec(spec)
     info = d.info()
