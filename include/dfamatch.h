@@ -63,7 +63,7 @@ typedef struct {
     uint32_t num_classes;    /* alphabet classes after merging identical columns   */
     uint32_t i_max;          /* Eq. (12): max_sigma |I_sigma|                      */
     uint32_t num_excluded;   /* non-accepting absorbing states left out of every I */
-    uint32_t state_bytes;    /* 1 (uint8 table) or 2 (uint16 table)                */
+    uint32_t state_bytes;    /* table entry size: 1 (|Q|+1 <= 256), 2 (<= 32768), else 4 */
     uint32_t placement;      /* 0 = table in shared memory, 1 = table read through L2 */
     uint32_t states_per_thread; /* chains one thread advances together (planner's K) */
     uint32_t q0;
@@ -78,7 +78,8 @@ typedef struct {
  * chunks are.  Zero fields mean "library default". */
 typedef struct {
     uint32_t states_per_thread; /* K in {2, 4, 8, 16}; ceil(I_max/K) must be <= 256
-                                   (Algorithm 2 launches raise K as needed)         */
+                                   unless K = 16 (Algorithm 2 launches raise K as
+                                   needed, up to 16)                                  */
     uint32_t tiles_per_cta;     /* single tests: aim for this many tiles per CTA (default 8) */
     uint32_t min_chunk_bytes;   /* single tests: shortest chunk (default 512)          */
     uint32_t batch_chunk_bytes; /* batched and served tests: chunk length (default 8192) */
@@ -139,12 +140,17 @@ typedef struct {
  *   finals         num_finals accepting states (< num_states, duplicates allowed). Copied.
  *   byte_to_symbol 256 entries mapping an input byte to a symbol (< num_symbols),
  *                  or 0xFF for "not in Sigma"; NULL = identity (needs num_symbols == 256).
- * Limits: 1 <= num_states <= 4095 (a chunk's chains must fit one thread block),
- * 1 <= num_symbols <= 256.
+ * Limits: 1 <= num_states <= 65534 (states, q_e included, are 16-bit ids with
+ * 0xFFFF reserved), 1 <= num_symbols <= 256.  A chunk whose initial-state set
+ * holds more chains than one thread block runs them in several passes over the
+ * chunk, and launches with sets above 4096 states keep their running state
+ * maps in global memory (part of the workspace); the r-symbol sets of Eq. (13)
+ * (opts->lookahead >= 2) are available for num_states <= 4095 (DFA_EINVAL
+ * above), and dfa_match pipelines host input only for such DFAs.
  * Compilation (the set computation of Algorithm 3, done once): bytes with identical delta
  * columns share a class; I_c (Eq. 11) and I_max (Eq. 12) are computed; the
- * class-major table (uint8 states if |Q|+1 <= 256, else uint16) is placed in
- * shared memory if it fits, otherwise read through L2.
+ * class-major table (uint8 states if |Q|+1 <= 256, uint16 up to 32768, else
+ * uint32) is placed in shared memory if it fits, otherwise read through L2.
  * Errors: DFA_EINVAL, DFA_ENOMEM, DFA_ECUDA.  *out is NULL on error.
  */
 int dfa_create(uint32_t num_states, uint32_t num_symbols, const int32_t *delta, uint32_t q0,
