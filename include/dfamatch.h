@@ -71,6 +71,10 @@ typedef struct {
     uint64_t device_bytes;   /* all device memory held by this dfa_t               */
     double gamma;            /* Eq. (18): I_max / |Q|                              */
     double mean_iset;        /* mean |I_c| over the classes                        */
+    uint32_t byte_rows;      /* 1: chains visit at most 16 states, so the match kernel
+                                steps them by byte permutes of 16-byte class rows
+                                held in shared memory instead of table loads       */
+    uint32_t reserved;
 } dfa_info_t;
 
 /* Per-DFA tuning record (the GPU counterpart of the paper's per-processor

@@ -42,7 +42,8 @@ class Info(ctypes.Structure):
                 ("state_bytes", ctypes.c_uint32), ("placement", ctypes.c_uint32),
                 ("states_per_thread", ctypes.c_uint32), ("q0", ctypes.c_uint32),
                 ("table_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("gamma", ctypes.c_double), ("mean_iset", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("mean_iset", ctypes.c_double),
+                ("byte_rows", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Tuning(ctypes.Structure):

@@ -136,6 +136,12 @@ uint32_t test_window(const dfa_match_opts_t* o, uint64_t n, uint32_t P, uint32_t
 }
 inline uint32_t seg_stride_for(uint32_t qe_max) { return (qe_max + 1) & ~1u; }
 
+// Bytes of a shared-memory DFA's table image in k_match's shared memory: its
+// byte rows when it has them, else its class-major table.
+inline uint32_t smem_table_bytes(const DevDfa& x) {
+    return (uint32_t)up(x.nib ? (x.C + 1) * 16u : x.table_bytes, 16);
+}
+
 // Launch-specific copy of a DFA's device descriptor for a tuning slot.  K is
 // raised when the largest set the launch matches would not fit one tile.
 DevDfa launch_desc(const dfa_t* d, uint32_t slot) {
@@ -221,9 +227,10 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
             // launch), capped at kBatchKMax unless a chunk's chains need more
             // to fit a tile, and a table above kBatchSmemTable is read through
             // L2, so that one DFA does not cut the occupancy of every other test.
-            if (x.placement == kSmem && x.table_bytes > kBatchSmemTable) {
+            if (x.placement == kSmem && smem_table_bytes(x) > kBatchSmemTable) {
                 x.placement = kGlobal;
                 x.stage_fmt = kOff32;
+                x.nib = 0;
             }
             // With Sec. 4.2 placement the chunks start after the symbols of the
             // smallest sets, so K follows the smallest set instead of the mean.
@@ -242,7 +249,7 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
         p.kmax = std::max(p.kmax, x.K);
         p.vcap = std::max(p.vcap, x.vcap);
         p.qe_max = std::max(p.qe_max, x.qe);
-        if (x.placement == kSmem) p.table_cap = std::max(p.table_cap, (uint32_t)up(x.table_bytes, 16));
+        if (x.placement == kSmem) p.table_cap = std::max(p.table_cap, smem_table_bytes(x));
     }
     uint32_t esz_max = 1;
     for (const DevDfa& x : p.dfas) esz_max = std::max(esz_max, stage_esz(x.stage_fmt));
@@ -373,11 +380,14 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     const uint32_t lookahead = opts_lookahead(opts), slot = opts_slot(opts);
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     DevDfa x = launch_desc(d, slot);
-    const uint32_t tcap = x.placement == kSmem ? (uint32_t)up(x.table_bytes, 16) : 0u;
-    s->kmax = x.K;
+    const uint32_t tcap = x.placement == kSmem ? smem_table_bytes(x) : 0u;
+    // byte-row DFAs take the kernel variant with the larger register budget:
+    // their chains are latency-bound (few chains per SM), and the rows loaded
+    // ahead of the chains need registers
+    s->kmax = x.nib ? std::max(x.K, 8u) : x.K;
     uint32_t stage = 0;
-    s->smem = match_smem_bytes(tcap, x.K, x.vcap, stage_esz(x.stage_fmt), &stage,
-                               match_target_ctas(x.K, d->tuning_for(slot).ctas_per_sm));
+    s->smem = match_smem_bytes(tcap, s->kmax, x.vcap, stage_esz(x.stage_fmt), &stage,
+                               match_target_ctas(s->kmax, d->tuning_for(slot).ctas_per_sm));
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
@@ -448,7 +458,7 @@ int prepare_parts(uint32_t count, const dfa_t* const* dfas, const uint8_t* const
         if (!dfas[i]) return DFA_EINVAL;
         several |= dfas[i] != first;
         const DevDfa x = launch_desc(dfas[i], slot);
-        const bool smem = x.placement == kSmem && x.table_bytes <= kBatchSmemTable;
+        const bool smem = x.placement == kSmem && smem_table_bytes(x) <= kBatchSmemTable;
         ids[smem ? 0 : 1].push_back(i);
     }
     if (!several || ids[0].empty() || ids[1].empty()) {
@@ -527,6 +537,12 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
     x.K = h.K;
     x.stage_fmt = h.placement == kGlobal ? kOff32 : (h.C + 1 <= 255 ? kCls8 : kOff16);
     x.n_all = h.iset_off[h.C + 2] - h.iset_off[h.C + 1];
+    x.nib = h.nib_rows.empty() ? 0u : 1u;
+    // with byte rows, the 16-bit stage entries are row offsets into them (class * 16)
+    std::vector<uint16_t> off16 = h.byte_off16;
+    if (x.nib)
+        for (int b = 0; b < 256; ++b)
+            off16[b] = h.byte_class[b] == kNone16 ? kNone16 : (uint16_t)(h.byte_class[b] * 16u);
     // planning lookup: one load gives a lookahead byte's class and |I_class|
     uint32_t byte_plan[256];
     for (int b = 0; b < 256; ++b) {
@@ -546,6 +562,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         const uint64_t o_ioff = take(4 * h.iset_off.size()), o_iset = take(2 * h.iset.size());
         const uint64_t o_pos = take(2 * h.pos.size()), o_acc = take(h.accept.size());
         const uint64_t o_exc = take(h.excluded.size()), o_bp = take(sizeof byte_plan);
+        const uint64_t o_nib = take(h.nib_rows.size());
         uint8_t* blk = nullptr;
         if (cudaMalloc(&blk, o) != cudaSuccess) {
             cudaGetLastError();
@@ -564,10 +581,11 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         x.accept = blk + o_acc;
         x.excluded = blk + o_exc;
         x.byte_plan = reinterpret_cast<const uint32_t*>(blk + o_bp);
+        x.nib_rows = x.nib ? blk + o_nib : nullptr;
         d->dev_desc = reinterpret_cast<DevDfa*>(blk + o_desc);
         bool ok = upload_descs(d) == DFA_OK &&
                   cudaMemcpy(blk + o_table, h.table.data(), h.table.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(blk + o_b16, h.byte_off16.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_b16, off16.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_b32, h.byte_off32.data(), 1024, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_bc, h.byte_class.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_ioff, h.iset_off.data(), 4 * h.iset_off.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -575,7 +593,9 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
                   cudaMemcpy(blk + o_pos, h.pos.data(), 2 * h.pos.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_acc, h.accept.data(), h.accept.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_exc, h.excluded.data(), h.excluded.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(blk + o_bp, byte_plan, sizeof byte_plan, cudaMemcpyHostToDevice) == cudaSuccess;
+                  cudaMemcpy(blk + o_bp, byte_plan, sizeof byte_plan, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  (!x.nib || cudaMemcpy(blk + o_nib, h.nib_rows.data(), h.nib_rows.size(),
+                                        cudaMemcpyHostToDevice) == cudaSuccess);
         if (!ok) {
             cudaFree(blk);
             delete d;
@@ -623,6 +643,7 @@ int dfa_info(const dfa_t* d, dfa_info_t* o) {
     o->device_bytes = d->dev_bytes;
     o->gamma = h.gamma;
     o->mean_iset = h.mean_iset;
+    o->byte_rows = h.nib_rows.empty() ? 0u : 1u;
     return DFA_OK;
 }
 
@@ -638,7 +659,7 @@ static int get_tuning_r(const dfa_t* d, uint32_t r, dfa_tuning_t* out) {
 static int set_tuning_r(dfa_t* d, uint32_t r, const dfa_tuning_t* t) {
     if (!d || !t || r >= kTuningSlots) return DFA_EINVAL;
     const uint32_t K = t->states_per_thread ? t->states_per_thread : d->h.K;
-    if (K != 2 && K != 4 && K != 8 && K != 16) return DFA_EINVAL;
+    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16) return DFA_EINVAL;
     if (!k_allowed(d, K)) return DFA_EINVAL;
     if (t->grid_waves > kMaxWaves) return DFA_EINVAL;
     dfa_tuning_t v = *t;
@@ -669,7 +690,7 @@ static int autotune_r(dfa_t* d, const dfa_match_opts_t* base, const uint8_t* dev
     o.lookahead = opts_lookahead(base);
     o.boundary_window = opts_window(base);
     std::vector<dfa_tuning_t> cands;
-    for (uint32_t K : {2u, 4u, 8u, 16u}) {
+    for (uint32_t K : {1u, 2u, 4u, 8u, 16u}) {
         if (!k_allowed(d, K)) continue;
         for (uint32_t tpc : {1u, 2u, 4u, 8u, 16u}) {
             for (uint32_t ctas : {2u, 3u}) {

@@ -151,6 +151,18 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
         h.byte_off32[b] = (uint32_t)off;
         if (fits16) h.byte_off16[b] = (uint16_t)off;
     }
+    // Byte rows (nib_code) when chains visit at most 16 states: every state
+    // including q_e fits, or q_e is unreachable (no -1 in delta; chains start
+    // in Q, as q_e is excluded from every set).  Row C is the identity.
+    bool qe_reachable = false;
+    for (uint64_t i = 0; i < (uint64_t)Q * S && !qe_reachable; ++i) qe_reachable = delta[i] < 0;
+    const uint32_t live = qe_reachable ? qe : Q;
+    if (live <= 16 && h.placement == kSmem) {
+        h.nib_rows.assign((size_t)(C + 1) * 16, 0);
+        for (uint32_t c = 0; c <= C; ++c)
+            for (uint32_t q = 0; q < live; ++q)
+                h.nib_rows[(size_t)c * 16 + q] = (uint8_t)nib_code(c < C ? cols[c][q] : q);
+    }
     // States per thread: enough chains per thread for latency hiding, few
     // enough that the padding of the last thread of a chunk stays small.
     double mean = std::max(1.0, h.mean_iset);
@@ -160,6 +172,9 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
     // further); a chunk with more chains than a tile holds runs its chains in
     // several passes over the chunk (large DFAs)
     while ((std::max(h.imax, 1u) + h.K - 1) / h.K > (uint32_t)kThreads / 2 && h.K < 16) h.K *= 2;
+    // byte-row chains are latency-bound (a step is a short dependent chain of
+    // permutes, not a load that other chains can hide): one chain per thread
+    if (!h.nib_rows.empty()) h.K = 1;
     h.K0 = h.K;
     *out = std::move(h);
     return DFA_OK;

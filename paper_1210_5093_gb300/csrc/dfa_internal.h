@@ -71,8 +71,24 @@ struct DevDfa {
     uint32_t vcap;               // largest set size (incl. start set) = capacity of a state map
     uint32_t stage_fmt;          // StageFmt of the staged input stream
     uint32_t n_all;              // |Q| minus the excluded states: the set Algorithm 2 matches
-    uint32_t pad_;
+    uint32_t nib;                // 1: at most 16 live states, matched from byte rows (nib_rows)
+    const uint8_t* nib_rows;     // nib: (C+1) rows of 16 bytes, byte s = nib_code(delta(s, c))
 };
+
+// Byte rows for DFAs whose chains only ever visit 16 states or fewer (every
+// state, or every state but an unreachable q_e): row c holds, in byte s,
+// the code of delta(s, c), so one step of a chain is a byte permute of the
+// row (two 8-byte halves, picked by bit 7 of the code) instead of a
+// dependent table load.  Code of state s: the low 3 bits of s, and bit 3 of
+// s moved to bit 7, so the code's low nibble is a clean permute selector.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t nib_code(uint32_t s) { return (s & 7u) | ((s & 8u) << 4); }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t nib_state(uint32_t code) { return (code & 7u) | ((code >> 4) & 8u); }
 
 // How a chunk's input is staged in shared memory: 8-bit class indices
 // (16 positions per 16-byte read; shared-memory tables with at most 254
@@ -223,6 +239,7 @@ struct HostDfa {
     std::vector<uint8_t> table;         // (C+1)*qpad*sb
     std::vector<uint16_t> byte_off16;   // 256
     std::vector<uint32_t> byte_off32;   // 256
+    std::vector<uint8_t> nib_rows;      // (C+1) x 16 when at most 16 states are live, else empty
 };
 
 // Compile (validation, classes, excluded states, I sets, table image).

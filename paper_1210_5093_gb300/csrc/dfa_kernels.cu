@@ -763,6 +763,60 @@ __device__ __forceinline__ void run_global(uint32_t (&s)[K], const uint8_t* tbl,
     }
 }
 
+// One chain step on a byte row (DFAs with at most 16 live states): the row's
+// 16 bytes hold the codes (nib_code) of the next states; the code's low
+// nibble selects a byte of each 8-byte half, and its bit 7 picks the half.
+// Only byte 0 of the result is meaningful, and it is the next code.  (A
+// third permute in place of the select measured slower: permutes issue at
+// half rate.)
+__device__ __forceinline__ uint32_t nib_step(const uint4& row, uint32_t code) {
+    const uint32_t lo = __byte_perm(row.x, row.y, code);
+    const uint32_t hi = __byte_perm(row.z, row.w, code);
+    return (code & 0x80u) ? hi : lo;
+}
+
+// Advance K chains over one staged segment of S positions with byte rows in
+// shared memory at tb.  The stage holds 8-bit class indices (CLS8; row =
+// class * 16) or 16-bit row byte offsets.  The rows of the next four steps
+// depend only on the input, so they are loaded while the chains take the
+// current four.
+template <int K, bool CLS8>
+__device__ __forceinline__ void run_nib(uint32_t (&s)[K], uint32_t tb, uint32_t stage_addr, int S) {
+    constexpr int kPer = CLS8 ? 16 : 8;  // stage entries per 16-byte read
+    auto row_addr = [&](const uint4& w, int i) -> uint32_t {
+        const uint32_t word = i / (4 / (CLS8 ? 1 : 2)) == 0 ? w.x
+                            : (i / (4 / (CLS8 ? 1 : 2)) == 1 ? w.y
+                            : (i / (4 / (CLS8 ? 1 : 2)) == 2 ? w.z : w.w));
+        return CLS8 ? tb + ((word >> (8 * (i & 3))) & 0xFFu) * 16u
+                    : tb + ((word >> (16 * (i & 1))) & 0xFFFFu);
+    };
+    uint4 w = lds_v4(stage_addr);
+    uint4 cur[4], nxt[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) cur[g] = lds_v4(row_addr(w, g));
+    for (int j = 0; j < S; j += kPer) {
+#pragma unroll
+        for (int q = 0; q < kPer; q += 4) {
+            // rows of steps j+q+4 .. j+q+7 (the next stage read at the end of
+            // this read's entries; the segment's last group reloads its own)
+            const bool last_of_read = q + 4 == kPer;
+            const bool last = last_of_read && j + kPer >= S;
+            uint4 wn = w;
+            if (last_of_read && !last) wn = lds_v4(stage_addr + (uint32_t)(j + kPer) * (CLS8 ? 1u : 2u));
+            const int qn = last ? q : (last_of_read ? 0 : q + 4);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) nxt[g] = lds_v4(row_addr(last_of_read && !last ? wn : w, qn + g));
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+#pragma unroll
+                for (int u = 0; u < K; ++u) s[u] = nib_step(cur[g], s[u]);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) cur[g] = nxt[g];
+            w = wn;
+        }
+    }
+}
+
 // One tile's chains for a given K: load initial states, run all segments
 // (staging is done by the caller through `stage_fn`), store the final states
 // into the tile-local map (plain state ids).
@@ -898,6 +952,7 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
     uint32_t s[K];
     const uint32_t fmt = d.stage_fmt;
     const uint32_t sh = d.sb == 4 ? 2 : (d.sb == 2 ? 1 : 0);
+    const bool nib = d.nib != 0;
     if (c.active) {
         const ChunkMeta m = meta[c.ci];
         const uint32_t size = m.size;
@@ -906,7 +961,7 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
             uint32_t slot = (uint32_t)c.r * K + u;
             if (slot >= size) slot = (uint32_t)c.r * K;  // padding chain: repeat the first
             const uint32_t init = m.init[slot];
-            s[u] = init << sh;
+            s[u] = nib ? nib_code(init) : init << sh;
             asm volatile("st.shared.u16 [%0], %1;" :: "r"(c.linit + 2u * ((uint32_t)(threadIdx.x) * K + u)),
                          "h"((uint16_t)init) : "memory");
         }
@@ -914,7 +969,7 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
 #pragma unroll
         for (int u = 0; u < K; ++u) s[u] = 0;
     }
-    const uint32_t rowbytes = d.qpad * d.sb;
+    const uint32_t rowbytes = nib ? 16u : d.qpad * d.sb;
     const uint32_t id_off = fmt == kCls8 ? d.C : d.C * rowbytes;  // the identity row
     const int nseg = (int)((maxlen + c.S - 1) / c.S);
     const uint32_t esz = stage_esz(fmt);
@@ -926,7 +981,10 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
         __syncthreads();
         if (c.active) {
             const uint32_t my = stage + (uint32_t)(c.ci * c.S) * esz;
-            if (fmt == kCls8) {
+            if (nib) {
+                if (fmt == kCls8) run_nib<K, true>(s, c.tb, my, c.S);
+                else run_nib<K, false>(s, c.tb, my, c.S);
+            } else if (fmt == kCls8) {
                 if (d.sb == 1) run_smem8<K, 1>(s, c.tb, rowbytes, my, c.S);
                 else run_smem8<K, 2>(s, c.tb, rowbytes, my, c.S);
             } else if (fmt == kOff16) {
@@ -944,7 +1002,7 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
         const ChunkMeta m = meta[c.ci];
 #pragma unroll
         for (int u = 0; u < K; ++u) {
-            uint32_t v = s[u] >> sh;
+            uint32_t v = nib ? nib_state(s[u] & 0xFFu) : s[u] >> sh;
             asm volatile("st.shared.u16 [%0], %1;" :: "r"(c.lmap + 2u * ((uint32_t)(threadIdx.x) * K + u)),
                          "h"((uint16_t)v) : "memory");
             // inspection output: L_k[j] = delta*(j, chunk k) for j in I_k (Sec. 4.1)
@@ -1180,9 +1238,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 reinterpret_cast<uint32_t*>(&d)[tid] = reinterpret_cast<const uint32_t*>(lp.dfas + di)[tid];
             __syncthreads();
             if (d.placement == kSmem) {
-                const uint4* src = reinterpret_cast<const uint4*>(d.table);
+                const uint4* src = reinterpret_cast<const uint4*>(d.nib ? d.nib_rows : d.table);
                 uint4* dst = reinterpret_cast<uint4*>(sm + L.table);
-                const uint32_t n16 = (d.table_bytes + 15) / 16;
+                const uint32_t n16 = d.nib ? d.C + 1 : (d.table_bytes + 15) / 16;
                 for (uint32_t i = tid; i < n16; i += kThreads) dst[i] = __ldg(src + i);
                 if (d.stage_fmt == kCls8) {
                     uint8_t* bc = sm + L.boff;
@@ -1284,7 +1342,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
         const uint32_t boff = sa(sm + L.boff);
         uint16_t* dbg = lp.dbg_maps;
         const uint32_t dst_ = lp.qe_max;
-        if (d.K == 2) tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        if (d.K == 1) tile_chains<1>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        else if (d.K == 2) tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         else if (KMAX >= 8 && d.K == 4)
             tile_chains<(KMAX >= 8 ? 4 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         else if (KMAX >= 16 && d.K == 8)

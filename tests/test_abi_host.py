@@ -184,3 +184,19 @@ def test_compile_large_dfas_and_the_state_limit(dm):
     with pytest.raises(dm.DfaError) as e:
         dm.Dfa(65535, 2, too_big, 0, [1], m2, host_only=True)
     assert e.value.status == dm.EINVAL
+
+
+def test_byte_rows_chosen_for_at_most_16_live_states(dm):
+    """Byte rows (16 next-state codes per class row) are used exactly when a
+    chain can visit at most 16 states: |Q| + 1 <= 16, or |Q| = 16 with q_e
+    unreachable (no -1 in delta), and the table is in shared memory."""
+    m = np.full(256, 0xFF, dtype=np.uint8)
+    m[97:100] = np.arange(3)
+    cases = [(gen.plain_dfa(1), 1),                                          # 16 states, no -1
+             (gen.random_dfa(3, 15, 3, missing=0.2, byte_to_symbol=m), 1),   # q_e is the 16th
+             (gen.random_dfa(4, 16, 3, missing=0.2, byte_to_symbol=m), 0),   # 17 live states
+             (gen.random_dfa(5, 8, 3, byte_to_symbol=m), 1),
+             (gen.regex_dfa(2), 0)]
+    for spec, want in cases:
+        d = dm.Dfa.from_spec(spec, host_only=True)
+        assert d.info().byte_rows == want, spec.name

@@ -70,6 +70,39 @@ def test_random_dfas_many_chunkings(dm, seed):
             _check(dm, d, spec, data[:n], num_chunks=P)
 
 
+@pytest.mark.parametrize("Q,S,missing", [(16, 256, 0.0), (15, 5, 0.2), (8, 3, 0.0),
+                                         (3, 2, 0.3), (12, 40, 0.05)])
+def test_byte_row_dfas(dm, Q, S, missing):
+    """DFAs whose chains visit at most 16 states are stepped by byte permutes
+    of 16-byte class rows.  Codes with bit 3 of the state set (states 8-15)
+    take the upper half of a row; q_e is the 16th state when |Q| = 15.  Every
+    chains-per-thread choice, Algorithm 2, Eq. 13 sets and a batch, against
+    the oracle."""
+    import torch
+    spec = gen.random_dfa(5000 + Q, Q, S, num_finals=max(1, Q // 4), missing=missing)
+    if S != 256:
+        m = np.full(256, 0xFF, dtype=np.uint8)
+        m[:S] = np.arange(S)
+        spec.byte_to_symbol = m
+    d = dm.Dfa.from_spec(spec)
+    assert d.info().byte_rows == 1
+    data = gen.uniform_bytes(6000 + Q, 1 << 20)
+    if S != 256:
+        data = (data % S).astype(np.uint8)
+    for K in (2, 4, 8, 16):
+        d.set_tuning(states_per_thread=K)
+        for n in (0, 1, 17, 4097, 1 << 20):
+            for P in (0, 1, 3, 1024):
+                _check(dm, d, spec, data[:n], num_chunks=P)
+    _check(dm, d, spec, data, lookahead=0)
+    _check(dm, d, spec, data, lookahead=3, num_chunks=500)
+    _check(dm, d, spec, data, boundary_window=64)
+    xs = [data[: 1000 * (i + 1) + i] for i in range(5)]
+    res = dm.match_batch([d] * 5, [torch.from_numpy(x).cuda() for x in xs])
+    for x, (fs, acc, st) in zip(xs, res):
+        assert (st, fs, acc) == _expect(spec, x)
+
+
 @pytest.mark.parametrize("k", [1, 3, 8])
 def test_mod_counter_gamma_one(dm, k):
     spec = gen.mod_counter_dfa(k, 3)
