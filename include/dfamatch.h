@@ -419,7 +419,10 @@ typedef struct {
  * at most 64), so new requests start while earlier batches still run
  * (continuous batching).  A batch takes at most hbm_budget_bytes /
  * max_inflight bytes, so one batch's copies overlap another's matching.
- * DFAs must stay alive while requests on them are pending.
+ * While two batches are on the device, the queue is launched only once it
+ * fills a whole batch; otherwise it keeps growing into the next batch (fewer,
+ * larger launches under load, each request launched at once when the device
+ * is idle).  DFAs must stay alive while requests on them are pending.
  */
 int dfa_server_create(uint64_t hbm_budget_bytes, uint32_t max_inflight, dfa_server_t **out);
 /* Planning options of the batches formed from now on: opts->lookahead (Algorithm

@@ -28,6 +28,11 @@ double now_s() {
 }
 
 constexpr uint32_t kMaxBatch = 4096;      // requests per launch
+// Batches on the device before a new one is formed from a partial queue: two
+// keep the GPU busy (one runs while the next waits on its stream), and while
+// they run the queue grows into a larger, more efficient next batch.  A queue
+// that fills a whole batch is launched whenever a stream is free.
+constexpr uint32_t kLaunchAhead = 2;
 constexpr size_t kMaxPending = 1u << 20;  // queued requests before EAGAIN
 
 // First-fit allocator over the device arena (offsets, 256-byte granules).
@@ -110,6 +115,7 @@ struct dfa_server_s {
     std::thread worker;
     bool stop = false;
     uint64_t next_ticket = 1;
+    uint64_t pending_bytes = 0;  // bytes of the queued requests (under mu)
     dfa_server_stats_t st{};
     int fatal = DFA_OK;
     dfa_match_opts_t opts{};  // lookahead and placement window of every batch (under mu)
@@ -166,8 +172,11 @@ static int grow(uint8_t** p, uint64_t* cap, uint64_t need, bool pinned) {
 
 bool dfa_server_s::launch_one() {
     Slot* slot = nullptr;
-    for (Slot& s : slots)
-        if (!s.busy) { slot = &s; break; }
+    uint32_t busy = 0;
+    for (Slot& s : slots) {
+        if (s.busy) ++busy;
+        else if (!slot) slot = &s;
+    }
     if (!slot) return false;
     std::vector<Req> batch;
     dfa_match_opts_t bo;
@@ -178,6 +187,8 @@ bool dfa_server_s::launch_one() {
         // at most budget / slots bytes, so that every slot can be in flight and
         // one batch's copies overlap another's matching
         const uint64_t batch_cap = std::max<uint64_t>(budget / slots.size(), 1);
+        if (busy >= kLaunchAhead && pending_bytes < batch_cap && pending.size() < kMaxBatch)
+            return false;  // let the queue grow while the device is busy
         uint64_t batch_bytes = 0;
         while (!pending.empty() && batch.size() < kMaxBatch) {
             Req r = pending.front();
@@ -188,6 +199,7 @@ bool dfa_server_s::launch_one() {
             r.dev_off = off;
             st.bytes_in_flight += r.len;
             if (st.bytes_in_flight > st.max_bytes_in_flight) st.max_bytes_in_flight = st.bytes_in_flight;
+            pending_bytes -= r.len;
             pending.pop_front();
             batch.push_back(r);
         }
@@ -337,6 +349,7 @@ int dfa_server_submit(dfa_server_t* s, const dfa_t* dfa, const uint8_t* str, uin
     if (s->pending.size() >= kMaxPending) return DFA_EAGAIN;
     Req r{s->next_ticket++, dfa, str, len, now_s(), 0};
     s->pending.push_back(r);
+    s->pending_bytes += len;
     s->st.submitted++;
     *ticket = r.ticket;
     s->cv.notify_one();
