@@ -16,6 +16,7 @@ import ctypes
 import math
 import os
 import subprocess
+import threading
 from dataclasses import dataclass, field
 from typing import Optional
 
@@ -24,6 +25,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libdfagen.so")
 _lib = None
+_lib_lock = threading.Lock()  # first use may come from several threads at once
 
 # stream ids (any distinct constants)
 S_DELTA, S_FINAL, S_GAMMA, S_TARGET, S_PERM, S_CLASSMAP, S_TEXT, S_PLANT, S_PLANTW, \
@@ -34,7 +36,7 @@ def build(force: bool = False) -> str:
     """Compile gen.c into libdfagen.so (gcc, no GPU)."""
     src = os.path.join(_HERE, "gen.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
-        tmp = _SO + ".tmp%d" % os.getpid()
+        tmp = _SO + ".tmp%d.%d" % (os.getpid(), threading.get_ident())
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", src,
                                "-o", tmp])
         os.replace(tmp, _SO)
@@ -42,6 +44,14 @@ def build(force: bool = False) -> str:
 
 
 def _L():
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        return _load()
+
+
+def _load():
     global _lib
     if _lib is None:
         build()

@@ -28,6 +28,7 @@ import ctypes
 import itertools
 import os
 import subprocess
+import threading
 from fractions import Fraction
 from math import floor
 from typing import Optional, Sequence
@@ -37,6 +38,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
+_lib_lock = threading.Lock()  # first use may come from several threads at once
 
 OK, EINVAL, ESYMBOL, ENOMEM = 0, -1, -2, -3
 
@@ -45,13 +47,21 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so with gcc (plain -O2, no vector flags)."""
     src = os.path.join(_HERE, "oracle.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
-        tmp = _SO + ".tmp%d" % os.getpid()
+        tmp = _SO + ".tmp%d.%d" % (os.getpid(), threading.get_ident())
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", src, "-o", tmp])
         os.replace(tmp, _SO)
     return _SO
 
 
 def _L():
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        return _load()
+
+
+def _load():
     global _lib
     if _lib is None:
         build()

@@ -28,11 +28,13 @@ double now_s() {
 }
 
 constexpr uint32_t kMaxBatch = 4096;      // requests per launch
-// Batches on the device before a new one is formed from a partial queue: two
-// keep the GPU busy (one runs while the next waits on its stream), and while
-// they run the queue grows into a larger, more efficient next batch.  A queue
-// that fills a whole batch is launched whenever a stream is free.
+// A queue shorter than kAheadBytes is held back (to grow into a larger, more
+// efficient batch) only while the device already has work: at least
+// kLaunchAhead batches and kAheadBytes of input in flight, a few milliseconds
+// of matching.  Below that every request is launched at once; a queue of
+// kAheadBytes or more is launched whenever a stream is free.
 constexpr uint32_t kLaunchAhead = 2;
+constexpr uint64_t kAheadBytes = 512ull << 20;
 constexpr size_t kMaxPending = 1u << 20;  // queued requests before EAGAIN
 
 // First-fit allocator over the device arena (offsets, 256-byte granules).
@@ -187,7 +189,8 @@ bool dfa_server_s::launch_one() {
         // at most budget / slots bytes, so that every slot can be in flight and
         // one batch's copies overlap another's matching
         const uint64_t batch_cap = std::max<uint64_t>(budget / slots.size(), 1);
-        if (busy >= kLaunchAhead && pending_bytes < batch_cap && pending.size() < kMaxBatch)
+        if (busy >= kLaunchAhead && st.bytes_in_flight >= kAheadBytes &&
+            pending_bytes < std::min(batch_cap, kAheadBytes) && pending.size() < kMaxBatch)
             return false;  // let the queue grow while the device is busy
         uint64_t batch_bytes = 0;
         while (!pending.empty() && batch.size() < kMaxBatch) {

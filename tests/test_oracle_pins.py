@@ -329,3 +329,18 @@ def test_excluded_states_keep_every_chunking_exact(which):
                 starts = [0, *cuts, L]
                 st2, fs2, a2, _ = o.chunked(data, starts)
                 assert (st2, fs2, a2) == (st, fs, a), (w, starts)
+
+
+def test_oracle_first_use_from_many_threads():
+    """The CPU baseline runs the oracle on all host cores at once: concurrent
+    builds and first loads of the C library must not collide."""
+    import concurrent.futures as cf
+    spec = gen.random_dfa(7, 9, 256, num_finals=2)
+    data = gen.uniform_bytes(8, 10000)
+    want = oracle.Dfa.from_spec(spec).run(data)
+
+    def one(_):
+        oracle.build(force=True)
+        return oracle.Dfa.from_spec(spec).run(data)
+    with cf.ThreadPoolExecutor(4) as ex:
+        assert set(ex.map(one, range(4))) == {want}
