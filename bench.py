@@ -430,7 +430,8 @@ def serving_leg(dm, torch, dfas, pinned, rate_gbs: float, seconds: float = 2.0,
             "offered_req_s": round(lam, 1), "achieved_gbs": round(nbytes / (t_last - t_first) / 1e9, 3),
             "p50_ms": round(lat[len(lat) // 2], 3),
             "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
-            "launches": int(st.launches), "max_concurrent_batches": int(st.max_concurrent),
+            "launches": int(st.launches), "mean_batch_bytes": int(nbytes / max(1, int(st.launches))),
+            "max_concurrent_batches": int(st.max_concurrent),
             "budget_bytes": budget, "clocks": clocks}, done, sub
 
 

@@ -188,7 +188,10 @@ bool dfa_server_s::launch_one() {
         // admission in arrival order while the arena has room; one batch takes
         // at most budget / slots bytes, so that every slot can be in flight and
         // one batch's copies overlap another's matching
-        const uint64_t batch_cap = std::max<uint64_t>(budget / slots.size(), 1);
+        // and at most 2 * kAheadBytes: larger batches fill slowly (latency) and
+        // serialise their copies before their matching
+        const uint64_t batch_cap =
+            std::max<uint64_t>(std::min<uint64_t>(budget / slots.size(), 2 * kAheadBytes), 1);
         if (busy >= kLaunchAhead && st.bytes_in_flight >= kAheadBytes &&
             pending_bytes < std::min(batch_cap, kAheadBytes) && pending.size() < kMaxBatch)
             return false;  // let the queue grow while the device is busy
