@@ -92,6 +92,7 @@ struct Req {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t copied = nullptr;  // the batch's input copies have landed (on copy_stream)
     bool busy = false;
     std::vector<Req> reqs;
     uint8_t* ws = nullptr;
@@ -115,6 +116,12 @@ struct dfa_server_s {
     std::deque<dfa_completion_t> done;
     std::vector<Slot> slots;
     std::thread worker;
+    // Every batch's input copies go on this one stream, in launch order, so the
+    // copies of the oldest batch finish first and its matching (on its own
+    // stream, after an event wait) overlaps the copies of the batches behind
+    // it.  Copies spread over the batches' own streams would share the link
+    // and delay every batch's matching until all their copies had landed.
+    cudaStream_t copy_stream = nullptr;
     bool stop = false;
     uint64_t next_ticket = 1;
     uint64_t pending_bytes = 0;  // bytes of the queued requests (under mu)
@@ -240,8 +247,11 @@ bool dfa_server_s::launch_one() {
         cudaStream_t s = slot->stream;
         for (uint32_t i = 0; i < n && rc == DFA_OK; ++i)
             if (lens[i] && cudaMemcpyAsync(arena_mem + batch[i].dev_off, batch[i].host, lens[i],
-                                           cudaMemcpyHostToDevice, s) != cudaSuccess)
+                                           cudaMemcpyHostToDevice, copy_stream) != cudaSuccess)
                 rc = DFA_ECUDA;
+        if (rc == DFA_OK && (cudaEventRecord(slot->copied, copy_stream) != cudaSuccess ||
+                             cudaStreamWaitEvent(s, slot->copied, 0) != cudaSuccess))
+            rc = DFA_ECUDA;
         slot->dev_out = reinterpret_cast<dfa_result_t*>(slot->ws + out_off);
         for (size_t k = 0; k < parts.size() && rc == DFA_OK; ++k) {
             rc = dfam::upload_desc_async(parts[k], slot->ws + ws_off[k], slot->pinned + stage_off[k], s);
@@ -265,6 +275,7 @@ bool dfa_server_s::launch_one() {
     }
     if (rc != DFA_OK) {
         cudaGetLastError();
+        cudaStreamSynchronize(copy_stream);  // no copy into the batch's arena space is left
         cudaStreamSynchronize(slot->stream);
     }
     return true;
@@ -308,18 +319,22 @@ int dfa_server_create(uint64_t budget, uint32_t max_inflight, dfa_server_t** out
     s->opts.lookahead = 1;
     s->arena.reset(budget);
     s->slots.resize(max_inflight);
-    for (Slot& sl : s->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            for (Slot& x : s->slots) {
-                if (x.stream) cudaStreamDestroy(x.stream);
-                if (x.done) cudaEventDestroy(x.done);
-            }
-            cudaFree(s->arena_mem);
-            delete s;
-            return DFA_ECUDA;
+    bool ok = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (Slot& sl : s->slots)
+        ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (Slot& x : s->slots) {
+            if (x.stream) cudaStreamDestroy(x.stream);
+            if (x.done) cudaEventDestroy(x.done);
+            if (x.copied) cudaEventDestroy(x.copied);
         }
+        if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+        cudaFree(s->arena_mem);
+        delete s;
+        return DFA_ECUDA;
     }
     s->worker = std::thread([s] { s->run(); });
     *out = s;
@@ -409,6 +424,11 @@ void dfa_server_destroy(dfa_server_t* s) {
         if (sl.pinned) cudaFreeHost(sl.pinned);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.copied) cudaEventDestroy(sl.copied);
+    }
+    if (s->copy_stream) {
+        cudaStreamSynchronize(s->copy_stream);
+        cudaStreamDestroy(s->copy_stream);
     }
     if (s->arena_mem) cudaFree(s->arena_mem);
     delete s;
