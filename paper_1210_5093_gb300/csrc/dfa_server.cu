@@ -245,6 +245,12 @@ bool dfa_server_s::launch_one() {
     if (rc == DFA_OK) rc = grow(&slot->pinned, &slot->pinned_bytes, pinned_need, true);
     if (rc == DFA_OK) {
         cudaStream_t s = slot->stream;
+        // the batch's launch descriptors, then its input, all on the copy
+        // stream: the matching stream then holds no host-to-device copy that
+        // could queue behind a later batch's input on the copy engine
+        for (size_t k = 0; k < parts.size() && rc == DFA_OK; ++k)
+            rc = dfam::upload_desc_async(parts[k], slot->ws + ws_off[k], slot->pinned + stage_off[k],
+                                         copy_stream);
         for (uint32_t i = 0; i < n && rc == DFA_OK; ++i)
             if (lens[i] && cudaMemcpyAsync(arena_mem + batch[i].dev_off, batch[i].host, lens[i],
                                            cudaMemcpyHostToDevice, copy_stream) != cudaSuccess)
@@ -253,10 +259,8 @@ bool dfa_server_s::launch_one() {
                              cudaStreamWaitEvent(s, slot->copied, 0) != cudaSuccess))
             rc = DFA_ECUDA;
         slot->dev_out = reinterpret_cast<dfa_result_t*>(slot->ws + out_off);
-        for (size_t k = 0; k < parts.size() && rc == DFA_OK; ++k) {
-            rc = dfam::upload_desc_async(parts[k], slot->ws + ws_off[k], slot->pinned + stage_off[k], s);
-            if (rc == DFA_OK) rc = dfam::launch_prepared(parts[k], slot->ws + ws_off[k], slot->dev_out, s);
-        }
+        for (size_t k = 0; k < parts.size() && rc == DFA_OK; ++k)
+            rc = dfam::launch_prepared(parts[k], slot->ws + ws_off[k], slot->dev_out, s);
         if (rc == DFA_OK &&
             cudaMemcpyAsync(slot->pinned, slot->dev_out, 12ull * n, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)
