@@ -418,10 +418,11 @@ typedef struct {
  * into batches as they arrive and launched on max_inflight streams (0 = 8,
  * at most 64), so new requests start while earlier batches still run
  * (continuous batching).  A batch takes at most hbm_budget_bytes /
- * max_inflight bytes and at most 1 GiB, so one batch's copies overlap
+ * max_inflight bytes and at most 512 MiB, so one batch's copies overlap
  * another's matching.  While two batches and 512 MiB are on the device, a
  * queue shorter than 512 MiB is held back to grow into the next batch (fewer,
  * larger launches under load); otherwise requests are launched at once.
+ * Input copies run in launch order on one copy stream.
  * DFAs must stay alive while requests on them are pending.
  */
 int dfa_server_create(uint64_t hbm_budget_bytes, uint32_t max_inflight, dfa_server_t **out);
