@@ -167,9 +167,15 @@ bool dfa_server_s::reap() {
     return any;
 }
 
+// Per-slot buffers are sized at creation for a full batch (kSlotWs device,
+// kSlotPinned pinned host bytes) and doubled when a batch needs more: each
+// regrowth frees memory, which waits for the whole device and stalls every
+// batch in flight.
+constexpr uint64_t kSlotWs = 32ull << 20, kSlotPinned = 1ull << 20;
+
 static int grow(uint8_t** p, uint64_t* cap, uint64_t need, bool pinned) {
     if (*cap >= need) return DFA_OK;
-    uint64_t n = need + need / 2 + 4096;
+    uint64_t n = std::max<uint64_t>(need, 2 * *cap);
     if (*p) { if (pinned) cudaFreeHost(*p); else cudaFree(*p); }
     *p = nullptr;
     *cap = 0;
@@ -329,9 +335,14 @@ int dfa_server_create(uint64_t budget, uint32_t max_inflight, dfa_server_t** out
         ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) == cudaSuccess;
+    for (Slot& sl : s->slots)
+        ok = ok && grow(&sl.ws, &sl.ws_bytes, kSlotWs, false) == DFA_OK &&
+             grow(&sl.pinned, &sl.pinned_bytes, kSlotPinned, true) == DFA_OK;
     if (!ok) {
         cudaGetLastError();
         for (Slot& x : s->slots) {
+            if (x.ws) cudaFree(x.ws);
+            if (x.pinned) cudaFreeHost(x.pinned);
             if (x.stream) cudaStreamDestroy(x.stream);
             if (x.done) cudaEventDestroy(x.done);
             if (x.copied) cudaEventDestroy(x.copied);
