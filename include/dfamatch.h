@@ -40,6 +40,10 @@ extern "C" {
 #define DFA_EAGAIN (-7)   /* server: queue full, retry later */
 #define DFA_ENOSPACE (-8) /* caller's workspace is smaller than the size query returned */
 #define DFA_EHOSTONLY (-9)/* the dfa_t was created with dfa_create_host and has no device image */
+#define DFA_EBOUNDS (-10) /* a device-side index check failed: reported only by the library's
+                             debug build (libdfamatch_debug.so, compiled with DFA_DEBUG_BOUNDS),
+                             which checks every state, class, set slot and chunk bound the
+                             kernels use and skips the access instead of making it */
 
 typedef struct dfa_s dfa_t;
 typedef struct dfa_batch_s dfa_batch_t;
@@ -52,7 +56,8 @@ typedef struct {
                              error state q_e (a -1 entry of delta was taken)  */
     uint8_t accept;       /* 1 iff final_state is in F                          */
     uint8_t reserved[3];
-    int32_t status;       /* DFA_OK, or DFA_ESYMBOL (then final_state/accept are 0) */
+    int32_t status;       /* DFA_OK, or DFA_ESYMBOL (then final_state/accept are 0);
+                             DFA_EBOUNDS only in the debug build                  */
 } dfa_result_t;
 
 /* Static properties of a compiled DFA (Eqs. 11, 12, 18 and the device layout). */

@@ -15,10 +15,14 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdfamatch.so")
+# DFA_DEBUG_BOUNDS=1 loads the build with device-side bounds checks instead
+# (libdfamatch_debug.so: the same kernels, every index checked; a failed check
+# is reported as DFA_EBOUNDS in the test's result)
+DEBUG_BOUNDS = os.environ.get("DFA_DEBUG_BOUNDS", "") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "libdfamatch_debug.so" if DEBUG_BOUNDS else "libdfamatch.so")
 
-OK, EINVAL, ESYMBOL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, EAGAIN, ENOSPACE, EHOSTONLY = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+OK, EINVAL, ESYMBOL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, EAGAIN, ENOSPACE, EHOSTONLY, EBOUNDS = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
 
 _lib = None
 
@@ -120,7 +124,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libdfamatch.so is not built; run paper_1210_5093_gb300.build.build()")
+            raise RuntimeError("%s is not built; run paper_1210_5093_gb300.build.build()"
+                               % os.path.basename(LIB_PATH))
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)

@@ -1327,6 +1327,7 @@ const char* dfa_strerror(int s) {
         case DFA_EAGAIN: return "try again";
         case DFA_ENOSPACE: return "workspace too small";
         case DFA_EHOSTONLY: return "DFA has no device image";
+        case DFA_EBOUNDS: return "device-side bounds check failed";
         default: return "unknown status";
     }
 }

@@ -30,6 +30,28 @@
 
 namespace dfam {
 
+// ------------------------------------------------------------ debug checks
+
+// The debug build (DFA_DEBUG_BOUNDS) checks every state, class, set slot and
+// chunk bound before the kernels use it.  A failed check sets bit 1 of the
+// test's error word (reported as DFA_EBOUNDS) and the caller skips or clamps
+// the access; in the release build the checks compile to nothing.
+#ifdef DFA_DEBUG_BOUNDS
+#define DFAM_OK(cond, err_word) ((cond) ? true : (atomicOr((err_word), 2u), false))
+#else
+#define DFAM_OK(cond, err_word) true
+#endif
+
+// Result status of a test from its error word: bit 0 = a byte outside Sigma,
+// bit 1 = a failed debug check.
+__device__ __forceinline__ int32_t status_of(uint32_t err) {
+    return (err & 2u) ? DFA_EBOUNDS : (err ? DFA_ESYMBOL : DFA_OK);
+}
+// The error word a continuation test inherits from its predecessor's status.
+__device__ __forceinline__ uint32_t err_of(int32_t status) {
+    return status == DFA_OK ? 0u : (status == DFA_EBOUNDS ? 2u : 1u);
+}
+
 // ------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t sa(const void* p) {
@@ -250,6 +272,7 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
             const uint32_t nx = d.sb == 1 ? row[s]
                                 : (d.sb == 2 ? (uint32_t)(reinterpret_cast<const uint16_t*>(row)[s] >> 1)
                                              : reinterpret_cast<const uint32_t*>(row)[s] >> 2);
+            if (!DFAM_OK(nx < d.qe, lp.test_err + ti)) continue;
             if (!d.excluded[nx]) atomicOr(bm + (nx >> 5), 1u << (nx & 31));
         }
         __syncwarp();
@@ -275,10 +298,12 @@ __global__ void __launch_bounds__(kLaWarps * 32) k_lookahead(LaunchPlan lp, uint
             while (bits) {
                 const uint32_t b = __ffs(bits) - 1;
                 bits &= bits - 1;
-                buf[pos++] = (uint16_t)(wi * 32 + b);
+                if (DFAM_OK(pos < gr.set_stride, lp.test_err + ti)) buf[pos] = (uint16_t)(wi * 32 + b);
+                ++pos;
             }
         }
         n = total;
+        if (!DFAM_OK(n <= gr.set_stride, lp.test_err + ti)) n = gr.set_stride;
         __syncwarp();
     }
     for (uint32_t x = lane; x < n; x += 32) out[x] = buf[x];
@@ -379,6 +404,10 @@ __device__ __forceinline__ void chunk_count_n(const LaunchPlan& lp, uint32_t g0,
                 cls = v >> 16;
                 size = v & 0xFFFFu;
             }
+        }
+        if (!DFAM_OK(size >= 1 && size <= 65535u && cls <= Ci + 2, &lp.test_err[lo[i]])) {
+            size = 1;
+            cls = Ci;
         }
         const uint32_t cnt = (size + Ki - 1) / Ki;
         cost[i] = cnt < 2 ? 2 : cnt;
@@ -843,7 +872,7 @@ struct TileCtx {
 // and also get the identity row.
 template <uint32_t FMT>
 __device__ __forceinline__ uint32_t stage_entry(uint32_t b, bool valid, uint32_t boff, uint32_t id_off,
-                                                bool& bad) {
+                                                bool& bad, bool& oob) {
     uint32_t x;
     if (FMT == kOff32) {
         asm volatile("ld.shared.u32 %0, [%1];" : "=r"(x) : "r"(boff + 4 * b));
@@ -855,6 +884,9 @@ __device__ __forceinline__ uint32_t stage_entry(uint32_t b, bool valid, uint32_t
         x = lds_u16(boff + 2 * b);
         if (x == kNone16) { bad |= valid; x = id_off; }
     }
+#ifdef DFA_DEBUG_BOUNDS
+    if (x > id_off) { oob = true; x = id_off; }  // a row past the identity row
+#endif
     return valid ? x : id_off;
 }
 
@@ -891,7 +923,7 @@ __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, ui
             v[2] = (uint32_t)hi; v[3] = (uint32_t)(hi >> 32);
         }
     }
-    bool bad = false;
+    bool bad = false, oob = false;
     if (FMT == kCls8) {
         uint32_t w[4];
 #pragma unroll
@@ -900,7 +932,7 @@ __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, ui
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t j = 4 * i + k;
-                word |= stage_entry<FMT>((v[i] >> (8 * k)) & 0xFFu, j < nvalid, boff, id_off, bad) << (8 * k);
+                word |= stage_entry<FMT>((v[i] >> (8 * k)) & 0xFFu, j < nvalid, boff, id_off, bad, oob) << (8 * k);
             }
             w[i] = word;
         }
@@ -913,8 +945,8 @@ __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, ui
             for (int i = 0; i < 4; ++i) {
                 const uint32_t j = 8 * h + 2 * i;
                 const uint32_t src = v[j >> 2] >> (8 * (j & 3));
-                w[i] = stage_entry<FMT>(src & 0xFFu, j < nvalid, boff, id_off, bad) |
-                       (stage_entry<FMT>((src >> 8) & 0xFFu, j + 1 < nvalid, boff, id_off, bad) << 16);
+                w[i] = stage_entry<FMT>(src & 0xFFu, j < nvalid, boff, id_off, bad, oob) |
+                       (stage_entry<FMT>((src >> 8) & 0xFFu, j + 1 < nvalid, boff, id_off, bad, oob) << 16);
             }
             sts_v4(dst + 16 * h, make_uint4(w[0], w[1], w[2], w[3]));
         }
@@ -924,11 +956,12 @@ __device__ __forceinline__ void stage_group(const ChunkMeta& m, uint32_t pos, ui
             uint32_t w[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                w[k] = stage_entry<FMT>((v[i] >> (8 * k)) & 0xFFu, 4u * i + k < nvalid, boff, id_off, bad);
+                w[k] = stage_entry<FMT>((v[i] >> (8 * k)) & 0xFFu, 4u * i + k < nvalid, boff, id_off, bad, oob);
             sts_v4(dst + 16 * i, make_uint4(w[0], w[1], w[2], w[3]));
         }
     }
     if (bad) atomicOr(test_err + m.test, 1u);
+    if (oob) atomicOr(test_err + m.test, 2u);
 }
 
 template <uint32_t FMT>
@@ -960,7 +993,8 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
         for (int u = 0; u < K; ++u) {
             uint32_t slot = (uint32_t)c.r * K + u;
             if (slot >= size) slot = (uint32_t)c.r * K;  // padding chain: repeat the first
-            const uint32_t init = m.init[slot];
+            uint32_t init = m.init[slot];
+            if (!DFAM_OK(init < d.qe && (!nib || init < 16u), test_err + m.test)) init = 0;
             s[u] = nib ? nib_code(init) : init << sh;
             asm volatile("st.shared.u16 [%0], %1;" :: "r"(c.linit + 2u * ((uint32_t)(threadIdx.x) * K + u)),
                          "h"((uint16_t)init) : "memory");
@@ -1003,6 +1037,7 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
 #pragma unroll
         for (int u = 0; u < K; ++u) {
             uint32_t v = nib ? nib_state(s[u] & 0xFFu) : s[u] >> sh;
+            if (!DFAM_OK(v < d.qe, test_err + m.test)) v = 0;
             asm volatile("st.shared.u16 [%0], %1;" :: "r"(c.lmap + 2u * ((uint32_t)(threadIdx.x) * K + u)),
                          "h"((uint16_t)v) : "memory");
             // inspection output: L_k[j] = delta*(j, chunk k) for j in I_k (Sec. 4.1)
@@ -1076,7 +1111,7 @@ __device__ void combine_test_map(const LaunchPlan& lp, uint32_t t, const DevTest
         r.final_state = 0;
         r.accept = 0;
         r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
-        r.status = atomicOr(lp.test_err + t, 0u) ? DFA_ESYMBOL : DFA_OK;
+        r.status = status_of(atomicOr(lp.test_err + t, 0u));
         lp.results[tt.out] = r;
     }
     __syncthreads();
@@ -1113,6 +1148,7 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
             const uint32_t cb = b0 + j;
             if (__ldcg(lp.cta_range + 2 * cb) == __ldcg(lp.cta_range + 2 * cb + 1)) continue;
             s = __ldcg(lp.seg_vals + (size_t)(cb + t) * lp.seg_stride + s);
+            if (!DFAM_OK(s < qe, lp.test_err + t)) s = 0;
         }
         *cell = s;
     }
@@ -1124,7 +1160,10 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
         if (threadIdx.x == 0) {
             uint32_t s = *cell;
             const uint16_t* m = reinterpret_cast<const uint16_t*>(sm);
-            for (uint32_t j = 0; j < nb; ++j) s = m[(size_t)j * 2 * words + s];
+            for (uint32_t j = 0; j < nb; ++j) {
+                s = m[(size_t)j * 2 * words + s];
+                if (!DFAM_OK(s < qe, lp.test_err + t)) s = 0;
+            }
             *cell = s;
         }
     }
@@ -1132,11 +1171,11 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
     if (threadIdx.x == 0) {
         const uint32_t s = *cell;
         dfa_result_t r;
-        const uint32_t err = atomicOr(lp.test_err + t, 0u) | (cont && lp.results[tt.out].status != DFA_OK);
+        const uint32_t err = atomicOr(lp.test_err + t, 0u) | (cont ? err_of(lp.results[tt.out].status) : 0u);
         r.final_state = err ? 0u : s;
         r.accept = err ? 0 : d.accept[s];
         r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
-        r.status = err ? DFA_ESYMBOL : DFA_OK;
+        r.status = status_of(err);
         lp.results[tt.out] = r;
     }
     __syncthreads();
@@ -1191,7 +1230,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 r.final_state = err ? 0u : s;
                 r.accept = err ? 0 : td.accept[s];
                 r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
-                r.status = err ? DFA_ESYMBOL : DFA_OK;
+                r.status = status_of(err);
                 lp.results[tt.out] = r;
             }
             return;
@@ -1203,7 +1242,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
         const uint32_t tqe = td.qe;
         for (uint32_t s = tid; s < tqe; s += kThreads) dense[s] = (uint16_t)s;
         __syncthreads();
-        for (uint32_t x = tid; x < nD; x += kThreads) dense[vdom[x]] = vmap[x];
+        for (uint32_t x = tid; x < nD; x += kThreads)
+            if (DFAM_OK(vdom[x] < tqe && vmap[x] < tqe, lp.test_err + cur_test)) dense[vdom[x]] = vmap[x];
         if (tid == 0) {
             lp.seg_hdr[slot * 4 + 0] = seg_first;
             lp.seg_hdr[slot * 4 + 1] = seg_n;
@@ -1267,8 +1307,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             const uint32_t te = lp.chunk_test[g];
             const DevTest tt = test_at(lp, te);
             const uint32_t k = g - tt.chunk_base;
-            const uint64_t st = cstart(lp, tt, k), en = cstart(lp, tt, k + 1);
-            const uint32_t cls = lp.chunk_cls[g];
+            uint64_t st = cstart(lp, tt, k), en = cstart(lp, tt, k + 1);
+            uint32_t cls = lp.chunk_cls[g];
+            if (!DFAM_OK(st <= en && en <= tt.n && en - st < (1ull << 31), lp.test_err + te)) en = st;
+            if (!DFAM_OK(cls <= d.C + 2 && (cls < d.C + 2 || lp.dyn), lp.test_err + te)) cls = d.C;
             ChunkMeta m;
             uint32_t size;
             if (cls == dyn_set(d.C)) {
@@ -1279,6 +1321,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 size = d.iset_off[cls + 1] - d.iset_off[cls];
                 m.init = d.iset + d.iset_off[cls];
             }
+            if (!DFAM_OK(size >= 1 && size <= lp.vcap, lp.test_err + te)) size = 1;
             m.size = (uint16_t)size;
             m.ptr = tt.str + st;
             m.len = (uint32_t)(en - st);
@@ -1378,6 +1421,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 const uint16_t* pos = d.pos + (size_t)m.cls * d.qe;
                 for (uint32_t x = tid; x < nD; x += kThreads) {
                     if ((vflag[x >> 5] >> (x & 31)) & 1u) continue;
+                    if (!DFAM_OK(vmap[x] < d.qe, lp.test_err + m.test)) continue;
                     const uint32_t p = __ldg(pos + vmap[x]);
                     if (p != kNone16 && p >= lo && p < hi) {
                         vmap[x] = lmap[p - lo];
@@ -1427,8 +1471,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 const uint16_t* pos = d.pos + (size_t)m.cls * d.qe;
                 for (uint32_t x = tid; x < nD; x += kThreads) {
                     const uint32_t v = vmap[x];
+                    if (!DFAM_OK(v < d.qe, lp.test_err + m.test)) continue;
                     const uint32_t p = __ldg(pos + v);
-                    if (p != kNone16) vmap[x] = lmap[base + p];
+                    if (p != kNone16 &&
+                        DFAM_OK(p < m.size && base + p < (uint32_t)kThreads * kmax, lp.test_err + m.test))
+                        vmap[x] = lmap[base + p];
                 }
             }
             ++seg_n;
@@ -1559,16 +1606,16 @@ __global__ void k_compose_segments(const dfa_result_t* seg_res, const uint16_t* 
                                    dfa_result_t* out) {
     if (threadIdx.x != 0) return;
     uint32_t s = seg_res[0].final_state;
-    bool err = seg_res[0].status != DFA_OK;
+    uint32_t err = err_of(seg_res[0].status);
     for (uint32_t i = 1; i < nseg; ++i) {
-        err |= seg_res[i].status != DFA_OK;
+        err |= err_of(seg_res[i].status);
         if (!err) s = maps[(size_t)i * stride + s];
     }
     dfa_result_t r;
     r.final_state = err ? 0u : s;
     r.accept = err ? 0 : accept[s];
     r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
-    r.status = err ? DFA_ESYMBOL : DFA_OK;
+    r.status = status_of(err);
     *out = r;
 }
 

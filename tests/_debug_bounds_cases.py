@@ -1,0 +1,86 @@
+"""Parity cases run against the debug build of the library (libdfamatch_debug.so,
+loaded when DFA_DEBUG_BOUNDS=1): the same kernels with every state, class, set
+slot and chunk bound checked before use.  A failed check would surface as
+DFA_EBOUNDS in a result; every answer must instead equal the oracle's.
+Run as a script in its own process (the library is chosen at load time)."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import gen      # noqa: E402
+import oracle   # noqa: E402
+
+
+def main():
+    assert os.environ.get("DFA_DEBUG_BOUNDS") == "1"
+    import torch
+    import paper_1210_5093_gb300 as dm
+    assert dm.LIB_PATH.endswith("libdfamatch_debug.so"), dm.LIB_PATH
+    checked = 0
+
+    def check(d, spec, data, **kw):
+        nonlocal checked
+        st, fs, acc = d.match(data, **kw)
+        host = data.cpu().numpy() if isinstance(data, torch.Tensor) else data
+        want = oracle.Dfa.from_spec(spec).run(host)
+        assert st != dm.EBOUNDS, ("bounds check failed", spec.name, kw)
+        assert (st, fs, acc) == want or (st == want[0] != 0), (spec.name, kw, (st, fs, acc), want)
+        checked += 1
+
+    m3 = np.full(256, 0xFF, dtype=np.uint8)
+    m3[:3] = np.arange(3)
+    cases = [
+        (gen.plain_dfa(1), gen.uniform_bytes(1, 1 << 20), [{}, {"num_chunks": 1024}]),
+        (gen.random_dfa(2, 5, 3, missing=0.2, byte_to_symbol=m3),
+         (gen.uniform_bytes(3, 300_000) % 3).astype(np.uint8),
+         [{}, {"num_chunks": 17}, {"lookahead": 0}, {"lookahead": 3}, {"boundary_window": 64}]),
+        (gen.random_dfa(4, 300, 64, num_finals=30, missing=0.02), gen.uniform_bytes(5, 2 << 20),
+         [{}, {"num_chunks": 3000}, {"lookahead": 2}]),
+        (gen.regex_dfa(2), gen.zipf_text(2, 16 << 20),
+         [{}, {"lookahead": 2}, {"lookahead": 4}, {"lookahead": 0}, {"boundary_window": 256},
+          {"num_chunks": 5000, "multiplicity": 3}]),
+        (gen.protein_dfa(3), gen.protein_text(3, 16 << 20), [{}, {"boundary_window": 256}]),
+        (gen.class_dfa(81, 1288, 256, 0.02, 0.3, 12, "byte"), gen.zipf_text(83, 4 << 20),
+         [{}, {"lookahead": 2}]),                                      # table read through L2
+        (gen.class_dfa(1020, 20000, 20, 0.2, 0.9, 200, "protein"), gen.protein_text(9, 300_000),
+         [{}, {"lookahead": 0, "num_chunks": 40}]),                    # multi-pass chunks
+    ]
+    for spec, data, kws in cases:
+        d = dm.Dfa.from_spec(spec)
+        for kw in kws:
+            check(d, spec, data, **kw)
+            check(d, spec, data[: len(data) // 3 + 7], **kw)
+        if spec.byte_to_symbol is not None and (spec.byte_to_symbol == 0xFF).any():
+            bad = data.copy()       # a byte outside Sigma in the middle: DFA_ESYMBOL
+            bad[len(bad) // 2] = int(np.nonzero(spec.byte_to_symbol == 0xFF)[0][0])
+            check(d, spec, bad)
+    # a batch of several DFAs (shared-memory and L2 tables), with graph replay
+    specs = [gen.regex_dfa(2), gen.plain_dfa(1), gen.class_dfa(81, 1288, 256, 0.02, 0.3, 12, "byte")]
+    dfas = [dm.Dfa.from_spec(s) for s in specs]
+    xs = [gen.zipf_text(40 + i, 50_000 * (i + 1) + i) for i in range(9)]
+    tens = [torch.from_numpy(x).cuda() for x in xs]
+    picks = [i % 3 for i in range(9)]
+    b = dm.Batch([dfas[p] for p in picks], tens)
+    out = torch.zeros(12 * len(tens), dtype=torch.uint8, device="cuda")
+    for graph in (False, True):
+        b.launch(out, graph=graph)
+        torch.cuda.synchronize()
+        for i, (fs, acc, st) in enumerate(dm.results_from(out)):
+            assert st != dm.EBOUNDS
+            assert (st, fs, acc) == oracle.Dfa.from_spec(specs[picks[i]]).run(xs[i])
+            checked += 1
+    b.close()
+    # the pipelined host path (map tests and their combine), on pinned memory
+    w = gen.regex_workload(2, 96 << 20)
+    d = dm.Dfa.from_spec(w.spec)
+    d.set_tuning(host_segment_bytes=8 << 20)
+    check(d, w.spec, torch.from_numpy(w.data).pin_memory())
+    print("debug-bounds parity ok: %d checks" % checked)
+
+
+if __name__ == "__main__":
+    main()

@@ -200,3 +200,14 @@ def test_byte_rows_chosen_for_at_most_16_live_states(dm):
     for spec, want in cases:
         d = dm.Dfa.from_spec(spec, host_only=True)
         assert d.info().byte_rows == want, spec.name
+
+
+def test_debug_library_exports_the_same_symbols(dm):
+    """The debug build (DFA_DEBUG_BOUNDS) is the same ABI."""
+    import ctypes
+    from paper_1210_5093_gb300 import build
+    build.build()
+    L = ctypes.CDLL(build.OUT_DEBUG)
+    for name in dm.SIGNATURES:
+        assert hasattr(L, name), name
+    assert L.dfa_strerror  # loads without a GPU
