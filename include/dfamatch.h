@@ -43,7 +43,8 @@ extern "C" {
 #define DFA_EBOUNDS (-10) /* a device-side index check failed: reported only by the library's
                              debug build (libdfamatch_debug.so, compiled with DFA_DEBUG_BOUNDS),
                              which checks every state, class, set slot and chunk bound the
-                             kernels use and skips the access instead of making it */
+                             kernels use and skips the access instead of making it; the
+                             result's final_state then holds the source line of the check */
 
 typedef struct dfa_s dfa_t;
 typedef struct dfa_batch_s dfa_batch_t;

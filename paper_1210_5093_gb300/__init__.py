@@ -291,6 +291,8 @@ class Dfa:
             ptr, n = keep.ctypes.data, keep.size
         rc = lib().dfa_match(self._h, ptr if n else None, n, ctypes.byref(o), ctypes.byref(res))
         del keep
+        if rc == EBOUNDS:   # debug build: final_state holds the source line of the failed check
+            raise DfaError(rc, "dfa_match (check at dfa_kernels.cu line %d)" % res.final_state)
         if rc not in (OK, ESYMBOL):
             raise DfaError(rc, "dfa_match")
         if rc == ESYMBOL:

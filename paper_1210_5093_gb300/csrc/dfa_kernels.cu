@@ -37,7 +37,10 @@ namespace dfam {
 // test's error word (reported as DFA_EBOUNDS) and the caller skips or clamps
 // the access; in the release build the checks compile to nothing.
 #ifdef DFA_DEBUG_BOUNDS
-#define DFAM_OK(cond, err_word) ((cond) ? true : (atomicOr((err_word), 2u), false))
+// the error word keeps the largest source line of a failed check above bit 8;
+// a DFA_EBOUNDS result reports it as its final_state
+#define DFAM_OK(cond, err_word) \
+    ((cond) ? true : (atomicMax((err_word), ((uint32_t)__LINE__ << 8) | 2u), false))
 #else
 #define DFAM_OK(cond, err_word) true
 #endif
@@ -46,6 +49,11 @@ namespace dfam {
 // bit 1 = a failed debug check.
 __device__ __forceinline__ int32_t status_of(uint32_t err) {
     return (err & 2u) ? DFA_EBOUNDS : (err ? DFA_ESYMBOL : DFA_OK);
+}
+// final_state of a result: the state, 0 for a failed test, or (debug build,
+// DFA_EBOUNDS) the source line of the failed check.
+__device__ __forceinline__ uint32_t final_of(uint32_t err, uint32_t s) {
+    return err ? ((err & 2u) ? err >> 8 : 0u) : s;
 }
 // The error word a continuation test inherits from its predecessor's status.
 __device__ __forceinline__ uint32_t err_of(int32_t status) {
@@ -405,7 +413,7 @@ __device__ __forceinline__ void chunk_count_n(const LaunchPlan& lp, uint32_t g0,
                 size = v & 0xFFFFu;
             }
         }
-        if (!DFAM_OK(size >= 1 && size <= 65535u && cls <= Ci + 2, &lp.test_err[lo[i]])) {
+        if (!DFAM_OK(size <= 65535u && cls <= Ci + 2, &lp.test_err[lo[i]])) {
             size = 1;
             cls = Ci;
         }
@@ -1172,7 +1180,7 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
         const uint32_t s = *cell;
         dfa_result_t r;
         const uint32_t err = atomicOr(lp.test_err + t, 0u) | (cont ? err_of(lp.results[tt.out].status) : 0u);
-        r.final_state = err ? 0u : s;
+        r.final_state = final_of(err, s);
         r.accept = err ? 0 : d.accept[s];
         r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
         r.status = status_of(err);
@@ -1205,6 +1213,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
     // a CTA without a share returns at once
     const uint32_t t0 = lp.cta_range[2 * b], t1 = lp.cta_range[2 * b + 1];
     if (t0 >= t1) return;
+    // the done-flags of multi-pass composition start cleared (shared memory
+    // holds whatever an earlier kernel left there); each multi-pass chunk
+    // clears the flags it set
+    if (lp.vmap_stride)
+        for (uint32_t w = tid; w < (lp.vcap + 31) / 32; w += kThreads) vflag[w] = 0;
     const uint32_t c_lo = lp.tile_first[t0], c_hi = lp.tile_first[t1];
 
     int cur_dfa = -1;
@@ -1227,7 +1240,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 const uint32_t s = vmap[0];
                 const uint32_t err = atomicOr(lp.test_err + cur_test, 0u);
                 dfa_result_t r;
-                r.final_state = err ? 0u : s;
+                r.final_state = final_of(err, s);
                 r.accept = err ? 0 : td.accept[s];
                 r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
                 r.status = status_of(err);
@@ -1321,7 +1334,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                 size = d.iset_off[cls + 1] - d.iset_off[cls];
                 m.init = d.iset + d.iset_off[cls];
             }
-            if (!DFAM_OK(size >= 1 && size <= lp.vcap, lp.test_err + te)) size = 1;
+            if (!DFAM_OK(size <= lp.vcap, lp.test_err + te)) size = 1;
             m.size = (uint16_t)size;
             m.ptr = tt.str + st;
             m.len = (uint32_t)(en - st);
@@ -1612,7 +1625,7 @@ __global__ void k_compose_segments(const dfa_result_t* seg_res, const uint16_t* 
         if (!err) s = maps[(size_t)i * stride + s];
     }
     dfa_result_t r;
-    r.final_state = err ? 0u : s;
+    r.final_state = final_of(err, s);
     r.accept = err ? 0 : accept[s];
     r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
     r.status = status_of(err);

@@ -38,7 +38,7 @@ def main():
         (gen.random_dfa(2, 5, 3, missing=0.2, byte_to_symbol=m3),
          (gen.uniform_bytes(3, 300_000) % 3).astype(np.uint8),
          [{}, {"num_chunks": 17}, {"lookahead": 0}, {"lookahead": 3}, {"boundary_window": 64}]),
-        (gen.random_dfa(4, 300, 64, num_finals=30, missing=0.02), gen.uniform_bytes(5, 2 << 20),
+        (gen.random_dfa(4, 300, 256, num_finals=30, missing=0.02), gen.uniform_bytes(5, 2 << 20),
          [{}, {"num_chunks": 3000}, {"lookahead": 2}]),
         (gen.regex_dfa(2), gen.zipf_text(2, 16 << 20),
          [{}, {"lookahead": 2}, {"lookahead": 4}, {"lookahead": 0}, {"boundary_window": 256},
@@ -51,6 +51,7 @@ def main():
     ]
     for spec, data, kws in cases:
         d = dm.Dfa.from_spec(spec)
+        print("case", spec.name, len(data), flush=True)
         for kw in kws:
             check(d, spec, data, **kw)
             check(d, spec, data[: len(data) // 3 + 7], **kw)

@@ -131,3 +131,24 @@ def test_large_dfa_in_a_batch_and_async(dm):
     torch.cuda.synchronize()
     (fs, acc, st), = dm.results_from(out)
     assert (st, fs, acc) == _expect(big, xs[4])
+
+
+def test_multipass_after_other_kernels(dm):
+    """Multi-pass composition marks finished map entries in shared memory;
+    those marks must start cleared in every launch whatever earlier kernels
+    left in shared memory.  Launches with large shared-memory use (the
+    regex-shaped DFA's table and stage buffers) alternate with multi-pass
+    launches of a 20000-state DFA whose CTAs hold several chunks each."""
+    import torch
+    big = gen.class_dfa(1020, 20000, 20, 0.2, 0.9, 200, "protein")
+    data = gen.protein_text(9, 300_000)
+    want = _expect(big, data)
+    db = dm.Dfa.from_spec(big)
+    w = gen.regex_workload(2, 32 << 20)
+    dr = dm.Dfa.from_spec(w.spec)
+    dev_r = torch.from_numpy(w.data).cuda()
+    want_r = _expect(w.spec, w.data)
+    for i in range(4):
+        assert dr.match(dev_r) == want_r
+        assert db.match(data) == want, i
+        assert db.match(data, num_chunks=585 + 7 * i) == want, i
