@@ -861,6 +861,27 @@ def main():
                          "ratio with the chunks' actual sets; the roof time is lookups / "
                          "(SMs x 32 x clock)",
                 "legs": mv}
+            # several DFAs on one input (Sec. 5: one symbol-index input run by
+            # several DFAs): one batched launch against one launch per DFA
+            if args.workload == "regex":
+                import gen
+                specs = [w.spec] + [sp for sp in gen.batch_dfas(21, 16)
+                                    if sp.byte_to_symbol is None][:7]
+                many = [dm.Dfa.from_spec(sp) for sp in specs]
+                n1 = min(n, 256 << 20)
+                bl1, res1, resp1 = batched_leg(dm, torch, many, [dev[:n1]] * len(many), reps=5)
+                exp1, t1s, thr1 = oracle_answers_all_cores(specs, list(range(len(specs))),
+                                                           [w.data[:n1]] * len(specs))
+                assert [_as_answer(r) for r in res1] == exp1 == [_as_answer(r) for r in resp1], \
+                    "several-DFA answers differ from the oracle"
+                bl1.update(workload="%d DFAs (regex512 and %d byte DFAs of the batched mix, |Q| %s) "
+                                    "on the first %d MiB of the input"
+                                    % (len(specs), len(specs) - 1,
+                                       sorted(sp.num_states for sp in specs), n1 >> 20),
+                           oracle_match="all %d tests" % len(specs))
+                line["several_dfas_one_input"] = bl1
+                for x in many:
+                    x.close()
             # Sec. 4.2 placement (opt-in; not the contracted method)
             if bw == 0:
                 pl = {}

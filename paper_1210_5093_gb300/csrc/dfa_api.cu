@@ -381,10 +381,13 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     DevDfa x = launch_desc(d, slot);
     const uint32_t tcap = x.placement == kSmem ? smem_table_bytes(x) : 0u;
-    // byte-row DFAs take the kernel variant with the larger register budget:
-    // their chains are latency-bound (few chains per SM), and the rows loaded
-    // ahead of the chains need registers
-    s->kmax = x.nib ? std::max(x.K, 8u) : x.K;
+    // The kernel variant with the larger register budget (64 per thread, two
+    // CTAs per SM) serves K <= 8; launches aiming for two CTAs per SM take it
+    // for K <= 4 too (the three-CTA variant's 40 registers spill), and so do
+    // byte-row DFAs, whose chains are latency-bound and whose rows loaded
+    // ahead of the chains need registers.
+    const uint32_t want_ctas = d->tuning_for(slot).ctas_per_sm;
+    s->kmax = (x.nib || match_target_ctas(x.K, want_ctas) <= 2) ? std::max(x.K, 8u) : x.K;
     uint32_t stage = 0;
     s->smem = match_smem_bytes(tcap, s->kmax, x.vcap, stage_esz(x.stage_fmt), &stage,
                                match_target_ctas(s->kmax, d->tuning_for(slot).ctas_per_sm));
