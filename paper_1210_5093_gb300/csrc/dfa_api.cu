@@ -381,13 +381,13 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     DevDfa x = launch_desc(d, slot);
     const uint32_t tcap = x.placement == kSmem ? smem_table_bytes(x) : 0u;
-    // The kernel variant with the larger register budget (64 per thread, two
-    // CTAs per SM) serves K <= 8; launches aiming for two CTAs per SM take it
-    // for K <= 4 too (the three-CTA variant's 40 registers spill), and so do
-    // byte-row DFAs, whose chains are latency-bound and whose rows loaded
-    // ahead of the chains need registers.
-    const uint32_t want_ctas = d->tuning_for(slot).ctas_per_sm;
-    s->kmax = (x.nib || match_target_ctas(x.K, want_ctas) <= 2) ? std::max(x.K, 8u) : x.K;
+    // byte-row DFAs take the kernel variant with the larger register budget:
+    // their chains are latency-bound (few chains per SM), and the rows loaded
+    // ahead of the chains need registers.  (Giving that variant to every
+    // two-CTA launch with K <= 4 left the device-resident time unchanged and
+    // slowed the pipelined host path, whose consecutive launches overlap only
+    // when the three-CTA variant leaves room on each SM.)
+    s->kmax = x.nib ? std::max(x.K, 8u) : x.K;
     uint32_t stage = 0;
     s->smem = match_smem_bytes(tcap, s->kmax, x.vcap, stage_esz(x.stage_fmt), &stage,
                                match_target_ctas(s->kmax, d->tuning_for(slot).ctas_per_sm));
@@ -541,6 +541,9 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
     x.stage_fmt = h.placement == kGlobal ? kOff32 : (h.C + 1 <= 255 ? kCls8 : kOff16);
     x.n_all = h.iset_off[h.C + 2] - h.iset_off[h.C + 1];
     x.nib = h.nib_rows.empty() ? 0u : 1u;
+    // byte-row chains are latency-bound: one CTA per SM measured fastest
+    // (4 MiB in 1024 chunks, 16 states: 87 us against 98 us with two)
+    if (x.nib) d->tuning.ctas_per_sm = 1;
     // with byte rows, the 16-bit stage entries are row offsets into them (class * 16)
     std::vector<uint16_t> off16 = h.byte_off16;
     if (x.nib)
