@@ -818,6 +818,22 @@ def main():
                                     "sample": "the whole %d MiB input, one run of Algorithm 1 (C, "
                                               "one core); the same run checks the answers"
                                               % (n >> 20)}
+        if world == 1:
+            # measured lookup roofs: the unit of work alone on this DFA's table
+            # (shared memory) and on a 256-class, 1288-state table read through L2
+            import gen
+            l2d = dm.Dfa.from_spec(gen.class_dfa(81, 1288, 256, 0.02, 0.3, 12, "byte"))
+            r_smem = dm.probe_lookup_rate(d, 4096, stream)
+            r_l2 = dm.probe_lookup_rate(l2d, 1024, stream)
+            l2d.close()
+            line["lookup_probe"] = {
+                "smem_glookup_s": round(r_smem / 1e9, 1),
+                "smem_vs_derived_peak": round(r_smem / lookup_peak, 4),
+                "l2_glookup_s": round(r_l2 / 1e9, 1),
+                "what": "dfa_probe_lookup_rate: 8 dependent chains per thread on the DFA's own "
+                        "table (%s table in shared memory) and on a 659 KB table read through "
+                        "L2 (256 classes x 1288 states), full-GPU launch, no staging" % w.name}
+            line["roofline"]["frac_of_probe"] = round(achieved / r_smem, 4)
         if not args.no_mix and args.workload in ("regex", "protein") and world == 1:
             tune = not args.tuning and not args.no_tune
             legs = {}

@@ -400,6 +400,21 @@ int dfa_batch_set_events(dfa_batch_t *batch, void *match_begin_event, void *matc
 int dfa_batch_num_kernels(const dfa_batch_t *batch, uint32_t *n);
 void dfa_batch_destroy(dfa_batch_t *batch);
 
+/*
+ * Measurement: the rate, in lookups per second, of the match kernel's unit of
+ * work - one dependent table lookup s <- T[row(class)][s] (Algorithm 3's inner
+ * step; Eq. 16 counts these) - on this DFA's own table and placement, with no
+ * staging, planning or composition: every thread of a full-GPU launch
+ * advances 8 independent chains for `steps` steps, all threads taking the
+ * same class per step (as one chunk's lanes do).  For a table in shared
+ * memory this probes the shared-memory lookup roof; for a table read through
+ * L2, the random-gather rate.  Best of three timed launches (CUDA events on
+ * `stream`), after a warm-up launch; synchronises the stream.  Tables with
+ * 1- or 2-byte entries.  Errors: DFA_EINVAL, DFA_ECUDA, DFA_ENOMEM,
+ * DFA_EHOSTONLY.
+ */
+int dfa_probe_lookup_rate(const dfa_t *dfa, uint32_t steps, void *stream, double *lookups_per_s);
+
 /* Human-readable text for a status code (static storage). */
 const char *dfa_strerror(int status);
 

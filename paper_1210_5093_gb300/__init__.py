@@ -101,6 +101,7 @@ SIGNATURES = {
     "dfa_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
     "dfa_match_noalloc": (_I, [_P, _P, _U64, _P, _P, _P]),
     "dfa_noalloc_scratch_bytes": (_U64, []),
+    "dfa_probe_lookup_rate": (_I, [_P, _U32, _P, _P]),
     "dfa_match_batch": (_I, [_U32, _P, _P, _P, _P, _P, _P]),
     "dfa_batch_prepare": (_I, [_U32, _P, _P, _P, _P, _P]),
     "dfa_batch_launch": (_I, [_P, _P, _P]),
@@ -391,6 +392,15 @@ class Dfa:
         rc = lib().dfa_match_noalloc(self._h, dev_data.data_ptr() if n else None, n,
                                      ctypes.byref(o), dev_out.data_ptr(), _stream_ptr(stream))
         _check(rc, "dfa_match_noalloc")
+
+
+def probe_lookup_rate(dfa: "Dfa", steps: int = 4096, stream=None) -> float:
+    """Lookups per second of one dependent table lookup on dfa's own table and
+    placement (dfa_probe_lookup_rate)."""
+    r = ctypes.c_double()
+    _check(lib().dfa_probe_lookup_rate(dfa.handle, steps, _stream_ptr(stream), ctypes.byref(r)),
+           "dfa_probe_lookup_rate")
+    return float(r.value)
 
 
 def noalloc_scratch_bytes() -> int:

@@ -19,7 +19,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 OUT_DEBUG = os.path.join(HERE, "libdfamatch_debug.so")
 BUILD_DIR_DEBUG = os.path.join(HERE, "_build_debug")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["dfa_kernels.cu", "dfa_api.cu", "dfa_server.cu", "dfa_noalloc.cu", "dfa_compile.cpp"]
+SOURCES = ["dfa_kernels.cu", "dfa_api.cu", "dfa_server.cu", "dfa_noalloc.cu", "dfa_probe.cu",
+           "dfa_compile.cpp"]
 
 
 def _nvcc() -> str:

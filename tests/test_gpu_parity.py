@@ -540,3 +540,19 @@ def test_smem_table_beyond_16bit_row_offsets(dm):
     for P in (0, 1, 7, 4000):
         for r in (0, 1, 3):
             _check(dm, d, spec, data, num_chunks=P, lookahead=r)
+
+
+def test_lookup_probe_rates(dm):
+    """The lookup-rate probe (the unit of work alone) runs on shared-memory and
+    L2-placed tables and gives rates in the range the hardware allows: the
+    shared-memory rate at most a little above SMs x 32 lanes x clock."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    d = dm.Dfa.from_spec(gen.regex_dfa(2))
+    r = dm.probe_lookup_rate(d, 2048)
+    peak = props.multi_processor_count * 32 * 2.07e9
+    assert 0.3 * peak < r < 1.1 * peak, (r, peak)
+    dl = dm.Dfa.from_spec(gen.class_dfa(81, 1288, 256, 0.02, 0.3, 12, "byte"))
+    assert dl.info().placement == 1
+    rl = dm.probe_lookup_rate(dl, 512)
+    assert 1e9 < rl < 1.1 * peak, rl
