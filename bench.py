@@ -75,6 +75,13 @@ def _workload(name: str, seed: int, nbytes: int = 0):
 
 def _cpu_model() -> str:
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 low = line.lower()
