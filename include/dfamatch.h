@@ -250,7 +250,9 @@ int dfa_partition(uint64_t n, uint32_t P, uint32_t m, uint64_t *starts);
  * (detected with cudaPointerGetAttributes).  Host input of at least two
  * first-segment lengths (dfa_tuning_t.host_segment_bytes) is copied and
  * matched as a pipeline when opts sets neither num_chunks nor multiplicity
- * (segments double in length up to an eighth of the string):
+ * (segments double in length up to an eighth of the string, or up to a
+ * quarter when the DFA's autotuned device rate is below 150 GB/s, so that the
+ * copies stay ahead of the matching and fewer launches are needed):
  * each segment is copied on a library-owned copy stream and matched, once its
  * copy has landed, as its own launch on one of two library-owned compute
  * streams (so consecutive launches overlap).  Every segment after the first

@@ -300,6 +300,9 @@ struct dfa_s {
     // its own record the base record
     dfa_tuning_t tuning_r[dfam::kTuningSlots]{};
     bool has_tuning_r[dfam::kTuningSlots]{};
+    // device-only rate (GB/s) the autotuner measured for each slot's chosen
+    // tuning on its sample (0: not autotuned); sizes the host pipeline's segments
+    double tuned_gbs[dfam::kTuningSlots]{};
     const dfa_tuning_t& tuning_for(uint32_t slot) const {
         if (slot < dfam::kTuningSlots && has_tuning_r[slot]) return tuning_r[slot];
         if (slot > dfam::kMaxLookahead && slot < dfam::kTuningSlots)
