@@ -986,73 +986,6 @@ __device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, ui
     }
 }
 
-// Asynchronous staging of the 8-bit class stream.  A chunk's bytes are copied
-// in 16-byte blocks aligned in global memory (cp.async, no registers), so
-// chunk position p sits at stage offset p + a, a = the chunk start's offset
-// within its block (chunk_align); the a bytes before the chunk and the bytes
-// after it become the identity class, so the chains step over them unchanged.
-// Every copied block holds at least one byte of the chunk, so it never leaves
-// the pages the string occupies.  The next segment's blocks are copied while
-// the chains run on the current one; each thread then converts, in place, the
-// blocks it copied itself (its own cp.async wait orders them), and the
-// segment's barrier publishes them.
-__device__ __forceinline__ uint32_t chunk_align(const ChunkMeta& m) {
-    return (uint32_t)((uintptr_t)m.ptr & 15u);
-}
-__device__ __forceinline__ const uint8_t* chunk_block(const ChunkMeta& m, int seg, int S, int q) {
-    return m.ptr - chunk_align(m) + (size_t)seg * (size_t)S + 16u * (uint32_t)q;
-}
-
-__device__ void copy_raw_cls8(const ChunkMeta* meta, int nch, int S, int seg, uint32_t stage) {
-    const int groups = S / 16;
-    const int items = nch * groups;
-    for (int it = threadIdx.x; it < items; it += kThreads) {
-        const int ci = it / groups, q = it - ci * groups;
-        const ChunkMeta& m = meta[ci];
-        const uint8_t* g = chunk_block(m, seg, S, q);
-        if (g < m.ptr + m.len)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                         :: "r"(stage + (uint32_t)(ci * S + 16 * q)), "l"(g) : "memory");
-    }
-}
-
-__device__ void convert_cls8(const ChunkMeta* meta, int nch, int S, int seg, uint32_t stage,
-                             uint32_t boff, uint32_t id_off, uint32_t* test_err) {
-    const int groups = S / 16;
-    const int items = nch * groups;
-    for (int it = threadIdx.x; it < items; it += kThreads) {
-        const int ci = it / groups, q = it - ci * groups;
-        const ChunkMeta& m = meta[ci];
-        const uint32_t dst = stage + (uint32_t)(ci * S + 16 * q);
-        const bool copied = chunk_block(m, seg, S, q) < m.ptr + m.len;
-        const uint4 raw = copied ? lds_v4(dst) : make_uint4(0, 0, 0, 0);
-        const uint32_t words[4] = {raw.x, raw.y, raw.z, raw.w};
-        // chunk position of the block's first byte (negative before the chunk)
-        const int64_t p0 = (int64_t)seg * S + 16 * q - (int64_t)chunk_align(m);
-        bool bad = false, oob = false;
-        uint32_t w[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            uint32_t word = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t p = p0 + 4 * i + k;
-                const bool valid = p >= 0 && p < (int64_t)m.len;
-                word |= stage_entry<kCls8>((words[i] >> (8 * k)) & 0xFFu, valid, boff, id_off, bad, oob)
-                        << (8 * k);
-            }
-            w[i] = word;
-        }
-        sts_v4(dst, make_uint4(w[0], w[1], w[2], w[3]));
-        if (bad) atomicOr(test_err + m.test, 1u);
-        if (oob) atomicOr(test_err + m.test, 2u);
-    }
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 template <int K>
 __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uint32_t maxlen,
                             const TileCtx& c, uint32_t boff, uint32_t* test_err,
@@ -1082,34 +1015,10 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
     const uint32_t id_off = fmt == kCls8 ? d.C : d.C * rowbytes;  // the identity row
     const int nseg = (int)((maxlen + c.S - 1) / c.S);
     const uint32_t esz = stage_esz(fmt);
-    if (fmt == kCls8) {
-        // class stream: the next segment is copied while the chains run
-        copy_raw_cls8(meta, nch, c.S, 0, c.stage0);
-        cp_async_wait_all();
-        convert_cls8(meta, nch, c.S, 0, c.stage0, boff, id_off, test_err);
-        __syncthreads();
-        for (int seg = 0; seg < nseg; ++seg) {
-            const uint32_t cur = c.stage0 + (uint32_t)(seg & 1) * c.stage_bytes;
-            const uint32_t nxt = c.stage0 + (uint32_t)((seg + 1) & 1) * c.stage_bytes;
-            if (seg + 1 < nseg) copy_raw_cls8(meta, nch, c.S, seg + 1, nxt);
-            if (c.active) {
-                const uint32_t my = cur + (uint32_t)(c.ci * c.S);
-                if (nib) run_nib<K, true>(s, c.tb, my, c.S);
-                else if (d.sb == 1) run_smem8<K, 1>(s, c.tb, rowbytes, my, c.S);
-                else run_smem8<K, 2>(s, c.tb, rowbytes, my, c.S);
-            }
-            if (seg + 1 < nseg) {
-                cp_async_wait_all();
-                convert_cls8(meta, nch, c.S, seg + 1, nxt, boff, id_off, test_err);
-            }
-            // every thread has left the current buffer and converted its blocks
-            // of the next one
-            __syncthreads();
-        }
-    } else
     for (int seg = 0; seg < nseg; ++seg) {
         const uint32_t stage = c.stage0 + (uint32_t)(seg & 1) * c.stage_bytes;
-        if (fmt == kOff16) stage_segment<kOff16>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
+        if (fmt == kCls8) stage_segment<kCls8>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
+        else if (fmt == kOff16) stage_segment<kOff16>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
         else stage_segment<kOff32>(meta, nch, c.S, seg, stage, boff, id_off, test_err);
         __syncthreads();
         if (c.active) {
@@ -1437,9 +1346,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             m.lo_slack = (uint8_t)(avail < 255 ? avail : 255);
             m.hi_slack = (uint8_t)(tt.n - en < 255 ? tt.n - en : 255);
             meta[i] = m;
-            // the class stream is staged from the chunk start's 16-byte block,
-            // so its chains take that block's leading bytes as identity steps too
-            atomicMax(misc + M_MAXLEN, m.len + (d.stage_fmt == kCls8 ? chunk_align(m) : 0u));
+            atomicMax(misc + M_MAXLEN, m.len);
         }
         __syncthreads();
         const uint32_t maxlen = misc[M_MAXLEN];
