@@ -171,7 +171,7 @@ bool dfa_server_s::reap() {
 // kSlotPinned pinned host bytes) and doubled when a batch needs more: each
 // regrowth frees memory, which waits for the whole device and stalls every
 // batch in flight.
-constexpr uint64_t kSlotWs = 32ull << 20, kSlotPinned = 1ull << 20;
+constexpr uint64_t kSlotWs = 64ull << 20, kSlotPinned = 1ull << 20;
 
 static int grow(uint8_t** p, uint64_t* cap, uint64_t need, bool pinned) {
     if (*cap >= need) return DFA_OK;
