@@ -34,6 +34,7 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import gc
 import hashlib
 import json
 import os
@@ -416,6 +417,7 @@ def serving_leg(dm, torch, dfas, pinned, rate_gbs: float, seconds: float = 2.0,
     picks = gen.below(gen.draws(gen.key(seed, 98), n), len(pinned)).astype(np.int64)
     srv = dm.Server(budget, max_inflight=inflight, boundary_window=window)
     clk = Clocks(torch.cuda.current_device()).start()
+    gc.disable()   # arrivals keep their schedule: no interpreter collection meanwhile
     t0 = time.perf_counter()
     t_next = t0
     sub = {}
@@ -425,6 +427,7 @@ def serving_leg(dm, torch, dfas, pinned, rate_gbs: float, seconds: float = 2.0,
             pass
         sub[srv.submit(dfas[picks[i]], pinned[picks[i]])] = int(picks[i])
     srv.drain(600.0)
+    gc.enable()
     clocks = clk.stop()
     done = srv.poll(n + 16)
     st = srv.stats()
@@ -749,10 +752,12 @@ def main():
     torch.cuda.synchronize()
     e2e_res = set()
     e2e_calls = []
+    gc.disable()   # no interpreter collection inside a timed call
     for _ in range(e2e_steps):
         te = time.perf_counter()
         e2e_res.add(d.match(pinned, boundary_window=bw))
         e2e_calls.append(time.perf_counter() - te)
+    gc.enable()
     e2e_s = statistics.median(e2e_calls)   # per call: copies, kernels and the result read
     # context: this box's plain host-to-device copy rate (the pipelined host
     # path cannot run faster than the copies that feed it)
