@@ -152,3 +152,35 @@ def test_multipass_after_other_kernels(dm):
         assert dr.match(dev_r) == want_r
         assert db.match(data) == want, i
         assert db.match(data, num_chunks=585 + 7 * i) == want, i
+
+
+def test_large_dfa_placement_server_and_noalloc(dm):
+    """A 20000-state DFA with Sec. 4.2 placement (the window search reads 16-bit
+    set sizes), through the serving loop next to a small DFA, and through the
+    allocation-free entry point, whose fixed scratch cannot hold the running maps
+    of such sets (DFA_ENOSPACE, nothing launched)."""
+    import torch
+    big = _large(20000, 91)
+    db = dm.Dfa.from_spec(big)
+    data = gen.protein_text(92, 400_000)
+    for w in (16, 256):
+        _check(dm, db, big, data, boundary_window=w)
+    small = gen.regex_dfa(2)
+    ds = dm.Dfa.from_spec(small)
+    xs = [gen.protein_text(93 + i, 20_000 * (i + 1)) if i % 2 == 0 else gen.zipf_text(93 + i, 50_000)
+          for i in range(6)]
+    srv = dm.Server(1 << 30, max_inflight=3)
+    tickets = {srv.submit(db if i % 2 == 0 else ds, x): i for i, x in enumerate(xs)}
+    srv.drain(120.0)
+    done = srv.poll(64)
+    srv.close()
+    assert len(done) == len(xs)
+    for c in done:
+        i = tickets[c[0]]
+        st, fs, acc = _expect(big if i % 2 == 0 else small, xs[i])
+        assert (c[3], c[1], c[2]) == (st, fs, acc), i
+    dev = torch.from_numpy(data).cuda()
+    out = torch.zeros(12, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dm.DfaError) as e:
+        db.match_noalloc(dev, out)
+    assert e.value.status == dm.ENOSPACE
