@@ -388,8 +388,11 @@ def test_many_dfas_on_one_input(dm):
     representation allows one input to be run by several DFAs, Sec. 5): each
     result equals that DFA run alone and the oracle."""
     import torch
-    specs = [s for s in gen.batch_dfas(21, 12) if s.byte_to_symbol is None]
-    specs.append(gen.regex_dfa(2))
+    # 8 DFAs, as the bench's several-DFA leg: the regex-shaped DFA, 6 byte DFAs of
+    # the batched mix and one 256-class table read through L2
+    specs = [gen.regex_dfa(2)] + [s for s in gen.batch_dfas(21, 16) if s.byte_to_symbol is None][:6]
+    specs.append(gen.class_dfa(81, 1288, 256, 0.02, 0.3, 12, "byte"))
+    assert len(specs) == 8
     dfas = [dm.Dfa.from_spec(s) for s in specs]
     x = gen.zipf_text(22, 3 << 20)
     dev = torch.from_numpy(x).cuda()
