@@ -809,7 +809,12 @@ __device__ __forceinline__ void run_global(uint32_t (&s)[K], const uint8_t* tbl,
 __device__ __forceinline__ uint32_t nib_step(const uint4& row, uint32_t code) {
     const uint32_t lo = __byte_perm(row.x, row.y, code);
     const uint32_t hi = __byte_perm(row.z, row.w, code);
-    return (code & 0x80u) ? hi : lo;
+    // all ones when bit 7 of the code is set: a permute in sign-replicating mode
+    // (selector nibbles 0x8: byte 0's sign bit in every byte), issued beside the
+    // two row permutes, so no predicate sits on the chain's dependent path
+    uint32_t half;
+    asm("prmt.b32 %0, %1, 0, 0x8888;" : "=r"(half) : "r"(code));
+    return (lo & ~half) | (hi & half);
 }
 
 // Advance K chains over one staged segment of S positions with byte rows in
