@@ -819,42 +819,51 @@ __device__ __forceinline__ uint32_t nib_step(const uint4& row, uint32_t code) {
 
 // Advance K chains over one staged segment of S positions with byte rows in
 // shared memory at tb.  The stage holds 8-bit class indices (CLS8; row =
-// class * 16) or 16-bit row byte offsets.  The rows of the next four steps
-// depend only on the input, so they are loaded while the chains take the
-// current four.
-template <int K, bool CLS8>
+// class * 16) or 16-bit row byte offsets.  The rows depend only on the
+// input, so they are loaded two groups of four steps ahead of the chains that
+// use them (the stage entry, then the row: two dependent loads per step).
+template <int K, bool CLS8, bool DEEP>
 __device__ __forceinline__ void run_nib(uint32_t (&s)[K], uint32_t tb, uint32_t stage_addr, int S) {
-    constexpr int kPer = CLS8 ? 16 : 8;  // stage entries per 16-byte read
-    auto row_addr = [&](const uint4& w, int i) -> uint32_t {
-        const uint32_t word = i / (4 / (CLS8 ? 1 : 2)) == 0 ? w.x
-                            : (i / (4 / (CLS8 ? 1 : 2)) == 1 ? w.y
-                            : (i / (4 / (CLS8 ? 1 : 2)) == 2 ? w.z : w.w));
-        return CLS8 ? tb + ((word >> (8 * (i & 3))) & 0xFFu) * 16u
-                    : tb + ((word >> (16 * (i & 1))) & 0xFFFFu);
+    auto row_addr = [&](int j) -> uint32_t {
+        return CLS8 ? tb + lds_u8(stage_addr + (uint32_t)j) * 16u
+                    : tb + lds_u16(stage_addr + 2u * (uint32_t)j);
     };
-    uint4 w = lds_v4(stage_addr);
-    uint4 cur[4], nxt[4];
+    if (K > 2 || !DEEP) {
+        // more chains per thread hide the loads themselves (and the kernel
+        // variant with 40 registers has no room for more rows): one group ahead
+        uint4 cur[4], nxt[4];
 #pragma unroll
-    for (int g = 0; g < 4; ++g) cur[g] = lds_v4(row_addr(w, g));
-    for (int j = 0; j < S; j += kPer) {
+        for (int g = 0; g < 4; ++g) cur[g] = lds_v4(row_addr(g));
+        for (int j = 0; j < S; j += 4) {
+            const int jn = j + 4 < S ? j + 4 : j;
 #pragma unroll
-        for (int q = 0; q < kPer; q += 4) {
-            // rows of steps j+q+4 .. j+q+7 (the next stage read at the end of
-            // this read's entries; the segment's last group reloads its own)
-            const bool last_of_read = q + 4 == kPer;
-            const bool last = last_of_read && j + kPer >= S;
-            uint4 wn = w;
-            if (last_of_read && !last) wn = lds_v4(stage_addr + (uint32_t)(j + kPer) * (CLS8 ? 1u : 2u));
-            const int qn = last ? q : (last_of_read ? 0 : q + 4);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) nxt[g] = lds_v4(row_addr(last_of_read && !last ? wn : w, qn + g));
+            for (int g = 0; g < 4; ++g) nxt[g] = lds_v4(row_addr(jn + g));
 #pragma unroll
             for (int g = 0; g < 4; ++g)
 #pragma unroll
                 for (int u = 0; u < K; ++u) s[u] = nib_step(cur[g], s[u]);
 #pragma unroll
             for (int g = 0; g < 4; ++g) cur[g] = nxt[g];
-            w = wn;
+        }
+        return;
+    }
+    uint4 r0[4], r1[4], r2[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) r0[g] = lds_v4(row_addr(g));
+#pragma unroll
+    for (int g = 0; g < 4; ++g) r1[g] = lds_v4(row_addr(4 + g));
+    for (int j = 0; j < S; j += 4) {
+        const int jn = j + 8 < S ? j + 8 : S - 4;  // past the end: reload the last group
+#pragma unroll
+        for (int g = 0; g < 4; ++g) r2[g] = lds_v4(row_addr(jn + g));
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+            for (int u = 0; u < K; ++u) s[u] = nib_step(r0[g], s[u]);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            r0[g] = r1[g];
+            r1[g] = r2[g];
         }
     }
 }
@@ -991,7 +1000,8 @@ __device__ void stage_segment(const ChunkMeta* meta, int nch, int S, int seg, ui
     }
 }
 
-template <int K>
+// DEEP: the kernel variant has the registers to load byte rows two groups ahead.
+template <int K, bool DEEP>
 __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uint32_t maxlen,
                             const TileCtx& c, uint32_t boff, uint32_t* test_err,
                             uint16_t* dbg_maps, uint32_t dbg_stride, uint32_t g0) {
@@ -1029,8 +1039,8 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
         if (c.active) {
             const uint32_t my = stage + (uint32_t)(c.ci * c.S) * esz;
             if (nib) {
-                if (fmt == kCls8) run_nib<K, true>(s, c.tb, my, c.S);
-                else run_nib<K, false>(s, c.tb, my, c.S);
+                if (fmt == kCls8) run_nib<K, true, DEEP>(s, c.tb, my, c.S);
+                else run_nib<K, false, DEEP>(s, c.tb, my, c.S);
             } else if (fmt == kCls8) {
                 if (d.sb == 1) run_smem8<K, 1>(s, c.tb, rowbytes, my, c.S);
                 else run_smem8<K, 2>(s, c.tb, rowbytes, my, c.S);
@@ -1403,13 +1413,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
         const uint32_t boff = sa(sm + L.boff);
         uint16_t* dbg = lp.dbg_maps;
         const uint32_t dst_ = lp.qe_max;
-        if (d.K == 1) tile_chains<1>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
-        else if (d.K == 2) tile_chains<2>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        constexpr bool kDeep = KMAX >= 8;
+        if (d.K == 1) tile_chains<1, kDeep>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        else if (d.K == 2) tile_chains<2, kDeep>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         else if (KMAX >= 8 && d.K == 4)
-            tile_chains<(KMAX >= 8 ? 4 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+            tile_chains<(KMAX >= 8 ? 4 : 2), kDeep>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         else if (KMAX >= 16 && d.K == 8)
-            tile_chains<(KMAX >= 16 ? 8 : 2)>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
-        else tile_chains<KMAX>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+            tile_chains<(KMAX >= 16 ? 8 : 2), kDeep>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
+        else tile_chains<KMAX, kDeep>(d, meta, nch, maxlen, c, boff, lp.test_err, dbg, dst_, gA);
         __syncthreads();
 
         if (passes > 1) {
