@@ -19,6 +19,7 @@ uint32_t match_smem_bytes(uint32_t table_cap, uint32_t kmax, uint32_t vcap, uint
 uint32_t match_target_ctas(uint32_t kmax, uint32_t want);
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid);
 uint32_t launch_kernel_count(uint32_t ptot, uint32_t grid, bool dyn, bool bnd);
+uint32_t device_sms();
 int launch_plan(const LaunchPlan& lp, uint32_t kmax, uint32_t smem, cudaStream_t st,
                 uint32_t* kernels, void* ev_begin = nullptr, void* ev_end = nullptr,
                 bool plan_only = false);
@@ -219,6 +220,9 @@ int prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs
     }
     for (const dfa_t* d : uniq) {
         DevDfa x = launch_desc(d, slot);
+        // batched launches are bound by the shared-memory pipe, where a byte
+        // row (a 16-byte read per step) costs more than a table lookup
+        x.nib = 0;
         if (uniq.size() > 1) {
             // One launch has one kernel variant and one shared-memory layout,
             // sized for its largest K and largest shared-memory table.  In a
@@ -380,17 +384,31 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     const uint32_t lookahead = opts_lookahead(opts), slot = opts_slot(opts);
     const uint32_t m = (opts && opts->multiplicity) ? opts->multiplicity : 1u;
     DevDfa x = launch_desc(d, slot);
+    const dfa_tuning_t& tu = d->tuning_for(slot);
+    // Byte rows serve latency-bound launches: few chains in all, at most 128 per
+    // SM (one warp per scheduler).  With more chains the launch is bound by the
+    // shared-memory pipe, where a row read per step (16 bytes) costs more than a
+    // table lookup, so the class-major table is used.
+    bool nib = false;
+    if (x.nib) {
+        const uint32_t sms = device_sms();
+        const uint64_t P0 = plan_chunks(d, len, std::max(sms, 1u) * 2, opts, false, 0);
+        nib = sms && P0 * std::max(x.imax, 1u) <= (uint64_t)sms * 128u;
+        x.nib = nib ? 1u : 0u;
+    }
     const uint32_t tcap = x.placement == kSmem ? smem_table_bytes(x) : 0u;
-    // byte-row DFAs take the kernel variant with the larger register budget:
-    // their chains are latency-bound (few chains per SM), and the rows loaded
-    // ahead of the chains need registers.  (Giving that variant to every
-    // two-CTA launch with K <= 4 left the device-resident time unchanged and
-    // slowed the pipelined host path, whose consecutive launches overlap only
-    // when the three-CTA variant leaves room on each SM.)
-    s->kmax = x.nib ? std::max(x.K, 8u) : x.K;
+    // byte-row launches take the kernel variant with the larger register
+    // budget, for the rows loaded ahead of the chains, and by default one CTA
+    // per SM (4 MiB in 1024 chunks, 16 states: 87 us against 98 us with two).
+    // (Giving that variant to every two-CTA launch with K <= 4 left the
+    // device-resident time unchanged and slowed the pipelined host path, whose
+    // consecutive launches overlap only when the three-CTA variant leaves room
+    // on each SM.)
+    s->kmax = nib ? std::max(x.K, 8u) : x.K;
+    const uint32_t want_ctas = tu.ctas_per_sm ? tu.ctas_per_sm : (nib ? 1u : 0u);
     uint32_t stage = 0;
     s->smem = match_smem_bytes(tcap, s->kmax, x.vcap, stage_esz(x.stage_fmt), &stage,
-                               match_target_ctas(s->kmax, d->tuning_for(slot).ctas_per_sm));
+                               match_target_ctas(s->kmax, want_ctas));
     uint32_t grid = 0;
     int rc = match_grid(s->smem, s->kmax, &grid);
     if (rc != DFA_OK) return rc;
@@ -415,6 +433,7 @@ int plan_single(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, Sing
     lp.stage_bytes = stage;
     lp.qe_max = x.qe;
     lp.dyn = lookahead >= 2 ? 1u : 0u;
+    lp.no_nib = (d->dev.nib && !nib) ? 1u : 0u;
     lp.dfas = d->dev_desc_for(slot);
     lp.tests = nullptr;
     lp.groups = nullptr;
@@ -541,14 +560,10 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
     x.stage_fmt = h.placement == kGlobal ? kOff32 : (h.C + 1 <= 255 ? kCls8 : kOff16);
     x.n_all = h.iset_off[h.C + 2] - h.iset_off[h.C + 1];
     x.nib = h.nib_rows.empty() ? 0u : 1u;
-    // byte-row chains are latency-bound: one CTA per SM measured fastest
-    // (4 MiB in 1024 chunks, 16 states: 87 us against 98 us with two)
-    if (x.nib) d->tuning.ctas_per_sm = 1;
-    // with byte rows, the 16-bit stage entries are row offsets into them (class * 16)
-    std::vector<uint16_t> off16 = h.byte_off16;
-    if (x.nib)
-        for (int b = 0; b < 256; ++b)
-            off16[b] = h.byte_class[b] == kNone16 ? kNone16 : (uint16_t)(h.byte_class[b] * 16u);
+    // with byte rows, 16-bit stage entries are row offsets into them (class * 16)
+    std::vector<uint16_t> nib16(256, kNone16);
+    for (int b = 0; b < 256; ++b)
+        if (h.byte_class[b] != kNone16) nib16[b] = (uint16_t)(h.byte_class[b] * 16u);
     // planning lookup: one load gives a lookahead byte's class and |I_class|
     uint32_t byte_plan[256];
     for (int b = 0; b < 256; ++b) {
@@ -568,7 +583,7 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         const uint64_t o_ioff = take(4 * h.iset_off.size()), o_iset = take(2 * h.iset.size());
         const uint64_t o_pos = take(2 * h.pos.size()), o_acc = take(h.accept.size());
         const uint64_t o_exc = take(h.excluded.size()), o_bp = take(sizeof byte_plan);
-        const uint64_t o_nib = take(h.nib_rows.size());
+        const uint64_t o_nib = take(h.nib_rows.size()), o_n16 = take(x.nib ? 512 : 0);
         uint8_t* blk = nullptr;
         if (cudaMalloc(&blk, o) != cudaSuccess) {
             cudaGetLastError();
@@ -588,10 +603,11 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
         x.excluded = blk + o_exc;
         x.byte_plan = reinterpret_cast<const uint32_t*>(blk + o_bp);
         x.nib_rows = x.nib ? blk + o_nib : nullptr;
+        x.nib_off16 = x.nib ? reinterpret_cast<const uint16_t*>(blk + o_n16) : nullptr;
         d->dev_desc = reinterpret_cast<DevDfa*>(blk + o_desc);
         bool ok = upload_descs(d) == DFA_OK &&
                   cudaMemcpy(blk + o_table, h.table.data(), h.table.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(blk + o_b16, off16.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(blk + o_b16, h.byte_off16.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_b32, h.byte_off32.data(), 1024, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_bc, h.byte_class.data(), 512, cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_ioff, h.iset_off.data(), 4 * h.iset_off.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -600,8 +616,10 @@ static int create_common(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t 
                   cudaMemcpy(blk + o_acc, h.accept.data(), h.accept.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_exc, h.excluded.data(), h.excluded.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                   cudaMemcpy(blk + o_bp, byte_plan, sizeof byte_plan, cudaMemcpyHostToDevice) == cudaSuccess &&
-                  (!x.nib || cudaMemcpy(blk + o_nib, h.nib_rows.data(), h.nib_rows.size(),
-                                        cudaMemcpyHostToDevice) == cudaSuccess);
+                  (!x.nib || (cudaMemcpy(blk + o_nib, h.nib_rows.data(), h.nib_rows.size(),
+                                         cudaMemcpyHostToDevice) == cudaSuccess &&
+                              cudaMemcpy(blk + o_n16, nib16.data(), 512, cudaMemcpyHostToDevice) ==
+                                  cudaSuccess));
         if (!ok) {
             cudaFree(blk);
             delete d;

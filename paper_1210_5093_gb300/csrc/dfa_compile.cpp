@@ -172,10 +172,11 @@ int compile_dfa(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const
     // further); a chunk with more chains than a tile holds runs its chains in
     // several passes over the chunk (large DFAs)
     while ((std::max(h.imax, 1u) + h.K - 1) / h.K > (uint32_t)kThreads / 2 && h.K < 16) h.K *= 2;
-    // byte-row chains are latency-bound (a step is a short dependent chain of
-    // permutes, not a load that other chains can hide): one chain per thread
-    if (!h.nib_rows.empty()) h.K = 1;
     h.K0 = h.K;
+    // single tests of byte-row DFAs are latency-bound when they use the rows (a
+    // step is a short dependent chain of permutes that other chains cannot
+    // hide): one chain per thread.  Batched launches keep K0.
+    if (!h.nib_rows.empty()) h.K = 1;
     *out = std::move(h);
     return DFA_OK;
 }

@@ -71,8 +71,9 @@ struct DevDfa {
     uint32_t vcap;               // largest set size (incl. start set) = capacity of a state map
     uint32_t stage_fmt;          // StageFmt of the staged input stream
     uint32_t n_all;              // |Q| minus the excluded states: the set Algorithm 2 matches
-    uint32_t nib;                // 1: at most 16 live states, matched from byte rows (nib_rows)
+    uint32_t nib;                // 1: at most 16 live states, byte rows available (nib_rows)
     const uint8_t* nib_rows;     // nib: (C+1) rows of 16 bytes, byte s = nib_code(delta(s, c))
+    const uint16_t* nib_off16;   // nib: [256] byte -> byte-row offset class * 16 (kNone16: not in Sigma)
 };
 
 // Byte rows for DFAs whose chains only ever visit 16 states or fewer (every
@@ -192,6 +193,7 @@ struct LaunchPlan {
     uint16_t* sets;             // lookahead-set arena (r >= 2), see DevGroup
     uint32_t* set_size;         // [ptot] |I| of each chunk computed by k_lookahead
     uint32_t dyn;               // 1 if some test uses r >= 2 lookahead symbols
+    uint32_t no_nib;            // 1: match byte-row DFAs from their class-major tables instead
     uint32_t bnd;               // 1 if some test places its chunk starts (Sec. 4.2)
     uint64_t* starts;           // [ptot] start of every chunk k >= 1 of a placing test
     uint16_t* dbg_maps;         // optional [ptot * qe_max]: chunk maps L_k (identity pre-filled)

@@ -1305,6 +1305,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
             if (tid < (int)(sizeof(DevDfa) / 4))
                 reinterpret_cast<uint32_t*>(&d)[tid] = reinterpret_cast<const uint32_t*>(lp.dfas + di)[tid];
             __syncthreads();
+            if (lp.no_nib) {  // this launch matches byte-row DFAs from their tables
+                if (tid == 0) d.nib = 0;
+                __syncthreads();
+            }
             if (d.placement == kSmem) {
                 const uint4* src = reinterpret_cast<const uint4*>(d.nib ? d.nib_rows : d.table);
                 uint4* dst = reinterpret_cast<uint4*>(sm + L.table);
@@ -1318,7 +1322,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_match(LaunchPlan lp, uint32_
                     }
                 } else {
                     uint16_t* bo = reinterpret_cast<uint16_t*>(sm + L.boff);
-                    for (int i = tid; i < 256; i += kThreads) bo[i] = __ldg(d.byte_off16 + i);
+                    const uint16_t* src16 = d.nib ? d.nib_off16 : d.byte_off16;
+                    for (int i = tid; i < 256; i += kThreads) bo[i] = __ldg(src16 + i);
                 }
             } else {
                 uint32_t* bo = reinterpret_cast<uint32_t*>(sm + L.boff);
@@ -1618,6 +1623,11 @@ static int grid_for(const DevProps& p, uint32_t smem, uint32_t* grid) {
         return DFA_ECUDA;
     *grid = p.sms * (uint32_t)per_sm;
     return DFA_OK;
+}
+
+uint32_t device_sms() {
+    const DevProps* p = dev_props();
+    return p ? p->sms : 0u;
 }
 
 int match_grid(uint32_t smem, uint32_t kmax, uint32_t* grid) {
