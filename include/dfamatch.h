@@ -77,9 +77,11 @@ typedef struct {
     uint64_t device_bytes;   /* all device memory held by this dfa_t               */
     double gamma;            /* Eq. (18): I_max / |Q|                              */
     double mean_iset;        /* mean |I_c| over the classes                        */
-    uint32_t byte_rows;      /* 1: chains visit at most 16 states, so the match kernel
-                                steps them by byte permutes of 16-byte class rows
-                                held in shared memory instead of table loads       */
+    uint32_t byte_rows;      /* 1: chains visit at most 16 states, so single-test
+                                launches with few chains (at most 128 per SM, where
+                                the chains are latency-bound) step them by byte
+                                permutes of 16-byte class rows held in shared memory
+                                instead of table loads; other launches use the table */
     uint32_t reserved;
 } dfa_info_t;
 
