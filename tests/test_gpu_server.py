@@ -92,3 +92,42 @@ def test_batches_overlap_under_continuous_arrivals(dm):
     _, efs, eacc = oracle.Dfa.from_spec(spec).run(x)
     assert all((r[1], r[2], r[3]) == (efs, eacc, 0) for r in res)
     srv.close()
+
+
+def test_error_paths_reported_without_a_fault(dm):
+    """Failures made on the host, none on the GPU: a server budget larger than the
+    device (DFA_ENOMEM from its allocation), a drain that runs out of time while
+    work is still on the device (DFA_ETIMEOUT, after which the work completes and
+    is right), a workspace smaller than the size query (DFA_ENOSPACE) and
+    misaligned device pointers (DFA_EINVAL)."""
+    import torch
+    with pytest.raises(dm.DfaError) as e:
+        dm.Server(1 << 50)
+    assert e.value.status == dm.ENOMEM
+    spec = gen.regex_dfa(2)
+    d = dm.Dfa.from_spec(spec)
+    x = gen.zipf_text(17, 256 << 20)
+    srv = dm.Server(2 << 30, max_inflight=2)
+    t = srv.submit(d, x)
+    with pytest.raises(dm.DfaError) as e:
+        srv.drain(1e-6)
+    assert e.value.status == dm.ETIMEOUT
+    srv.drain(120.0)
+    done = srv.poll(8)
+    srv.close()
+    assert len(done) == 1 and done[0][0] == t
+    assert (done[0][3], done[0][1], done[0][2]) == oracle.Dfa.from_spec(spec).run(x)
+    dev = torch.from_numpy(x[: 1 << 20]).cuda()
+    out = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    need = d.workspace_size(dev.numel())
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dm.DfaError) as e:
+        d.match_async(dev, out, ws[: need - 256])
+    assert e.value.status == dm.ENOSPACE
+    with pytest.raises(dm.DfaError) as e:
+        d.match_async(dev, out[1:], ws)           # result not 4-byte aligned
+    assert e.value.status == dm.EINVAL
+    big = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dm.DfaError) as e:
+        d.match_async(dev, out, big[16:])         # workspace not 256-byte aligned
+    assert e.value.status == dm.EINVAL
