@@ -457,6 +457,19 @@ def protein_workload(seed: int = 3, n: int = 10 * 10**9, words=None) -> Workload
                     "|Q|=1288, 20 amino-acid letters, i.i.d. residues, motifs at 1e-6")
 
 
+# |Q| of the protein-shaped DFAs matched together on one protein text (a
+# group of PROSITE-like patterns of growing size; their joint tables, 21 rows
+# of 16-bit entries each, total about 64 KB)
+PROTEIN_GROUP_SIZES = (16, 32, 64, 100, 160, 240, 340, 480)
+
+
+def protein_group_dfas(seed: int = 7, sizes=PROTEIN_GROUP_SIZES):
+    """Protein-shaped DFAs over the 20 amino-acid letters (gamma_c in
+    [0.02, 0.35], as protein_dfa), one per entry of sizes."""
+    return [class_dfa(seed * 100 + i, q, 20, 0.02, 0.35, max(1, q // 100), "protein",
+                      name="protein%d" % q) for i, q in enumerate(sizes)]
+
+
 def _size_name(n: int) -> str:
     if n >= 10**9 and n % 10**9 == 0:
         return "%dGB" % (n // 10**9)

@@ -422,6 +422,107 @@ int dfa_probe_lookup_rate(const dfa_t *dfa, uint32_t steps, void *stream, double
 /* Human-readable text for a status code (static storage). */
 const char *dfa_strerror(int status);
 
+/* ---------------------------------------------- several DFAs on one input */
+
+/*
+ * A group matches several DFAs against one input string and reads and
+ * converts that input once for all of them.  This is the arrangement of
+ * Sec. 5: the tables of several DFAs stored side by side (SBase), and one
+ * input converted to symbol indices (IBase) that every DFA reads.  Each DFA's
+ * answer is computed by the method dfa_match uses (Algorithm 3 with one
+ * reverse-lookahead symbol, Eqs. 8-9 to combine), on chunk starts shared by
+ * the whole group (Eqs. 6-7 with unit weights and m = 1), so it equals the
+ * answer dfa_match gives for that DFA alone.
+ *
+ * Joint classes: two bytes share a joint class iff they share a class in
+ * every DFA of the group (or lie outside Sigma for the same DFAs).  The input
+ * is staged once as joint-class indices, and the group holds a copy of every
+ * DFA's table with one row per joint class.  This suits DFAs over one
+ * alphabet, such as protein patterns over the 20 amino-acid letters (at most
+ * 21 joint classes); DFAs with unrelated byte classes give many joint classes
+ * and large tables.
+ *
+ * Limits (DFA_EINVAL at creation): 1 <= count <= 16 DFAs, each with at most
+ * 4095 states; at most 255 joint classes; all joint tables together at most
+ * 160 KiB (every thread block holds all of them in shared memory); the sum
+ * over the DFAs of their largest initial-state set (Eq. 12, or 1) at most 8192,
+ * and at most 512 thread slots for one chunk's sets at K = 16.
+ */
+typedef struct dfa_group_s dfa_group_t;
+
+typedef struct {
+    uint32_t num_dfas;
+    uint32_t joint_classes;     /* J                                                  */
+    uint32_t state_bytes;       /* joint-table entry size: 1 if every |Q|+1 <= 256, else 2 */
+    uint32_t states_per_thread; /* default K (chains one thread advances together)    */
+    uint32_t max_states_ext;    /* largest |Q|+1 of the group: the row stride of
+                                   dfa_group_debug_chunk_maps                          */
+    uint32_t sum_max_set;       /* sum over the DFAs of their largest initial-state set */
+    uint64_t table_bytes;       /* all joint tables (J+1 rows per DFA)                */
+    uint64_t device_bytes;      /* device memory held by the group (0: host-only)     */
+} dfa_group_info_t;
+
+/* Optional per-call settings; NULL for the defaults. */
+typedef struct {
+    uint32_t num_chunks;        /* P, shared by the group's DFAs; 0 = planner default  */
+    uint32_t states_per_thread; /* K in {1, 2, 4, 8, 16}; 0 = the group's default. One
+                                   chunk's sets must fit 512 threads (DFA_EINVAL)      */
+    uint32_t ctas_per_sm;       /* 1 or 2; 0 = 2 where shared memory allows            */
+    uint32_t reserved;          /* 0                                                   */
+    uint64_t *dev_work;         /* optional device uint64 (8-byte aligned): receives the
+                                   launch's lookups, the sum over DFAs and chunks of
+                                   L_k |I_k| (the work term of Eq. 16)                 */
+    void *match_begin_event;    /* optional cudaEvent_t pair recorded right before and */
+    void *match_end_event;      /* after the match kernel                              */
+} dfa_group_opts_t;
+
+/*
+ * Builds a group of count DFAs (joint classes, joint tables) and uploads it to
+ * the current device, which must be the DFAs' device.  The DFAs must outlive
+ * the group.  DFAs made by dfa_create_host give a host-only group:
+ * dfa_group_info and dfa_group_joint_classes work, the other calls return
+ * DFA_EHOSTONLY.  Mixing device and host-only DFAs is DFA_EINVAL.
+ * Errors: DFA_EINVAL (limits above), DFA_ENOMEM, DFA_ECUDA.  *out is NULL on error.
+ */
+int dfa_group_create(const dfa_t *const *dfas, uint32_t count, dfa_group_t **out);
+void dfa_group_destroy(dfa_group_t *group);
+int dfa_group_info(const dfa_group_t *group, dfa_group_info_t *out);
+/* out[b] (256 entries): the joint class of byte b. */
+int dfa_group_joint_classes(const dfa_group_t *group, uint16_t *out);
+/* P that dfa_group_match_async uses for (group, len, opts). */
+int dfa_group_plan_chunks(const dfa_group_t *group, uint64_t len, const dfa_group_opts_t *opts,
+                          uint32_t *P);
+int dfa_group_workspace_size(const dfa_group_t *group, uint64_t len, const dfa_group_opts_t *opts,
+                             uint64_t *bytes);
+
+/*
+ * Asynchronous membership test of every DFA of the group on dev_str (device,
+ * len < 2^46 bytes), on `stream`: dev_out[i] (device, count entries, 4-byte
+ * aligned) receives DFA i's result, with DFA_ESYMBOL in its status when the
+ * input holds a byte outside that DFA's Sigma (the other DFAs' results are
+ * unaffected).  dev_workspace (256-byte aligned, at least
+ * dfa_group_workspace_size bytes) is the caller's and must not be used by
+ * another launch until this one completes.  Issues one memset and two kernels
+ * (no allocation, no host synchronisation).
+ * Errors (returned): DFA_EINVAL, DFA_ENOSPACE, DFA_EHOSTONLY, DFA_ECUDA.
+ */
+int dfa_group_match_async(const dfa_group_t *group, const uint8_t *dev_str, uint64_t len,
+                          const dfa_group_opts_t *opts, dfa_result_t *dev_out, void *dev_workspace,
+                          uint64_t workspace_bytes, void *stream);
+
+/*
+ * Inspection: the chunk maps L_k (Sec. 4.1) of every DFA of the group, as the
+ * match kernel computed them: maps[(i*np + k)*stride + j] = delta_i*(j, chunk k)
+ * for j in DFA i's I_k and j otherwise, with np = min(cap, P) and stride =
+ * max_states_ext of dfa_group_info.  final_states[i] (optional, count
+ * entries) gets DFA i's final state (0xFFFFFFFF for a failed test).  *P
+ * receives the chunk count; with maps and final_states both NULL nothing is
+ * launched.  Allocates device memory and synchronises the device.
+ */
+int dfa_group_debug_chunk_maps(const dfa_group_t *group, const uint8_t *dev_str, uint64_t len,
+                               const dfa_group_opts_t *opts, uint16_t *maps, uint32_t cap,
+                               uint32_t *P, uint32_t *final_states);
+
 /* ------------------------------------------------------------- serving */
 
 typedef struct {

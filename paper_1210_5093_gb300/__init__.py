@@ -63,6 +63,20 @@ class MatchOpts(ctypes.Structure):
                 ("match_begin_event", ctypes.c_void_p), ("match_end_event", ctypes.c_void_p)]
 
 
+class GroupInfo(ctypes.Structure):
+    _fields_ = [("num_dfas", ctypes.c_uint32), ("joint_classes", ctypes.c_uint32),
+                ("state_bytes", ctypes.c_uint32), ("states_per_thread", ctypes.c_uint32),
+                ("max_states_ext", ctypes.c_uint32), ("sum_max_set", ctypes.c_uint32),
+                ("table_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+
+
+class GroupOpts(ctypes.Structure):
+    _fields_ = [("num_chunks", ctypes.c_uint32), ("states_per_thread", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("dev_work", ctypes.c_void_p), ("match_begin_event", ctypes.c_void_p),
+                ("match_end_event", ctypes.c_void_p)]
+
+
 class Completion(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("result", Result), ("submit_s", ctypes.c_double),
                 ("done_s", ctypes.c_double)]
@@ -110,6 +124,14 @@ SIGNATURES = {
     "dfa_batch_set_events": (_I, [_P, _P, _P]),
     "dfa_batch_destroy": (None, [_P]),
     "dfa_strerror": (ctypes.c_char_p, [_I]),
+    "dfa_group_create": (_I, [_P, _U32, _P]),
+    "dfa_group_destroy": (None, [_P]),
+    "dfa_group_info": (_I, [_P, _P]),
+    "dfa_group_joint_classes": (_I, [_P, _P]),
+    "dfa_group_plan_chunks": (_I, [_P, _U64, _P, _P]),
+    "dfa_group_workspace_size": (_I, [_P, _U64, _P, _P]),
+    "dfa_group_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
+    "dfa_group_debug_chunk_maps": (_I, [_P, _P, _U64, _P, _P, _U32, _P, _P]),
     "dfa_server_create": (_I, [_U64, _U32, _P]),
     "dfa_server_set_opts": (_I, [_P, _P]),
     "dfa_server_submit": (_I, [_P, _P, _P, _U64, _P]),
@@ -469,6 +491,109 @@ def match_batch(dfas: Sequence[Dfa], tensors, stream=None, num_chunks: int = 0,
     _check(lib().dfa_match_batch(n, dp, sp, lens.ctypes.data, ctypes.byref(o), out.data_ptr(),
                                  _stream_ptr(stream)), "dfa_match_batch")
     return results_from(out)
+
+
+def _gopts(num_chunks=0, states_per_thread=0, ctas_per_sm=0, work=None, events=None) -> GroupOpts:
+    ev = (None, None) if events is None else (events[0].cuda_event, events[1].cuda_event)
+    return GroupOpts(int(num_chunks), int(states_per_thread), int(ctas_per_sm), 0,
+                     None if work is None else work.data_ptr(), ev[0], ev[1])
+
+
+class Group:
+    """Several DFAs matched together on one input, the input staged once for
+    all of them (dfa_group_t).  The Dfa objects are kept alive with the group."""
+
+    def __init__(self, dfas: Sequence[Dfa]):
+        self._dfas = list(dfas)
+        dp = _ptr_array([d.handle.value for d in self._dfas])
+        h = ctypes.c_void_p()
+        _check(lib().dfa_group_create(dp, len(self._dfas), ctypes.byref(h)), "dfa_group_create")
+        self._h = h
+        self.count = len(self._dfas)
+
+    def info(self) -> GroupInfo:
+        out = GroupInfo()
+        _check(lib().dfa_group_info(self._h, ctypes.byref(out)), "dfa_group_info")
+        return out
+
+    def joint_classes(self) -> np.ndarray:
+        out = np.zeros(256, dtype=np.uint16)
+        _check(lib().dfa_group_joint_classes(self._h, out.ctypes.data), "dfa_group_joint_classes")
+        return out
+
+    def plan_chunks(self, n: int, num_chunks: int = 0, states_per_thread: int = 0,
+                    ctas_per_sm: int = 0) -> int:
+        P = ctypes.c_uint32()
+        o = _gopts(num_chunks, states_per_thread, ctas_per_sm)
+        _check(lib().dfa_group_plan_chunks(self._h, n, ctypes.byref(o), ctypes.byref(P)),
+               "dfa_group_plan_chunks")
+        return int(P.value)
+
+    def workspace_size(self, n: int, num_chunks: int = 0, states_per_thread: int = 0,
+                       ctas_per_sm: int = 0) -> int:
+        out = ctypes.c_uint64()
+        o = _gopts(num_chunks, states_per_thread, ctas_per_sm)
+        _check(lib().dfa_group_workspace_size(self._h, n, ctypes.byref(o), ctypes.byref(out)),
+               "dfa_group_workspace_size")
+        return int(out.value)
+
+    def match_async(self, dev_data, dev_out, workspace, stream=None, num_chunks: int = 0,
+                    states_per_thread: int = 0, ctas_per_sm: int = 0, work=None, events=None):
+        """Enqueue the group's tests on dev_data (CUDA uint8 tensor); dev_out: CUDA
+        uint8 tensor of >= 12*count bytes; work: optional CUDA int64 tensor that
+        receives the launch's lookups; events: optional (begin, end) pair."""
+        o = _gopts(num_chunks, states_per_thread, ctas_per_sm, work, events)
+        n = dev_data.numel()
+        _check(lib().dfa_group_match_async(self._h, dev_data.data_ptr() if n else None, n,
+                                           ctypes.byref(o), dev_out.data_ptr(), workspace.data_ptr(),
+                                           workspace.numel(), _stream_ptr(stream)),
+               "dfa_group_match_async")
+
+    def match(self, dev_data, num_chunks: int = 0, states_per_thread: int = 0,
+              ctas_per_sm: int = 0) -> list:
+        """Synchronous: one (status, final_state, accept) per DFA, in order
+        (final_state and accept are None for a failed test)."""
+        torch = _torch()
+        n = dev_data.numel()
+        ws = torch.empty(max(256, self.workspace_size(n, num_chunks, states_per_thread, ctas_per_sm)),
+                         dtype=torch.uint8, device=dev_data.device)
+        out = torch.zeros(12 * self.count, dtype=torch.uint8, device=dev_data.device)
+        self.match_async(dev_data, out, ws, None, num_chunks, states_per_thread, ctas_per_sm)
+        torch.cuda.current_stream().synchronize()
+        res = []
+        for f, a, st in results_from(out):
+            if st == EBOUNDS:
+                raise DfaError(st, "dfa_group_match_async (check at dfa_group.cu line %d)" % f)
+            res.append((st, f, a) if st == OK else (st, None, None))
+        return res
+
+    def chunk_maps(self, dev_data, num_chunks: int = 0, states_per_thread: int = 0):
+        """(maps [count, P, max_states_ext] uint16, final states): every DFA's
+        chunk maps L_k as the match kernel computed them."""
+        o = _gopts(num_chunks, states_per_thread)
+        n = dev_data.numel()
+        ptr = dev_data.data_ptr() if n else None
+        P = ctypes.c_uint32()
+        _check(lib().dfa_group_debug_chunk_maps(self._h, ptr, n, ctypes.byref(o), None, 0,
+                                                ctypes.byref(P), None), "dfa_group_debug_chunk_maps")
+        stride = self.info().max_states_ext
+        out = np.zeros((self.count, P.value, stride), dtype=np.uint16)
+        fs = np.zeros(self.count, dtype=np.uint32)
+        _check(lib().dfa_group_debug_chunk_maps(self._h, ptr, n, ctypes.byref(o), out.ctypes.data,
+                                                P.value, ctypes.byref(P), fs.ctypes.data),
+               "dfa_group_debug_chunk_maps")
+        return out, fs
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().dfa_group_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

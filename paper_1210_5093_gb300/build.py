@@ -20,6 +20,7 @@ OUT_DEBUG = os.path.join(HERE, "libdfamatch_debug.so")
 BUILD_DIR_DEBUG = os.path.join(HERE, "_build_debug")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["dfa_kernels.cu", "dfa_api.cu", "dfa_server.cu", "dfa_noalloc.cu", "dfa_probe.cu",
+           "dfa_group.cu",
            "dfa_compile.cpp"]
 
 
