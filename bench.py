@@ -536,6 +536,77 @@ def batch_inputs(args):
     return specs, picks, datas
 
 
+def group_config(args, dm, torch, lookup_peak, n: int = 1 << 30, reps: int = 5):
+    """Several DFAs on one input, the input staged once for all of them (Sec. 5):
+    8 protein-shaped DFAs (|Q| 16-480 over the 20 amino-acid letters) on n bytes
+    of protein text, as one group launch (tuned on the input first), against one
+    batched launch of the same 8 tests and one launch per DFA.  GB/s count the
+    input bytes once per DFA (every DFA reads the whole input)."""
+    import gen
+    specs = gen.protein_group_dfas(7)
+    dfas = [dm.Dfa.from_spec(s) for s in specs]
+    g = dm.Group(dfas)
+    data = gen.protein_text(3, n)
+    dev = torch.from_numpy(data).cuda()
+    expect, t_or, thr = oracle_answers_all_cores(specs, list(range(len(specs))), [data] * len(specs))
+    stream = torch.cuda.Stream()
+    K, cps, _ = g.autotune(dev, stream=stream)
+    info = g.info()
+    ws = torch.empty(g.workspace_size(n), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(12 * g.count, dtype=torch.uint8, device="cuda")
+    work = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(reps)] for _ in range(4)]
+    for e in sum(ev, []):
+        e.record(stream)    # creates the events; the library re-records the first two kinds
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.match_async(dev, out, ws, stream=stream, work=work)
+    torch.cuda.synchronize()
+    res = dm.results_from(out)
+    assert [_as_answer(r) for r in res] == expect, "group answers differ from the oracle"
+    W = int(work.item())
+    clk = Clocks(torch.cuda.current_device()).start()
+    with torch.cuda.stream(stream):
+        for i in range(reps):
+            ev[2][i].record(stream)
+            g.match_async(dev, out, ws, stream=stream, events=(ev[0][i], ev[1][i]))
+            ev[3][i].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    assert dm.results_from(out) == res, "the answers changed between steps"
+    km = statistics.median(a.elapsed_time(b) for a, b in zip(ev[0], ev[1]))
+    sm_ = statistics.median(a.elapsed_time(b) for a, b in zip(ev[2], ev[3]))
+    bl, res_b, res_p = batched_leg(dm, torch, dfas, [dev] * len(dfas), reps=reps)
+    assert [_as_answer(r) for r in res_b] == expect == [_as_answer(r) for r in res_p], \
+        "batched or per-DFA answers differ from the oracle"
+    total = n * len(specs)
+    leg = {"workload": "protein_group_%ddfa_%s" % (len(specs), gen._size_name(n)),
+           "states": [s.num_states for s in specs], "input_bytes": n,
+           "joint_classes": int(info.joint_classes), "table_bytes": int(info.table_bytes),
+           "state_bytes": int(info.state_bytes),
+           "tuning": {"states_per_thread": K, "ctas_per_sm": cps}, "chunks": g.plan_chunks(n),
+           "gbs": round(total / sm_ / 1e6, 3), "input_gbs": round(n / sm_ / 1e6, 3),
+           "step_ms": round(sm_, 4), "kernel_ms": round(km, 4), "steps_timed": reps,
+           "lookups_per_byte": round(W / n, 3),
+           "lookup_roof_frac": round(W / (km / 1e3) / lookup_peak, 4),
+           "batched": {"gbs": bl["gbs"], "ms": bl["ms"], "launches": bl["launches"]},
+           "per_dfa": {"gbs": bl["plain_gbs"], "ms": bl["plain_ms"], "launches": bl["plain_launches"]},
+           "speedup_vs_batched": round(bl["ms"] / sm_, 3),
+           "speedup_vs_per_dfa": round(bl["plain_ms"] / sm_, 3),
+           "launches": 2, "clocks": clocks, "l2": "input larger than L2, not flushed",
+           "oracle_match": "all %d DFAs (group, batched and per-DFA launches)" % len(specs),
+           "cpu_baseline": {"value": round(total / t_or / 1e9, 4), "unit": "GB/s", "cores": thr,
+                            "kind": "oracle",
+                            "sample": "every DFA on the whole input, Algorithm 1 (C), one DFA "
+                                      "per host thread; the same run checks every answer"}}
+    g.close()
+    for d in dfas:
+        d.close()
+    del dev, ws, out, work
+    return leg
+
+
 def batch_config(args, dm, torch):
     """One persistent graph-replayed launch over the batched mix against the
     plain path (one call per test); every answer checked against the oracle,
@@ -937,6 +1008,10 @@ def main():
             cfg["protein1288_%s" % ("10GB" if args.protein_bytes == 10 * 10**9
                                     else "%dB" % args.protein_bytes)] = \
                 protein_config(args, dm, torch, lookup_peak, args.protein_bytes)
+            _free(torch)
+            grp = group_config(args, dm, torch, lookup_peak)
+            cfg[grp["workload"]] = grp
+            _free(torch)
             bl, state = batch_config(args, dm, torch)
             cfg["batched_cfg4"] = bl
             cfg["serving_cfg5"] = serve_config(args, dm, torch, state, bl["gbs"])

@@ -454,10 +454,15 @@ typedef struct {
     uint32_t num_dfas;
     uint32_t joint_classes;     /* J                                                  */
     uint32_t state_bytes;       /* joint-table entry size: 1 if every |Q|+1 <= 256, else 2 */
-    uint32_t states_per_thread; /* default K (chains one thread advances together)    */
+    uint32_t states_per_thread; /* default K (chains one thread advances together):
+                                   the compiler's rule on the mean set size, or what
+                                   dfa_group_autotune chose                             */
+    uint32_t ctas_per_sm;       /* default thread blocks per SM (0: 2 where shared
+                                   memory allows), or what dfa_group_autotune chose    */
     uint32_t max_states_ext;    /* largest |Q|+1 of the group: the row stride of
                                    dfa_group_debug_chunk_maps                          */
     uint32_t sum_max_set;       /* sum over the DFAs of their largest initial-state set */
+    uint32_t reserved;
     uint64_t table_bytes;       /* all joint tables (J+1 rows per DFA)                */
     uint64_t device_bytes;      /* device memory held by the group (0: host-only)     */
 } dfa_group_info_t;
@@ -467,7 +472,7 @@ typedef struct {
     uint32_t num_chunks;        /* P, shared by the group's DFAs; 0 = planner default  */
     uint32_t states_per_thread; /* K in {1, 2, 4, 8, 16}; 0 = the group's default. One
                                    chunk's sets must fit 512 threads (DFA_EINVAL)      */
-    uint32_t ctas_per_sm;       /* 1 or 2; 0 = 2 where shared memory allows            */
+    uint32_t ctas_per_sm;       /* 1 or 2; 0 = the group's default                     */
     uint32_t reserved;          /* 0                                                   */
     uint64_t *dev_work;         /* optional device uint64 (8-byte aligned): receives the
                                    launch's lookups, the sum over DFAs and chunks of
@@ -489,6 +494,17 @@ void dfa_group_destroy(dfa_group_t *group);
 int dfa_group_info(const dfa_group_t *group, dfa_group_info_t *out);
 /* out[b] (256 entries): the joint class of byte b. */
 int dfa_group_joint_classes(const dfa_group_t *group, uint16_t *out);
+/*
+ * Tuning (the GPU counterpart of the paper's per-processor profiling, Sec. 4.1):
+ * times every K in {1, 2, 4, 8, 16} whose chunk sets fit 512 threads, with 1
+ * and 2 thread blocks per SM, on a device sample of len bytes (one warm-up and
+ * two timed launches each, CUDA events on `stream`), and keeps the fastest as
+ * the group's default.  *states_per_thread, *ctas_per_sm and *best_ms (each
+ * optional) receive it.  Allocates a workspace and synchronises the stream.
+ * Errors: DFA_EINVAL, DFA_EHOSTONLY, DFA_ENOMEM, DFA_ECUDA.
+ */
+int dfa_group_autotune(dfa_group_t *group, const uint8_t *dev_sample, uint64_t len, void *stream,
+                       uint32_t *states_per_thread, uint32_t *ctas_per_sm, double *best_ms);
 /* P that dfa_group_match_async uses for (group, len, opts). */
 int dfa_group_plan_chunks(const dfa_group_t *group, uint64_t len, const dfa_group_opts_t *opts,
                           uint32_t *P);

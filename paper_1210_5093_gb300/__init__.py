@@ -66,7 +66,8 @@ class MatchOpts(ctypes.Structure):
 class GroupInfo(ctypes.Structure):
     _fields_ = [("num_dfas", ctypes.c_uint32), ("joint_classes", ctypes.c_uint32),
                 ("state_bytes", ctypes.c_uint32), ("states_per_thread", ctypes.c_uint32),
-                ("max_states_ext", ctypes.c_uint32), ("sum_max_set", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("max_states_ext", ctypes.c_uint32),
+                ("sum_max_set", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("table_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
 
 
@@ -128,6 +129,7 @@ SIGNATURES = {
     "dfa_group_destroy": (None, [_P]),
     "dfa_group_info": (_I, [_P, _P]),
     "dfa_group_joint_classes": (_I, [_P, _P]),
+    "dfa_group_autotune": (_I, [_P, _P, _U64, _P, _P, _P, _P]),
     "dfa_group_plan_chunks": (_I, [_P, _U64, _P, _P]),
     "dfa_group_workspace_size": (_I, [_P, _U64, _P, _P]),
     "dfa_group_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
@@ -520,6 +522,16 @@ class Group:
         out = np.zeros(256, dtype=np.uint16)
         _check(lib().dfa_group_joint_classes(self._h, out.ctypes.data), "dfa_group_joint_classes")
         return out
+
+    def autotune(self, dev_sample, stream=None):
+        """Time the candidate K and CTAs per SM on a device sample and keep the
+        fastest as the group's default.  Returns (K, ctas_per_sm, best_ms)."""
+        K, c, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+        n = dev_sample.numel()
+        _check(lib().dfa_group_autotune(self._h, dev_sample.data_ptr() if n else None, n,
+                                        _stream_ptr(stream), ctypes.byref(K), ctypes.byref(c),
+                                        ctypes.byref(ms)), "dfa_group_autotune")
+        return int(K.value), int(c.value), float(ms.value)
 
     def plan_chunks(self, n: int, num_chunks: int = 0, states_per_thread: int = 0,
                     ctas_per_sm: int = 0) -> int:

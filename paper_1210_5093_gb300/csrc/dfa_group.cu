@@ -761,6 +761,7 @@ using namespace dfam::grp;
 struct dfa_group_s {
     std::vector<const dfa_s*> dfas;
     uint32_t G = 0, J = 0, sb = 1, tbytes = 0, vcap_sum = 0, qe_max = 0, K0 = 4, seg_stride = 0;
+    uint32_t ctas0 = 0;            // default thread blocks per SM (0: 2 where they fit)
     std::vector<uint16_t> jmap;    // 256: joint class | 0x8000 if some DFA has it outside Sigma
     std::vector<uint16_t> jbad;    // 256: joint class -> mask of DFAs with it outside Sigma
     std::vector<uint32_t> jinfo;   // G * 256
@@ -805,7 +806,7 @@ int plan_launch(const dfa_group_s* g, uint64_t n, const dfa_group_opts_t* o, GLa
     if (n >= kMaxLen) return DFA_EINVAL;
     const uint32_t K = (o && o->states_per_thread) ? o->states_per_thread : g->K0;
     if (k_index(K) > 4 || max_chunk_slots(g, K) > kGThreads) return DFA_EINVAL;
-    const uint32_t want = (o && o->ctas_per_sm) ? o->ctas_per_sm : 2u;
+    const uint32_t want = (o && o->ctas_per_sm) ? o->ctas_per_sm : (g->ctas0 ? g->ctas0 : 2u);
     if (want > 2) return DFA_EINVAL;
     const Props* pr = props();
     if (!pr) return DFA_ECUDA;
@@ -1095,6 +1096,7 @@ int dfa_group_info(const dfa_group_t* g, dfa_group_info_t* out) {
     out->joint_classes = g->J;
     out->state_bytes = g->sb;
     out->states_per_thread = g->K0;
+    out->ctas_per_sm = g->ctas0;
     out->max_states_ext = g->qe_max;
     out->sum_max_set = g->vcap_sum;
     out->table_bytes = g->tbytes;
@@ -1105,6 +1107,77 @@ int dfa_group_info(const dfa_group_t* g, dfa_group_info_t* out) {
 int dfa_group_joint_classes(const dfa_group_t* g, uint16_t* out) {
     if (!g || !out) return DFA_EINVAL;
     for (uint32_t b = 0; b < 256; ++b) out[b] = g->jmap[b] & 0xFFu;
+    return DFA_OK;
+}
+
+int dfa_group_autotune(dfa_group_t* g, const uint8_t* dev_sample, uint64_t len, void* stream,
+                       uint32_t* states_per_thread, uint32_t* ctas_per_sm, double* best_ms) {
+    if (!g || (len && !dev_sample)) return DFA_EINVAL;
+    if (!g->on_device) return DFA_EHOSTONLY;
+    struct Cand {
+        uint32_t K, ctas;
+        GLaunch l;
+    };
+    std::vector<Cand> cands;
+    uint64_t ws_need = 0;
+    for (uint32_t K : {1u, 2u, 4u, 8u, 16u})
+        for (uint32_t c : {1u, 2u}) {
+            dfa_group_opts_t o;
+            std::memset(&o, 0, sizeof o);
+            o.states_per_thread = K;
+            o.ctas_per_sm = c;
+            Cand x;
+            x.K = K;
+            x.ctas = c;
+            if (plan_launch(g, len, &o, &x.l) != DFA_OK) continue;
+            ws_need = std::max(ws_need, x.l.ws_total);
+            cands.push_back(x);
+        }
+    if (cands.empty()) return DFA_EINVAL;
+    void *ws = nullptr, *res = nullptr;
+    if (cudaMalloc(&ws, ws_need) != cudaSuccess || cudaMalloc(&res, sizeof(dfa_result_t) * g->G) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ws);
+        return DFA_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) ? DFA_OK
+                                                                                          : DFA_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double best = 1e30;
+    const Cand* win = nullptr;
+    for (Cand& x : cands) {
+        if (rc != DFA_OK) break;
+        bind_ws(x.l, static_cast<uint8_t*>(ws));
+        x.l.p.str = dev_sample;
+        x.l.p.results = static_cast<dfa_result_t*>(res);
+        float t = 1e30f;
+        for (int rep = 0; rep < 3 && rc == DFA_OK; ++rep) {  // the first launch warms up
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = DFA_ECUDA;
+            if (rc == DFA_OK) rc = issue(x.l, g->sb, nullptr, stream);
+            if (rc == DFA_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                 cudaEventSynchronize(e1) != cudaSuccess))
+                rc = DFA_ECUDA;
+            float ms = 0;
+            if (rc == DFA_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                t = std::min(t, ms);
+        }
+        if (rc == DFA_OK && t < best) {
+            best = t;
+            win = &x;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(ws);
+    cudaFree(res);
+    if (rc != DFA_OK) return rc;
+    if (!win) return DFA_ECUDA;
+    g->K0 = win->K;
+    g->ctas0 = win->ctas;
+    if (states_per_thread) *states_per_thread = win->K;
+    if (ctas_per_sm) *ctas_per_sm = win->ctas;
+    if (best_ms) *best_ms = best;
     return DFA_OK;
 }
 

@@ -80,6 +80,23 @@ def main():
     d = dm.Dfa.from_spec(w.spec)
     d.set_tuning(host_segment_bytes=8 << 20)
     check(d, w.spec, torch.from_numpy(w.data).pin_memory())
+    # groups of DFAs sharing one stage: protein DFAs at several K and chunk
+    # counts, and a group whose byte-classed DFA has every byte in Sigma while
+    # its protein DFA does not (a byte outside the letters fails only the latter)
+    groups = [(gen.protein_group_dfas(7), gen.protein_text(11, 4 << 20)),
+              ([gen.class_dfa(75, 60, 8, 0.05, 0.4, 2, "byte")] + gen.protein_group_dfas(8, (20, 90)),
+               gen.protein_text(12, 1 << 20))]
+    groups[1][1][300_000] = ord("#")
+    for gspecs, x in groups:
+        g = dm.Group([dm.Dfa.from_spec(s) for s in gspecs])
+        dev = torch.from_numpy(x).cuda()
+        want = [oracle.Dfa.from_spec(s).run(x) for s in gspecs]
+        for kw in ({}, {"states_per_thread": 1}, {"states_per_thread": 16, "num_chunks": 3000},
+                   {"num_chunks": 7}):
+            got = g.match(dev, **kw)       # raises on DFA_EBOUNDS
+            assert got == want, (kw, got, want)
+            checked += len(gspecs)
+        g.close()
     print("debug-bounds parity ok: %d checks" % checked)
 
 

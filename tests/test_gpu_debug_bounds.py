@@ -2,8 +2,8 @@
 and chunk bound; DFA_EBOUNDS on a failed check) gives the oracle's answer on
 the paper's workloads and on every kind of launch: Algorithms 2 and 3, Eq. 13
 sets, Sec. 4.2 placement, tables in shared memory and through L2, byte rows,
-multi-pass chunks of a 20000-state DFA, batches with graph replay and the
-pipelined host path.  Runs in its own process, which loads the debug library."""
+multi-pass chunks of a 20000-state DFA, batches with graph replay, the
+pipelined host path and groups of DFAs sharing one stage.  Runs in its own process, which loads the debug library."""
 import os
 import subprocess
 import sys

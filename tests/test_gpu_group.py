@@ -175,6 +175,8 @@ def test_group_async_reuse_and_events(dm, protein_group):
     ws = torch.empty(max(g.workspace_size(len(x)) for x in xs), dtype=torch.uint8, device="cuda")
     st = torch.cuda.Stream()
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for e in ev:
+        e.record(st)    # creates the events; the library re-records them around the match kernel
     devs = [torch.from_numpy(x).cuda() for x in xs]
     for rep in range(2):
         for x, dev, w in zip(xs, devs, want):
@@ -187,6 +189,22 @@ def test_group_async_reuse_and_events(dm, protein_group):
             got = dm.results_from(out)
             for (fs, acc, s_), (es, efs, eacc) in zip(got, w):
                 assert s_ == es and (s_ != 0 or (fs, acc) == (efs, eacc))
+
+
+def test_group_autotune(dm):
+    """The tuner keeps one of the candidates as the group's default; answers
+    with the tuned default equal the oracle's."""
+    import torch
+    specs = gen.protein_group_dfas(11, (24, 150, 400))
+    g = dm.Group([dm.Dfa.from_spec(s) for s in specs])
+    data = gen.protein_text(78, 3 << 20)
+    dev = torch.from_numpy(data).cuda()
+    K, c, ms = g.autotune(dev)
+    info = g.info()
+    assert K in (1, 2, 4, 8, 16) and c in (1, 2) and ms > 0
+    assert (info.states_per_thread, info.ctas_per_sm) == (K, c)
+    _check(g, specs, dev, data)
+    _check(g, specs, dev[:77_777], data[:77_777], num_chunks=33)
 
 
 def test_group_rejections(dm, protein_group):
