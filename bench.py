@@ -536,70 +536,87 @@ def batch_inputs(args):
     return specs, picks, datas
 
 
-def group_config(args, dm, torch, lookup_peak, n: int = 1 << 30, reps: int = 5):
+def group_config(args, dm, torch, lookup_peak, n: int = 1 << 30, reps: int = 5, tuning=None,
+                 check: bool = True, compare: bool = True):
     """Several DFAs on one input, the input staged once for all of them (Sec. 5):
     8 protein-shaped DFAs (|Q| 16-480 over the 20 amino-acid letters) on n bytes
-    of protein text, as one group launch (tuned on the input first), against one
-    batched launch of the same 8 tests and one launch per DFA.  GB/s count the
-    input bytes once per DFA (every DFA reads the whole input)."""
+    of protein text, as one group launch (tuned on the input first, or with the
+    given (K, CTAs per SM)), against one batched launch of the same 8 tests and
+    one launch per DFA.  GB/s count the input bytes once per DFA (every DFA
+    reads the whole input)."""
     import gen
     specs = gen.protein_group_dfas(7)
     dfas = [dm.Dfa.from_spec(s) for s in specs]
     g = dm.Group(dfas)
     data = gen.protein_text(3, n)
     dev = torch.from_numpy(data).cuda()
-    expect, t_or, thr = oracle_answers_all_cores(specs, list(range(len(specs))), [data] * len(specs))
+    expect = None
+    if check:
+        expect, t_or, thr = oracle_answers_all_cores(specs, list(range(len(specs))),
+                                                     [data] * len(specs))
     stream = torch.cuda.Stream()
-    K, cps, _ = g.autotune(dev, stream=stream)
+    if tuning:
+        K, cps = tuning
+    else:
+        K, cps, _ = g.autotune(dev, stream=stream)
     info = g.info()
-    ws = torch.empty(g.workspace_size(n), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(g.workspace_size(n, states_per_thread=K, ctas_per_sm=cps), dtype=torch.uint8,
+                     device="cuda")
     out = torch.zeros(12 * g.count, dtype=torch.uint8, device="cuda")
     work = torch.zeros(1, dtype=torch.int64, device="cuda")
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(reps)] for _ in range(4)]
     for e in sum(ev, []):
         e.record(stream)    # creates the events; the library re-records the first two kinds
     stream.wait_stream(torch.cuda.current_stream())
+    kw = {"states_per_thread": K, "ctas_per_sm": cps}
     with torch.cuda.stream(stream):
         for _ in range(3):
-            g.match_async(dev, out, ws, stream=stream, work=work)
+            g.match_async(dev, out, ws, stream=stream, work=work, **kw)
     torch.cuda.synchronize()
     res = dm.results_from(out)
-    assert [_as_answer(r) for r in res] == expect, "group answers differ from the oracle"
+    assert expect is None or [_as_answer(r) for r in res] == expect, \
+        "group answers differ from the oracle"
     W = int(work.item())
     clk = Clocks(torch.cuda.current_device()).start()
     with torch.cuda.stream(stream):
         for i in range(reps):
             ev[2][i].record(stream)
-            g.match_async(dev, out, ws, stream=stream, events=(ev[0][i], ev[1][i]))
+            g.match_async(dev, out, ws, stream=stream, events=(ev[0][i], ev[1][i]), **kw)
             ev[3][i].record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     assert dm.results_from(out) == res, "the answers changed between steps"
     km = statistics.median(a.elapsed_time(b) for a, b in zip(ev[0], ev[1]))
     sm_ = statistics.median(a.elapsed_time(b) for a, b in zip(ev[2], ev[3]))
-    bl, res_b, res_p = batched_leg(dm, torch, dfas, [dev] * len(dfas), reps=reps)
-    assert [_as_answer(r) for r in res_b] == expect == [_as_answer(r) for r in res_p], \
-        "batched or per-DFA answers differ from the oracle"
     total = n * len(specs)
     leg = {"workload": "protein_group_%ddfa_%s" % (len(specs), gen._size_name(n)),
            "states": [s.num_states for s in specs], "input_bytes": n,
            "joint_classes": int(info.joint_classes), "table_bytes": int(info.table_bytes),
            "state_bytes": int(info.state_bytes),
-           "tuning": {"states_per_thread": K, "ctas_per_sm": cps}, "chunks": g.plan_chunks(n),
+           "tuning": {"states_per_thread": K, "ctas_per_sm": cps, "fixed": bool(tuning)},
+           "chunks": g.plan_chunks(n, **kw),
            "gbs": round(total / sm_ / 1e6, 3), "input_gbs": round(n / sm_ / 1e6, 3),
            "step_ms": round(sm_, 4), "kernel_ms": round(km, 4), "steps_timed": reps,
            "lookups_per_byte": round(W / n, 3),
            "lookup_roof_frac": round(W / (km / 1e3) / lookup_peak, 4),
-           "batched": {"gbs": bl["gbs"], "ms": bl["ms"], "launches": bl["launches"]},
-           "per_dfa": {"gbs": bl["plain_gbs"], "ms": bl["plain_ms"], "launches": bl["plain_launches"]},
-           "speedup_vs_batched": round(bl["ms"] / sm_, 3),
-           "speedup_vs_per_dfa": round(bl["plain_ms"] / sm_, 3),
-           "launches": 2, "clocks": clocks, "l2": "input larger than L2, not flushed",
-           "oracle_match": "all %d DFAs (group, batched and per-DFA launches)" % len(specs),
-           "cpu_baseline": {"value": round(total / t_or / 1e9, 4), "unit": "GB/s", "cores": thr,
-                            "kind": "oracle",
-                            "sample": "every DFA on the whole input, Algorithm 1 (C), one DFA "
-                                      "per host thread; the same run checks every answer"}}
+           "launches": 2, "clocks": clocks,
+           "l2": "input larger than L2, not flushed" if n > L2_BYTES else "input fits in L2"}
+    if compare:
+        bl, res_b, res_p = batched_leg(dm, torch, dfas, [dev] * len(dfas), reps=reps)
+        assert expect is None or [_as_answer(r) for r in res_b] == expect == \
+            [_as_answer(r) for r in res_p], "batched or per-DFA answers differ from the oracle"
+        leg.update(batched={"gbs": bl["gbs"], "ms": bl["ms"], "launches": bl["launches"]},
+                   per_dfa={"gbs": bl["plain_gbs"], "ms": bl["plain_ms"],
+                            "launches": bl["plain_launches"]},
+                   speedup_vs_batched=round(bl["ms"] / sm_, 3),
+                   speedup_vs_per_dfa=round(bl["plain_ms"] / sm_, 3))
+    if check:
+        leg["oracle_match"] = "all %d DFAs (group%s)" % (
+            len(specs), ", batched and per-DFA launches" if compare else "")
+        leg["cpu_baseline"] = {"value": round(total / t_or / 1e9, 4), "unit": "GB/s", "cores": thr,
+                               "kind": "oracle",
+                               "sample": "every DFA on the whole input, Algorithm 1 (C), one DFA "
+                                         "per host thread; the same run checks every answer"}
     g.close()
     for d in dfas:
         d.close()
@@ -681,7 +698,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="regex",
-                    choices=["regex", "plain", "protein", "batch", "serve"])
+                    choices=["regex", "plain", "protein", "batch", "serve", "group"])
     ap.add_argument("--tests", type=int, default=4096, help="batch/serve: number of tests")
     ap.add_argument("--max-len", type=int, default=64 << 20, help="batch/serve: longest test")
     ap.add_argument("--budget", type=int, default=40 << 30, help="serve: admission budget (bytes)")
@@ -700,7 +717,7 @@ def main():
                          "(0: the starts of Eqs. 6-7, the paper's partition)")
     ap.add_argument("--tuning", default="",
                     help="K,tiles_per_cta,ctas_per_sm[,grid_waves] instead of the autotuner "
-                         "(profiling runs)")
+                         "(profiling runs; for --workload group: K,ctas_per_sm)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -729,6 +746,25 @@ def main():
     hbm_peak, sm_max_mhz, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     lookup_peak = nsm * 32 * sm_max_mhz * 1e6           # 32 shared-memory lanes per clock per SM
+
+    if args.workload == "group":
+        # several DFAs on one input with one shared stage, alone (profiling runs):
+        # --bytes sets the input size, --tuning K,C fixes the tuning
+        if rank == 0:
+            tu = tuple(int(x) for x in args.tuning.split(",")[:2]) if args.tuning else None
+            leg = group_config(args, dm, torch, lookup_peak, n=args.bytes or (1 << 30),
+                               reps=max(1, args.steps), tuning=tu, check=not args.no_cpu,
+                               compare=not args.no_mix)
+            line = {"metric": METRIC, "value": leg["gbs"], "unit": "GB/s", "n_gpus": 1,
+                    "steps": leg["steps_timed"], "warmup": 3, "ms_per_step": leg["step_ms"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                    "dtype": "u16", "data": "synthetic", "config": {"workload": leg["workload"]},
+                    "group": leg}
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     if args.workload in ("batch", "serve"):
         if rank == 0:
