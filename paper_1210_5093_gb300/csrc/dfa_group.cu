@@ -258,7 +258,7 @@ static_assert(sizeof(GChunk) == 16, "GChunk layout");
 
 // Shared-memory carve-up of k_group_match (byte offsets, 16-byte aligned).
 struct GSmem {
-    uint32_t table, jmap, gd, stage, lmap, linit, vmap, vdom, vdfa, items, chunks, misc, total;
+    uint32_t table, jmap, stage, lmap, linit, vmap, vdom, vdfa, items, chunks, misc, gd, total;
 };
 
 __host__ __device__ inline uint32_t g_align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -268,8 +268,7 @@ __host__ __device__ inline GSmem g_layout(uint32_t tbytes, uint32_t K, uint32_t 
     GSmem L;
     L.table = 0;
     L.jmap = g_align16(tbytes);
-    L.gd = L.jmap + 1024;  // byte -> joint class, joint class -> outside-Sigma mask (u16 x 256 each)
-    L.stage = L.gd + kMaxDfas * (uint32_t)sizeof(GDfa);
+    L.stage = L.jmap + 1024;  // byte -> joint class, joint class -> outside-Sigma mask (u16 x 256 each)
     L.lmap = L.stage + 2 * stage_bytes;
     L.linit = L.lmap + kGThreads * K * 2;
     L.vmap = L.linit + kGThreads * K * 2;
@@ -278,7 +277,10 @@ __host__ __device__ inline GSmem g_layout(uint32_t tbytes, uint32_t K, uint32_t 
     L.items = L.vdfa + g_align16(vcap_sum);
     L.chunks = L.items + kGThreads * (uint32_t)sizeof(GItem);
     L.misc = L.chunks + kMaxTileChunks * (uint32_t)sizeof(GChunk);
-    L.total = L.misc + 64 * 4;
+    // last: the descriptors and misc words outlive the tiles (the combine uses
+    // everything below misc as its buffer)
+    L.gd = L.misc + 64 * 4;
+    L.total = L.gd + kMaxDfas * (uint32_t)sizeof(GDfa);
     return L;
 }
 
@@ -400,34 +402,39 @@ __device__ __forceinline__ uint32_t g_block_scan(uint32_t v, uint32_t* tmp) {
 
 // Eq. (8) for every DFA of the group, by the last CTA to finish: each DFA's
 // final state is q0 pushed through the CTA maps in CTA order (CTAs without a
-// share published nothing and are skipped).  The maps are staged through
-// shared memory (buf, buf_bytes) in batches of CTAs so the dependent walks
-// run at shared-memory latency; thread g walks DFA g.
+// share published nothing and are skipped).  The maps (rows b * G + g of
+// seg_stride entries, b-major) are staged through shared memory (buf,
+// buf_bytes: at least one row) in batches of consecutive rows, so the
+// dependent walks run at shared-memory latency; thread g walks DFA g through
+// the rows of each batch that belong to it, in order of b.
 __device__ void g_combine(const GPlan& p, const GDfa* gd, uint8_t* buf, uint32_t buf_bytes,
                           uint32_t* cur) {
     const uint32_t tid = threadIdx.x;
     if (tid < p.G) cur[tid] = gd[tid].q0;
-    // one staged CTA = G rows of seg_stride entries (seg_stride is a multiple of 8)
-    const uint32_t per_cta = p.G * p.seg_stride * 2u;
-    uint32_t nb = buf_bytes / per_cta;
-    if (nb == 0) nb = 1;  // host guarantees buf_bytes >= per_cta
+    const uint32_t row_bytes = p.seg_stride * 2u;   // a multiple of 16
+    const uint32_t rows = p.grid * p.G;
+    uint32_t per = buf_bytes / row_bytes;
+    if (per == 0) per = 1;  // the host guarantees buf_bytes >= row_bytes
+    const uint32_t vec_row = row_bytes / 16u;
     __syncthreads();
-    for (uint32_t b0 = 0; b0 < p.grid; b0 += nb) {
-        const uint32_t b1 = min(p.grid, b0 + nb);
-        const uint32_t vec = (b1 - b0) * per_cta / 16u;
-        const uint4* src = reinterpret_cast<const uint4*>(p.seg_maps + (size_t)b0 * p.G * p.seg_stride);
+    for (uint32_t r0 = 0; r0 < rows; r0 += per) {
+        const uint32_t r1 = min(rows, r0 + per);
+        const uint4* src = reinterpret_cast<const uint4*>(p.seg_maps + (size_t)r0 * p.seg_stride);
         uint4* dst = reinterpret_cast<uint4*>(buf);
-        for (uint32_t i = tid; i < vec; i += kGThreads) {
-            const uint32_t cta = b0 + i / (per_cta / 16u);
+        for (uint32_t i = tid; i < (r1 - r0) * vec_row; i += kGThreads) {
+            const uint32_t cta = (r0 + i / vec_row) / p.G;
             if (p.share[cta] < p.share[cta + 1]) dst[i] = __ldcg(src + i);
         }
         __syncthreads();
         if (tid < p.G) {
             uint32_t s = cur[tid];
-            const uint16_t* rows = reinterpret_cast<const uint16_t*>(buf);
-            for (uint32_t b = b0; b < b1; ++b) {
+            const uint16_t* m = reinterpret_cast<const uint16_t*>(buf);
+            // rows r of this batch with r % G == tid, in increasing r (hence b)
+            uint32_t r = r0 + (tid + p.G - r0 % p.G) % p.G;
+            for (; r < r1; r += p.G) {
+                const uint32_t b = r / p.G;
                 if (p.share[b] >= p.share[b + 1]) continue;
-                const uint32_t nx = rows[((size_t)(b - b0) * p.G + tid) * p.seg_stride + s];
+                const uint32_t nx = m[(size_t)(r - r0) * p.seg_stride + s];
                 if (GRP_OK(nx < gd[tid].qe, p.err + tid)) s = nx;
             }
             cur[tid] = s;
@@ -690,8 +697,8 @@ __global__ void __launch_bounds__(kGThreads, 2) k_group_match(GPlan p) {
     __syncthreads();
     if (misc[GM_LAST]) {
         __threadfence();
-        // everything below the descriptors is free now
-        g_combine(p, gd, sm, L.gd, misc + GM_CUR);
+        // everything below the misc words is free now
+        g_combine(p, gd, sm, L.misc, misc + GM_CUR);
     }
 }
 
@@ -825,7 +832,7 @@ int plan_launch(const dfa_group_s* g, uint64_t n, const dfa_group_opts_t* o, GLa
         }
     if (!ctas) return DFA_EINVAL;
     const GSmem L = g_layout(g->tbytes, K, g->vcap_sum, stage);
-    if (L.gd < g->G * g->seg_stride * 2u) return DFA_EINVAL;
+    if (L.misc < g->seg_stride * 2u) return DFA_EINVAL;  // the combine stages one map row at least
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick(K, g->sb), kGThreads, L.total) !=
             cudaSuccess ||
@@ -840,6 +847,7 @@ int plan_launch(const dfa_group_s* g, uint64_t n, const dfa_group_opts_t* o, GLa
         const double mean = std::max(1.0, g->mean_slots_by_k[k_index(K)]);
         const double want_p = (double)grid * kGThreads * kTilesPerCta * 0.9 / mean;
         P = std::min<uint64_t>((uint64_t)want_p, n / kMinChunk);
+        P = std::min<uint64_t>(P, kMaxChunks);
         P = std::max<uint64_t>(P, (n + 0x7FFFFFFFull - 1) / 0x7FFFFFFFull);
         P = std::max<uint64_t>(P, 1);
     }

@@ -191,6 +191,27 @@ def test_group_async_reuse_and_events(dm, protein_group):
                 assert s_ == es and (s_ != 0 or (fs, acc) == (efs, eacc))
 
 
+def test_group_sixteen_dfas(dm):
+    """The largest group: 16 DFAs, one of 2000 states (the combine stages
+    the CTA maps in batches that split a CTA's 16 rows); answers and chunk maps
+    against the oracle."""
+    import torch
+    specs = gen.protein_group_dfas(12, tuple(range(8, 68, 4))) + gen.protein_group_dfas(13, (2000,))
+    assert len(specs) == 16
+    g = dm.Group([dm.Dfa.from_spec(s) for s in specs])
+    assert g.info().max_states_ext == 2001 and g.info().state_bytes == 2
+    data = gen.protein_text(79, 500_000)
+    dev = torch.from_numpy(data).cuda()
+    for P in (0, 1, 5, 500):
+        _check(g, specs, dev, data, num_chunks=P)
+    maps, fs = g.chunk_maps(dev[:30_000], num_chunks=6)
+    starts = oracle.chunk_starts(30_000, 6, 1)
+    for i in (0, 7, 15):
+        st, efs, _, want = oracle.Dfa.from_spec(specs[i]).chunked(data[:30_000], starts, want_maps=True)
+        assert st == 0 and fs[i] == efs
+        assert np.array_equal(maps[i, :, :specs[i].num_states + 1].astype(np.uint32), want), i
+
+
 def test_group_autotune(dm):
     """The tuner keeps one of the candidates as the group's default; answers
     with the tuned default equal the oracle's."""
