@@ -135,7 +135,9 @@ uint32_t test_window(const dfa_match_opts_t* o, uint64_t n, uint32_t P, uint32_t
     const uint64_t quarter = n / ((uint64_t)m + P - 1) / 4;
     return (uint32_t)std::min<uint64_t>(w, quarter);
 }
-inline uint32_t seg_stride_for(uint32_t qe_max) { return (qe_max + 1) & ~1u; }
+// Entries per segment map: |Q|+1 rounded up to 8, so every map starts on a
+// 16-byte boundary (the combine stages them with 16-byte loads).
+inline uint32_t seg_stride_for(uint32_t qe_max) { return (qe_max + 7) & ~7u; }
 
 // Bytes of a shared-memory DFA's table image in k_match's shared memory: its
 // byte rows when it has them, else its class-major table.

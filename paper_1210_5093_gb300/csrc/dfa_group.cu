@@ -404,27 +404,38 @@ __device__ __forceinline__ uint32_t g_block_scan(uint32_t v, uint32_t* tmp) {
 // final state is q0 pushed through the CTA maps in CTA order (CTAs without a
 // share published nothing and are skipped).  The maps (rows b * G + g of
 // seg_stride entries, b-major) are staged through shared memory (buf,
-// buf_bytes: at least one row) in batches of consecutive rows, so the
-// dependent walks run at shared-memory latency; thread g walks DFA g through
-// the rows of each batch that belong to it, in order of b.
+// buf_bytes: at least one row and 1 KB of flags) in batches of consecutive
+// rows, so the dependent walks run at shared-memory latency; thread g walks
+// DFA g through the rows of each batch that belong to it, in order of b.
 __device__ void g_combine(const GPlan& p, const GDfa* gd, uint8_t* buf, uint32_t buf_bytes,
                           uint32_t* cur) {
     const uint32_t tid = threadIdx.x;
     if (tid < p.G) cur[tid] = gd[tid].q0;
     const uint32_t row_bytes = p.seg_stride * 2u;   // a multiple of 16
     const uint32_t rows = p.grid * p.G;
-    uint32_t per = buf_bytes / row_bytes;
-    if (per == 0) per = 1;  // the host guarantees buf_bytes >= row_bytes
+    // rows per batch; the last kBatchMax bytes of buf hold the batch's valid flags
+    constexpr uint32_t kBatchMax = 1024;
+    uint32_t per = (buf_bytes - kBatchMax) / row_bytes;
+    per = per < 1 ? 1 : (per > kBatchMax ? kBatchMax : per);  // the host guarantees room for one row
+    uint8_t* valid = buf + buf_bytes - kBatchMax;
     const uint32_t vec_row = row_bytes / 16u;
     __syncthreads();
     for (uint32_t r0 = 0; r0 < rows; r0 += per) {
-        const uint32_t r1 = min(rows, r0 + per);
-        const uint4* src = reinterpret_cast<const uint4*>(p.seg_maps + (size_t)r0 * p.seg_stride);
-        uint4* dst = reinterpret_cast<uint4*>(buf);
-        for (uint32_t i = tid; i < (r1 - r0) * vec_row; i += kGThreads) {
-            const uint32_t cta = (r0 + i / vec_row) / p.G;
-            if (p.share[cta] < p.share[cta + 1]) dst[i] = __ldcg(src + i);
+        const uint32_t r1 = min(rows, r0 + per), total = (r1 - r0) * vec_row;
+        for (uint32_t r = r0 + tid; r < r1; r += kGThreads) {
+            const uint32_t b = r / p.G;
+            valid[r - r0] = p.share[b] < p.share[b + 1] ? 1 : 0;
         }
+        __syncthreads();
+        const uint4* src = reinterpret_cast<const uint4*>(p.seg_maps + (size_t)r0 * p.seg_stride);
+        const uint32_t dst = g_sa(buf);
+        // asynchronous 16-byte global-to-shared copies: all of a thread's
+        // copies in flight at once, none of the data in registers
+        for (uint32_t i = tid; i < total; i += kGThreads)
+            if (valid[i / vec_row])
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             :: "r"(dst + 16u * i), "l"(src + i) : "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         if (tid < p.G) {
             uint32_t s = cur[tid];
@@ -432,8 +443,7 @@ __device__ void g_combine(const GPlan& p, const GDfa* gd, uint8_t* buf, uint32_t
             // rows r of this batch with r % G == tid, in increasing r (hence b)
             uint32_t r = r0 + (tid + p.G - r0 % p.G) % p.G;
             for (; r < r1; r += p.G) {
-                const uint32_t b = r / p.G;
-                if (p.share[b] >= p.share[b + 1]) continue;
+                if (!valid[r - r0]) continue;  // a CTA without a share published nothing
                 const uint32_t nx = m[(size_t)(r - r0) * p.seg_stride + s];
                 if (GRP_OK(nx < gd[tid].qe, p.err + tid)) s = nx;
             }
@@ -832,7 +842,7 @@ int plan_launch(const dfa_group_s* g, uint64_t n, const dfa_group_opts_t* o, GLa
         }
     if (!ctas) return DFA_EINVAL;
     const GSmem L = g_layout(g->tbytes, K, g->vcap_sum, stage);
-    if (L.misc < g->seg_stride * 2u) return DFA_EINVAL;  // the combine stages one map row at least
+    if (L.misc < g->seg_stride * 2u + 1024u) return DFA_EINVAL;  // the combine stages one map row at least
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick(K, g->sb), kGThreads, L.total) !=
             cudaSuccess ||

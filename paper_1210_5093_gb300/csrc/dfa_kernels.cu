@@ -1071,33 +1071,50 @@ __device__ void tile_chains(const DevDfa& d, const ChunkMeta* meta, int nch, uin
     }
 }
 
-// Stages segment maps i0 .. i0+nb-1 of test t (CTAs b0 + i0 + j) into sm,
-// words u32 words each; a CTA without a share contributes the identity.
+// Stages segment maps i0 .. i0+nb-1 of test t (CTAs b0 + i0 + j) into sm, vw
+// 16-byte vectors each (a segment map is seg_stride entries, a multiple of 8);
+// a CTA without a share contributes the identity.  `valid` (nb bytes of shared
+// memory) first records which CTAs hold a part of the test; the maps are then
+// copied with asynchronous 16-byte global-to-shared copies, so every thread
+// has all of its copies in flight at once and holds none of the data in
+// registers.  The caller's barrier after the call publishes the stage.
 __device__ __forceinline__ void stage_seg_maps(const LaunchPlan& lp, uint32_t t, uint32_t b0,
-                                               uint32_t i0, uint32_t nb, uint32_t words,
-                                               uint32_t* sm) {
-    for (uint32_t k = threadIdx.x; k < nb * words; k += kThreads) {
-        const uint32_t j = k / words, w = k - j * words;
-        const uint32_t cb = b0 + i0 + j;
+                                               uint32_t i0, uint32_t nb, uint32_t vw, uint4* sm,
+                                               uint8_t* valid) {
+    for (uint32_t j = threadIdx.x; j < nb; j += kThreads) {
         // a CTA between the test's first and last CTA either holds a part
         // of it or got no share at all (then its map is the identity)
-        if (__ldcg(lp.cta_range + 2 * cb) == __ldcg(lp.cta_range + 2 * cb + 1)) {
-            sm[j * words + w] = (2 * w) | ((2 * w + 1) << 16);
-            continue;
-        }
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(
-            lp.seg_vals + (size_t)(cb + t) * lp.seg_stride);
-        sm[j * words + w] = __ldcg(src + w);
+        const uint32_t cb = b0 + i0 + j;
+        valid[j] = __ldcg(lp.cta_range + 2 * cb) != __ldcg(lp.cta_range + 2 * cb + 1) ? 1 : 0;
     }
+    __syncthreads();
+    const uint32_t total = nb * vw;
+    for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
+        const uint32_t j = k / vw, w = k - j * vw;
+        if (valid[j]) {
+            const uint4* src = reinterpret_cast<const uint4*>(
+                lp.seg_vals + (size_t)(b0 + i0 + j + t) * lp.seg_stride) + w;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                         :: "r"(sa(sm + k)), "l"(src) : "memory");
+        } else {
+            const uint32_t e = 8 * w;  // entries e .. e+7 of the identity
+            sm[k] = make_uint4(e | ((e + 1) << 16), (e + 2) | ((e + 3) << 16),
+                               (e + 4) | ((e + 5) << 16), (e + 6) | ((e + 7) << 16));
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
+
+// Shared memory a combine keeps for the valid flags of one batch of maps.
+constexpr uint32_t kCombineBatchMax = 1024;
 
 constexpr uint32_t kMapStatesPerThread = (kMaxSmallQe + kThreads - 1) / kThreads;
 
 // Map test: compose the whole segment maps (Eq. 9) for every state at once;
 // thread x follows states x, x + kThreads, ... through the maps in order.
 __device__ void combine_test_map(const LaunchPlan& lp, uint32_t t, const DevTest& tt,
-                                 const DevDfa& d, uint32_t b0, uint32_t nseg, uint32_t* sm,
-                                 uint32_t per, uint32_t words) {
+                                 const DevDfa& d, uint32_t b0, uint32_t nseg, uint4* sm,
+                                 uint8_t* valid, uint32_t per, uint32_t vw) {
     const uint32_t qe = d.qe;
     if (qe > kMapStatesPerThread * kThreads) {  // the host never pipelines such DFAs
         if (threadIdx.x == 0) {
@@ -1114,13 +1131,13 @@ __device__ void combine_test_map(const LaunchPlan& lp, uint32_t t, const DevTest
     for (uint32_t i0 = 0; i0 < nseg; i0 += per) {
         const uint32_t nb = min(per, nseg - i0);
         __syncthreads();
-        stage_seg_maps(lp, t, b0, i0, nb, words, sm);
+        stage_seg_maps(lp, t, b0, i0, nb, vw, sm, valid);
         __syncthreads();
         const uint16_t* m = reinterpret_cast<const uint16_t*>(sm);
         for (uint32_t j = 0; j < nb; ++j) {
 #pragma unroll
             for (uint32_t i = 0; i < kMapStatesPerThread; ++i)
-                if (cur[i] < qe) cur[i] = m[(size_t)j * 2 * words + cur[i]];
+                if (cur[i] < qe) cur[i] = m[(size_t)j * 8 * vw + cur[i]];
         }
     }
     uint16_t* out = lp.maps + (size_t)tt.out * lp.map_stride;
@@ -1152,15 +1169,18 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
     const DevDfa& d = lp.dfas[tt.dfa];
     const uint32_t b0 = __ldcg(lp.first_cta + t), b1 = __ldcg(lp.last_cta + t);
     const uint32_t nseg = b1 - b0 + 1;
-    const uint32_t qe = d.qe;
-    const uint32_t words = (qe + 1) / 2;  // u32 words per map
-    const uint32_t per = buf_bytes / (4 * words);
-    uint32_t* sm = reinterpret_cast<uint32_t*>(buf);
+    [[maybe_unused]] const uint32_t qe = d.qe;  // (read by the debug build's checks)
+    const uint32_t vw = lp.seg_stride / 8;  // 16-byte vectors per map
+    // maps per batch; the last kCombineBatchMax bytes of buf hold the batch's valid flags
+    const uint32_t per = buf_bytes > kCombineBatchMax
+                             ? min(kCombineBatchMax, (buf_bytes - kCombineBatchMax) / (16 * vw)) : 0u;
+    uint4* sm = reinterpret_cast<uint4*>(buf);
+    uint8_t* valid = buf + buf_bytes - kCombineBatchMax;
     // a continuation segment starts from the previous segment's final state;
     // that launch ran earlier on the same stream, so its result is complete
     const bool cont = (tt.flags & kTestCont) != 0;
     if (tt.flags & kTestMap) {
-        combine_test_map(lp, t, tt, d, b0, nseg, sm, per, words);
+        combine_test_map(lp, t, tt, d, b0, nseg, sm, valid, per, vw);
         return;
     }
     if (threadIdx.x == 0) *cell = cont ? lp.results[tt.out].final_state : d.q0;
@@ -1178,13 +1198,13 @@ __device__ void combine_test(const LaunchPlan& lp, uint32_t t, uint8_t* buf, uin
     for (uint32_t i0 = 0; i0 < nseg && per; i0 += per) {
         const uint32_t nb = min(per, nseg - i0);
         __syncthreads();
-        stage_seg_maps(lp, t, b0, i0, nb, words, sm);
+        stage_seg_maps(lp, t, b0, i0, nb, vw, sm, valid);
         __syncthreads();
         if (threadIdx.x == 0) {
             uint32_t s = *cell;
             const uint16_t* m = reinterpret_cast<const uint16_t*>(sm);
             for (uint32_t j = 0; j < nb; ++j) {
-                s = m[(size_t)j * 2 * words + s];
+                s = m[(size_t)j * 8 * vw + s];
                 if (!DFAM_OK(s < qe, lp.test_err + t)) s = 0;
             }
             *cell = s;
