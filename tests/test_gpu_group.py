@@ -191,6 +191,54 @@ def test_group_async_reuse_and_events(dm, protein_group):
                 assert s_ == es and (s_ != 0 or (fs, acc) == (efs, eacc))
 
 
+def _random_group(case):
+    """1-16 random DFAs over the letters a-h: each maps a random subset of them
+    (at least one) onto its symbols, so some letters are outside some DFAs'
+    Sigma; random sizes, missing delta entries and accepting states."""
+    u = gen.unit(gen.draws(gen.key(900 + case, 1), 64))
+    G = 1 + int(u[0] * 16)
+    specs = []
+    for i in range(G):
+        Q = 1 + int(u[1 + i] ** 2 * 300)
+        m = np.full(256, 0xFF, dtype=np.uint8)
+        letters = [c for j, c in enumerate(b"abcdefgh") if u[17 + (i + j) % 40] < 0.85 or j == 0]
+        S = 1 + int(u[20 + i] * len(letters))
+        for j, c in enumerate(letters):
+            m[c] = j % S
+        specs.append(gen.random_dfa(1000 * case + i, Q, S, num_finals=max(1, Q // 4),
+                                    missing=0.1 * u[40 + i], byte_to_symbol=m))
+    return specs, u
+
+
+def test_group_random(dm):
+    """Random groups, inputs, chunk counts and K against the oracle."""
+    import torch
+    done = 0
+    for case in range(30):
+        specs, u = _random_group(case)
+        try:
+            g = dm.Group([dm.Dfa.from_spec(s) for s in specs])
+        except dm.DfaError as e:          # limits of a group (sets of one chunk, ...)
+            assert e.status == dm.EINVAL
+            continue
+        n = int(u[60] * 200_000)
+        x = (gen.uniform_bytes(case, n) % 8 + ord("a")).astype(np.uint8)
+        if u[61] < 0.3 and n:
+            x[int(u[62] * n)] = ord("z")     # outside every DFA's Sigma
+        dev = torch.from_numpy(x).cuda()
+        want = _expect(specs, x)
+        for P in (0, 1 + int(u[63] * 3000)):
+            for K in (0, 1, 2, 4, 8, 16):
+                try:
+                    got = g.match(dev, num_chunks=P, states_per_thread=K)
+                except dm.DfaError as e:     # K too small for one chunk's sets
+                    assert e.status == dm.EINVAL and K > 0
+                    continue
+                assert got == want, (case, P, K)
+                done += 1
+    assert done > 100
+
+
 def test_group_sixteen_dfas(dm):
     """The largest group: 16 DFAs, one of 2000 states (the combine stages
     the CTA maps in batches that split a CTA's 16 rows); answers and chunk maps
