@@ -715,6 +715,10 @@ def main():
     ap.add_argument("--boundary-window", type=int, default=0,
                     help="Sec. 4.2 boundary placement window in bytes for the headline "
                          "(0: the starts of Eqs. 6-7, the paper's partition)")
+    ap.add_argument("--lookahead", type=int, default=1,
+                    help="reverse-lookahead symbols r of the headline test (profiling runs; "
+                         "1 = Algorithm 3 as contracted, 2-8 = the sets of Eq. 13; the extra "
+                         "legs and configs are skipped when r != 1)")
     ap.add_argument("--tuning", default="",
                     help="K,tiles_per_cta,ctas_per_sm[,grid_waves] instead of the autotuner "
                          "(profiling runs; for --workload group: K,ctas_per_sm)")
@@ -789,19 +793,22 @@ def main():
     dev = torch.from_numpy(w.data).cuda()
     tuning = None
     bw = args.boundary_window
+    la = args.lookahead
+    if la != 1:
+        args.no_mix = args.no_configs = True
     if args.tuning:
         k, tpc, cps, *gw = (int(x) for x in args.tuning.split(","))
         d.set_tuning(states_per_thread=k, tiles_per_cta=tpc, ctas_per_sm=cps, boundary_window=bw,
-                     grid_waves=gw[0] if gw else 0)
+                     grid_waves=gw[0] if gw else 0, lookahead=la)
         tuning = {"states_per_thread": k, "tiles_per_cta": tpc, "ctas_per_sm": cps,
                   "grid_waves": gw[0] if gw else 1, "fixed": True}
     elif not w.num_chunks and not args.no_tune:
         # the library's per-DFA tuner (on at most 1 GiB), before any timing
-        t, _ = d.autotune(dev[: 1 << 30], boundary_window=bw)
+        t, _ = d.autotune(dev[: 1 << 30], boundary_window=bw, lookahead=la)
         tuning = {"states_per_thread": t.states_per_thread, "tiles_per_cta": t.tiles_per_cta,
                   "ctas_per_sm": t.ctas_per_sm, "grid_waves": max(1, t.grid_waves)}
-    P = d.plan_chunks(n, num_chunks=w.num_chunks, boundary_window=bw)
-    ws = torch.empty(d.workspace_size(n, num_chunks=w.num_chunks, boundary_window=bw),
+    P = d.plan_chunks(n, num_chunks=w.num_chunks, boundary_window=bw, lookahead=la)
+    ws = torch.empty(d.workspace_size(n, num_chunks=w.num_chunks, boundary_window=bw, lookahead=la),
                      dtype=torch.uint8, device="cuda")
     out = torch.zeros(12, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
@@ -820,7 +827,7 @@ def main():
         if timed:
             sb[i].record(stream)
         d.match_async(dev, out, ws, stream=stream, num_chunks=w.num_chunks, events=ev,
-                      boundary_window=bw)
+                      boundary_window=bw, lookahead=la)
         if timed:
             se[i].record(stream)
 
@@ -855,14 +862,14 @@ def main():
     pinned = torch.from_numpy(w.data).pin_memory()
     e2e_steps = max(3, min(10, args.steps))
     for _ in range(2):
-        d.match(pinned, boundary_window=bw)
+        d.match(pinned, boundary_window=bw, lookahead=la)
     torch.cuda.synchronize()
     e2e_res = set()
     e2e_calls = []
     gc.disable()   # no interpreter collection inside a timed call
     for _ in range(e2e_steps):
         te = time.perf_counter()
-        e2e_res.add(d.match(pinned, boundary_window=bw))
+        e2e_res.add(d.match(pinned, boundary_window=bw, lookahead=la))
         e2e_calls.append(time.perf_counter() - te)
     gc.enable()
     e2e_s = statistics.median(e2e_calls)   # per call: copies, kernels and the result read
@@ -889,11 +896,11 @@ def main():
         assert e2e_res == {expect}, ("end-to-end answer differs from the oracle", e2e_res, expect)
 
     if rank == 0:
-        W, mean_I = lookups_per_launch(dm, d, dev, n, w.num_chunks, 1, bw)
+        W, mean_I = lookups_per_launch(dm, d, dev, n, w.num_chunks, la, bw)
         k_avg_s = statistics.mean(k_ms) / 1e3
         achieved = W / k_avg_s
         info = d.info()
-        traffic = _traffic_record(w.name, bw)
+        traffic = _traffic_record(w.name, bw) if la == 1 else None
         fs, acc, st = res_timed
         line = {
             "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world,
@@ -902,7 +909,10 @@ def main():
             "dtype": _dtype(w.spec), "data": "synthetic",
             "config": {"workload": w.name, "states": w.spec.num_states,
                        "classes": int(info.num_classes), "input_bytes": n, "chunks": int(P),
-                       "lookahead": 1, "algorithm": "Algorithm 3, one reverse-lookahead symbol",
+                       "lookahead": la,
+                       "algorithm": ("Algorithm 3, one reverse-lookahead symbol" if la == 1 else
+                                     "Algorithm 3 with the %d-symbol sets of Eq. 13" % la
+                                     if la > 1 else "Algorithm 2 (every chunk from all of Q)"),
                        "i_max": int(info.i_max), "gamma": round(info.gamma, 4),
                        "chunk_starts": ("Sec. 4.2 placement within %d bytes of Eqs. 6-7 (%s)"
                                         % (bw, OUTSIDE) if bw else "Eqs. 6-7"),
@@ -928,7 +938,8 @@ def main():
                     "api": "dfa_match (pinned host buffer)", "h2d_copy_gbs": round(h2d_gbs, 1),
                     "calls": e2e_steps, "statistic": "median call time",
                     "call_ms": [round(x * 1e3, 2) for x in e2e_calls]},
-            "gpu_launches": d.num_kernels(n, num_chunks=w.num_chunks, boundary_window=bw) * args.steps,
+            "gpu_launches": d.num_kernels(n, num_chunks=w.num_chunks, boundary_window=bw,
+                                          lookahead=la) * args.steps,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"]},
             "result": {"final_state": fs, "accept": acc, "status": st},
