@@ -455,8 +455,9 @@ typedef struct {
     uint32_t joint_classes;     /* J                                                  */
     uint32_t state_bytes;       /* joint-table entry size: 1 if every |Q|+1 <= 256, else 2 */
     uint32_t states_per_thread; /* default K (chains one thread advances together):
-                                   the compiler's rule on the mean set size, or what
-                                   dfa_group_autotune chose                             */
+                                   for one DFA the compiler's rule on its mean set size,
+                                   for several at most 2 (raised until one chunk's sets
+                                   fit 512 threads), or what dfa_group_autotune chose   */
     uint32_t ctas_per_sm;       /* default thread blocks per SM (0: 2 where shared
                                    memory allows), or what dfa_group_autotune chose    */
     uint32_t max_states_ext;    /* largest |Q|+1 of the group: the row stride of
