@@ -162,9 +162,10 @@ __device__ __forceinline__ uint32_t g_lookahead(const GPlan& p, const uint16_t* 
 // One CTA.  Thread t takes chunks [P t / 1024, P (t+1) / 1024): their thread
 // slots (sum over the DFAs of ceil(|I|/K), at least 1 each) times their
 // length is their work; a block scan gives each chunk's work prefix, and
-// chunk k goes to CTA share floor(mid2 G / (2 W)), mid2 being twice its work
-// midpoint, so every CTA gets W / G +- one chunk.  The shares are monotone in
-// k, hence contiguous; share[b] is the first chunk of share b.
+// chunk k goes to CTA share floor(mid2 * grid / (2 W)), mid2 being twice its
+// work midpoint, so every CTA gets W / grid +- one chunk.  The shares are
+// monotone in k (the rounding of the product is monotone too), hence
+// contiguous; share[b] is the first chunk of share b.
 __global__ void __launch_bounds__(kPlanThreads) k_group_plan(GPlan p) {
     __shared__ uint16_t s_jmap[256];
     __shared__ unsigned long long s_w[kPlanThreads / 32], s_l[kPlanThreads / 32];
