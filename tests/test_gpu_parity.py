@@ -70,6 +70,46 @@ def test_random_dfas_many_chunkings(dm, seed):
             _check(dm, d, spec, data[:n], num_chunks=P)
 
 
+def test_random_options(dm):
+    """Random DFAs, inputs and launch options together: sizes 1-700 states over
+    1-40 symbols on random byte subsets, missing entries, bytes outside Sigma,
+    chunk counts, multiplicities, lookahead depths 0-4, placement windows and
+    tunings, each answer against the oracle (Algorithm 1)."""
+    done = 0
+    for case in range(40):
+        u = gen.unit(gen.draws(gen.key(7000 + case, 3), 32))
+        Q = 1 + int(u[0] ** 2 * 700)
+        S = 1 + int(u[1] * 40)
+        m = np.full(256, 0xFF, dtype=np.uint8)
+        alphabet = gen.permutation(gen.key(7000 + case, 4), 256)[: S + int(u[2] * 3 * S)]
+        m[alphabet] = np.arange(len(alphabet)) % S
+        spec = gen.random_dfa(7100 + case, Q, S, num_finals=max(1, Q // 3),
+                              missing=0.15 * u[3], byte_to_symbol=m)
+        d = dm.Dfa.from_spec(spec)
+        n = int(u[4] ** 2 * 400_000)
+        x = alphabet[gen.below(gen.draws(gen.key(7200 + case, 5), n), len(alphabet))].astype(np.uint8)
+        if u[5] < 0.25 and n:
+            outside = np.nonzero(m == 0xFF)[0]
+            x[int(u[6] * n)] = outside[int(u[7] * len(outside))]
+        if u[8] < 0.5:
+            try:      # a K too small for the DFA's largest set is refused (DFA_EINVAL)
+                d.set_tuning(states_per_thread=[2, 4, 8, 16][int(u[9] * 4)],
+                             tiles_per_cta=1 + int(u[10] * 16), ctas_per_sm=1 + int(u[11] * 3))
+            except dm.DfaError as e:
+                assert e.status == dm.EINVAL
+        for trial in range(4):
+            v = gen.unit(gen.draws(gen.key(7300 + case, 6 + trial), 8))
+            kw = {"num_chunks": 0 if v[0] < 0.4 else 1 + int(v[1] ** 2 * 5000),
+                  "lookahead": int(v[2] * 5) if Q < 4096 else 1}
+            if kw["lookahead"] >= 1 and v[3] < 0.3:
+                kw["boundary_window"] = [1, 16, 256, 4096][int(v[4] * 4)]
+            if v[5] < 0.3:
+                kw["multiplicity"] = 1 + int(v[6] * 8)
+            _check(dm, d, spec, x, **kw)
+            done += 1
+    assert done == 160
+
+
 @pytest.mark.parametrize("Q,S,missing", [(16, 256, 0.0), (15, 5, 0.2), (8, 3, 0.0),
                                          (3, 2, 0.3), (12, 40, 0.05)])
 def test_byte_row_dfas(dm, Q, S, missing):
