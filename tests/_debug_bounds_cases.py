@@ -80,6 +80,25 @@ def main():
     d = dm.Dfa.from_spec(w.spec)
     d.set_tuning(host_segment_bytes=8 << 20)
     check(d, w.spec, torch.from_numpy(w.data).pin_memory())
+    # random DFAs with random launch options (as the random-options parity test)
+    for case in range(20):
+        u = gen.unit(gen.draws(gen.key(7000 + case, 3), 32))
+        Q, S = 1 + int(u[0] ** 2 * 700), 1 + int(u[1] * 40)
+        m = np.full(256, 0xFF, dtype=np.uint8)
+        alphabet = gen.permutation(gen.key(7000 + case, 4), 256)[: S + int(u[2] * 3 * S)]
+        m[alphabet] = np.arange(len(alphabet)) % S
+        spec = gen.random_dfa(7100 + case, Q, S, num_finals=max(1, Q // 3),
+                              missing=0.15 * u[3], byte_to_symbol=m)
+        d = dm.Dfa.from_spec(spec)
+        n = int(u[4] ** 2 * 400_000)
+        x = alphabet[gen.below(gen.draws(gen.key(7200 + case, 5), n), len(alphabet))].astype(np.uint8)
+        for trial in range(3):
+            v = gen.unit(gen.draws(gen.key(7300 + case, 6 + trial), 8))
+            kw = {"num_chunks": 0 if v[0] < 0.4 else 1 + int(v[1] ** 2 * 5000),
+                  "lookahead": int(v[2] * 5)}
+            if kw["lookahead"] >= 1 and v[3] < 0.3:
+                kw["boundary_window"] = [1, 16, 256, 4096][int(v[4] * 4)]
+            check(d, spec, x, **kw)
     # groups of DFAs sharing one stage: protein DFAs at several K and chunk
     # counts, and a group whose byte-classed DFA has every byte in Sigma while
     # its protein DFA does not (a byte outside the letters fails only the latter)
