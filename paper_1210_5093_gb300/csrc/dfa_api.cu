@@ -637,12 +637,16 @@ extern "C" {
 
 int dfa_create(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0, const uint32_t* finals,
                uint32_t nf, const uint8_t* b2s, dfa_t** out) {
-    return create_common(Q, S, delta, q0, finals, nf, b2s, true, out);
+    return dfam::no_throw([&]() -> int {
+        return create_common(Q, S, delta, q0, finals, nf, b2s, true, out);
+    });
 }
 
 int dfa_create_host(uint32_t Q, uint32_t S, const int32_t* delta, uint32_t q0,
                     const uint32_t* finals, uint32_t nf, const uint8_t* b2s, dfa_t** out) {
-    return create_common(Q, S, delta, q0, finals, nf, b2s, false, out);
+    return dfam::no_throw([&]() -> int {
+        return create_common(Q, S, delta, q0, finals, nf, b2s, false, out);
+    });
 }
 
 void dfa_destroy(dfa_t* d) {
@@ -832,11 +836,13 @@ static int autotune_r(dfa_t* d, const dfa_match_opts_t* base, const uint8_t* dev
 
 int dfa_get_tuning(const dfa_t* d, dfa_tuning_t* out) { return get_tuning_r(d, 1, out); }
 
-int dfa_set_tuning(dfa_t* d, const dfa_tuning_t* t) { return set_tuning_r(d, 1, t); }
+int dfa_set_tuning(dfa_t* d, const dfa_tuning_t* t) { return dfam::no_throw([&]() -> int { return set_tuning_r(d, 1, t); }); }
 
 int dfa_autotune(dfa_t* d, const uint8_t* dev_sample, uint64_t len, void* stream,
                  dfa_tuning_t* chosen, double* best_ms) {
-    return autotune_r(d, nullptr, dev_sample, len, stream, chosen, best_ms);
+    return dfam::no_throw([&]() -> int {
+        return autotune_r(d, nullptr, dev_sample, len, stream, chosen, best_ms);
+    });
 }
 
 int dfa_get_tuning_opts(const dfa_t* d, const dfa_match_opts_t* opts, dfa_tuning_t* out) {
@@ -845,14 +851,18 @@ int dfa_get_tuning_opts(const dfa_t* d, const dfa_match_opts_t* opts, dfa_tuning
 }
 
 int dfa_set_tuning_opts(dfa_t* d, const dfa_match_opts_t* opts, const dfa_tuning_t* t) {
-    if (!opts_valid(opts)) return DFA_EINVAL;
-    return set_tuning_r(d, opts_slot(opts), t);
+    return dfam::no_throw([&]() -> int {
+        if (!opts_valid(opts)) return DFA_EINVAL;
+        return set_tuning_r(d, opts_slot(opts), t);
+    });
 }
 
 int dfa_autotune_opts(dfa_t* d, const uint8_t* dev_sample, uint64_t len,
                       const dfa_match_opts_t* opts, void* stream, dfa_tuning_t* chosen,
                       double* best_ms) {
-    return autotune_r(d, opts, dev_sample, len, stream, chosen, best_ms);
+    return dfam::no_throw([&]() -> int {
+        return autotune_r(d, opts, dev_sample, len, stream, chosen, best_ms);
+    });
 }
 
 int dfa_class_of_bytes(const dfa_t* d, uint16_t* out) {
@@ -885,137 +895,149 @@ __global__ void k_identity_maps(uint16_t* maps, uint64_t P, uint32_t qe) {
 int dfa_debug_chunk_maps(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
                          const dfa_match_opts_t* opts, uint16_t* maps, uint32_t cap, uint32_t* P,
                          uint32_t* final_state) {
-    if (!P || (len && !dev_str)) return DFA_EINVAL;
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    *P = s.lp.ptot;
-    if (!maps || cap == 0) return DFA_OK;
-    const uint32_t qe = s.lp.qe_max;
-    const uint64_t map_bytes = up(2ull * s.lp.ptot * qe, 256);  // keeps the result 256-byte aligned
-    uint8_t* ws = nullptr;
-    if (cudaMalloc(&ws, s.ws.total + map_bytes + 256) != cudaSuccess) {
-        cudaGetLastError();
-        return DFA_ENOMEM;
-    }
-    uint16_t* dmaps = reinterpret_cast<uint16_t*>(ws + s.ws.total);
-    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(ws + s.ws.total + map_bytes);
-    k_identity_maps<<<1024, 256>>>(dmaps, s.lp.ptot, qe);
-    s.lp.test1.str = dev_str;
-    bind(s.lp, ws, s.ws);
-    s.lp.results = dres;
-    s.lp.dbg_maps = dmaps;
-    rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr);
-    dfa_result_t r{};
-    const uint32_t n = std::min(cap, s.lp.ptot);
-    if (rc == DFA_OK && cudaMemcpy(maps, dmaps, 2ull * n * qe, cudaMemcpyDeviceToHost) != cudaSuccess)
-        rc = DFA_ECUDA;
-    if (rc == DFA_OK && cudaMemcpy(&r, dres, sizeof r, cudaMemcpyDeviceToHost) != cudaSuccess)
-        rc = DFA_ECUDA;
-    cudaFree(ws);
-    if (rc == DFA_OK && final_state) *final_state = r.final_state;
-    if (rc == DFA_OK && r.status != DFA_OK) rc = r.status;
-    return rc;
+    return dfam::no_throw([&]() -> int {
+        if (!P || (len && !dev_str)) return DFA_EINVAL;
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        *P = s.lp.ptot;
+        if (!maps || cap == 0) return DFA_OK;
+        const uint32_t qe = s.lp.qe_max;
+        const uint64_t map_bytes = up(2ull * s.lp.ptot * qe, 256);  // keeps the result 256-byte aligned
+        uint8_t* ws = nullptr;
+        if (cudaMalloc(&ws, s.ws.total + map_bytes + 256) != cudaSuccess) {
+            cudaGetLastError();
+            return DFA_ENOMEM;
+        }
+        uint16_t* dmaps = reinterpret_cast<uint16_t*>(ws + s.ws.total);
+        dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(ws + s.ws.total + map_bytes);
+        k_identity_maps<<<1024, 256>>>(dmaps, s.lp.ptot, qe);
+        s.lp.test1.str = dev_str;
+        bind(s.lp, ws, s.ws);
+        s.lp.results = dres;
+        s.lp.dbg_maps = dmaps;
+        rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr);
+        dfa_result_t r{};
+        const uint32_t n = std::min(cap, s.lp.ptot);
+        if (rc == DFA_OK && cudaMemcpy(maps, dmaps, 2ull * n * qe, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = DFA_ECUDA;
+        if (rc == DFA_OK && cudaMemcpy(&r, dres, sizeof r, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = DFA_ECUDA;
+        cudaFree(ws);
+        if (rc == DFA_OK && final_state) *final_state = r.final_state;
+        if (rc == DFA_OK && r.status != DFA_OK) rc = r.status;
+        return rc;
+    });
 }
 
 int dfa_match_num_kernels(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, uint32_t* n) {
-    if (!n) return DFA_EINVAL;
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    *n = launch_kernel_count(s.lp.ptot, s.lp.grid, s.lp.dyn != 0, s.lp.bnd != 0);
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!n) return DFA_EINVAL;
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        *n = launch_kernel_count(s.lp.ptot, s.lp.grid, s.lp.dyn != 0, s.lp.bnd != 0);
+        return DFA_OK;
+    });
 }
 
 int dfa_plan_sets(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
                   const dfa_match_opts_t* opts, uint32_t* sizes, uint32_t cap, uint32_t* P) {
-    if (!P || (len && !dev_str)) return DFA_EINVAL;
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    *P = s.lp.ptot;
-    uint8_t* ws = nullptr;
-    if (cudaMalloc(&ws, s.ws.total) != cudaSuccess) { cudaGetLastError(); return DFA_ENOMEM; }
-    s.lp.test1.str = dev_str;
-    bind(s.lp, ws, s.ws);
-    s.lp.results = nullptr;
-    rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr, nullptr, nullptr, true);
-    const uint32_t n = std::min(cap, s.lp.ptot);
-    std::vector<uint16_t> cls(n);
-    std::vector<uint32_t> dyn(n);
-    if (rc == DFA_OK && n) {
-        if (cudaMemcpy(cls.data(), s.lp.chunk_cls, 2ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
-            rc = DFA_ECUDA;
-        if (rc == DFA_OK && s.lp.dyn &&
-            cudaMemcpy(dyn.data(), s.lp.set_size, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
-            rc = DFA_ECUDA;
-    }
-    if (cudaDeviceSynchronize() != cudaSuccess) rc = DFA_ECUDA;
-    cudaFree(ws);
-    if (rc != DFA_OK) return rc;
-    const HostDfa& h = d->h;
-    for (uint32_t k = 0; k < n; ++k)
-        sizes[k] = cls[k] == dyn_set(h.C) ? dyn[k] : h.iset_off[cls[k] + 1] - h.iset_off[cls[k]];
-    return DFA_OK;
-}
-
-int dfa_plan_starts(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
-                    const dfa_match_opts_t* opts, uint64_t* starts, uint32_t cap, uint32_t* P) {
-    if (!P || (len && !dev_str)) return DFA_EINVAL;
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    *P = s.lp.ptot;
-    if (!starts || cap == 0) return DFA_OK;
-    const uint32_t P1 = s.lp.ptot + 1, n = std::min(cap, P1);
-    std::vector<uint64_t> placed;
-    if (s.lp.bnd) {
+    return dfam::no_throw([&]() -> int {
+        if (!P || (len && !dev_str)) return DFA_EINVAL;
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        *P = s.lp.ptot;
         uint8_t* ws = nullptr;
         if (cudaMalloc(&ws, s.ws.total) != cudaSuccess) { cudaGetLastError(); return DFA_ENOMEM; }
         s.lp.test1.str = dev_str;
         bind(s.lp, ws, s.ws);
         s.lp.results = nullptr;
         rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr, nullptr, nullptr, true);
-        placed.resize(s.lp.ptot);
-        if (rc == DFA_OK &&
-            cudaMemcpy(placed.data(), s.lp.starts, 8ull * s.lp.ptot, cudaMemcpyDeviceToHost) != cudaSuccess)
-            rc = DFA_ECUDA;
+        const uint32_t n = std::min(cap, s.lp.ptot);
+        std::vector<uint16_t> cls(n);
+        std::vector<uint32_t> dyn(n);
+        if (rc == DFA_OK && n) {
+            if (cudaMemcpy(cls.data(), s.lp.chunk_cls, 2ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+                rc = DFA_ECUDA;
+            if (rc == DFA_OK && s.lp.dyn &&
+                cudaMemcpy(dyn.data(), s.lp.set_size, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+                rc = DFA_ECUDA;
+        }
         if (cudaDeviceSynchronize() != cudaSuccess) rc = DFA_ECUDA;
         cudaFree(ws);
         if (rc != DFA_OK) return rc;
-    }
-    const DevTest& t = s.lp.test1;
-    for (uint32_t k = 0; k < n; ++k)
-        starts[k] = (k == 0) ? 0 : (k >= t.P ? len : (t.window ? placed[k] : chunk_start(len, t.P, t.m, k)));
-    return DFA_OK;
+        const HostDfa& h = d->h;
+        for (uint32_t k = 0; k < n; ++k)
+            sizes[k] = cls[k] == dyn_set(h.C) ? dyn[k] : h.iset_off[cls[k] + 1] - h.iset_off[cls[k]];
+        return DFA_OK;
+    });
+}
+
+int dfa_plan_starts(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
+                    const dfa_match_opts_t* opts, uint64_t* starts, uint32_t cap, uint32_t* P) {
+    return dfam::no_throw([&]() -> int {
+        if (!P || (len && !dev_str)) return DFA_EINVAL;
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        *P = s.lp.ptot;
+        if (!starts || cap == 0) return DFA_OK;
+        const uint32_t P1 = s.lp.ptot + 1, n = std::min(cap, P1);
+        std::vector<uint64_t> placed;
+        if (s.lp.bnd) {
+            uint8_t* ws = nullptr;
+            if (cudaMalloc(&ws, s.ws.total) != cudaSuccess) { cudaGetLastError(); return DFA_ENOMEM; }
+            s.lp.test1.str = dev_str;
+            bind(s.lp, ws, s.ws);
+            s.lp.results = nullptr;
+            rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr, nullptr, nullptr, true);
+            placed.resize(s.lp.ptot);
+            if (rc == DFA_OK &&
+                cudaMemcpy(placed.data(), s.lp.starts, 8ull * s.lp.ptot, cudaMemcpyDeviceToHost) != cudaSuccess)
+                rc = DFA_ECUDA;
+            if (cudaDeviceSynchronize() != cudaSuccess) rc = DFA_ECUDA;
+            cudaFree(ws);
+            if (rc != DFA_OK) return rc;
+        }
+        const DevTest& t = s.lp.test1;
+        for (uint32_t k = 0; k < n; ++k)
+            starts[k] = (k == 0) ? 0 : (k >= t.P ? len : (t.window ? placed[k] : chunk_start(len, t.P, t.m, k)));
+        return DFA_OK;
+    });
 }
 
 int dfa_match_workspace_size(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts,
                              uint64_t* bytes) {
-    if (!bytes) return DFA_EINVAL;
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    *bytes = s.ws.total;
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!bytes) return DFA_EINVAL;
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        *bytes = s.ws.total;
+        return DFA_OK;
+    });
 }
 
 int dfa_match_async(const dfa_t* d, const uint8_t* dev_str, uint64_t len,
                     const dfa_match_opts_t* opts, dfa_result_t* dev_out, void* ws,
                     uint64_t ws_bytes, void* stream) {
-    if (!dev_out || (len && !dev_str) || !ws) return DFA_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(dev_out) & 3u) || (reinterpret_cast<uintptr_t>(ws) & 255u))
-        return DFA_EINVAL;  // results are 4-byte aligned, the workspace 256-byte aligned
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    if (ws_bytes < s.ws.total) return DFA_ENOSPACE;
-    s.lp.test1.str = dev_str;
-    bind(s.lp, static_cast<uint8_t*>(ws), s.ws);
-    s.lp.results = dev_out;
-    return launch_plan(s.lp, s.kmax, s.smem, static_cast<cudaStream_t>(stream), nullptr,
-                       opts ? opts->match_begin_event : nullptr,
-                       opts ? opts->match_end_event : nullptr);
+    return dfam::no_throw([&]() -> int {
+        if (!dev_out || (len && !dev_str) || !ws) return DFA_EINVAL;
+        if ((reinterpret_cast<uintptr_t>(dev_out) & 3u) || (reinterpret_cast<uintptr_t>(ws) & 255u))
+            return DFA_EINVAL;  // results are 4-byte aligned, the workspace 256-byte aligned
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        if (ws_bytes < s.ws.total) return DFA_ENOSPACE;
+        s.lp.test1.str = dev_str;
+        bind(s.lp, static_cast<uint8_t*>(ws), s.ws);
+        s.lp.results = dev_out;
+        return launch_plan(s.lp, s.kmax, s.smem, static_cast<cudaStream_t>(stream), nullptr,
+                           opts ? opts->match_begin_event : nullptr,
+                           opts ? opts->match_end_event : nullptr);
+    });
 }
 
 // Per-device buffers of the synchronous path (grown on demand, never shrunk).
@@ -1100,12 +1122,14 @@ static int grow_dev(uint8_t** p, uint64_t* cap, uint64_t need) {
 }
 
 int dfa_plan_chunks(const dfa_t* d, uint64_t len, const dfa_match_opts_t* opts, uint32_t* P) {
-    if (!P) return DFA_EINVAL;
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    *P = s.lp.ptot;
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!P) return DFA_EINVAL;
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        *P = s.lp.ptot;
+        return DFA_OK;
+    });
 }
 
 // Host input in segments: segment i is copied on B.cs and matched once its
@@ -1179,45 +1203,47 @@ static int match_pipelined(const dfa_t* d, const uint8_t* str, const std::vector
 
 int dfa_match(const dfa_t* d, const uint8_t* str, uint64_t len, const dfa_match_opts_t* opts,
               dfa_result_t* out) {
-    if (!d || !out || (len && !str)) return DFA_EINVAL;
-    if (!d->on_device) return DFA_EHOSTONLY;
-    bool on_dev = false;
-    if (len) {
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, str) == cudaSuccess)
-            on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-        cudaGetLastError();
-    }
-    Single s;
-    int rc = plan_single(d, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DFA_ECUDA;
-    SyncBuffers& B = g_sync[dev];
-    std::lock_guard<std::mutex> lock(B.mu);
-    std::vector<uint64_t> seg;
-    if (len && !on_dev && !(opts && (opts->num_chunks || opts->multiplicity)) &&
-        d->h.qe <= kMaxSmallQe &&
-        host_segments(len, d->tuning.host_segment_bytes, segment_cap_div(d, opts), &seg))
-        return match_pipelined(d, str, seg, opts, B, out);
-    const uint8_t* use = str;
-    if (len && !on_dev) {
-        if ((rc = grow_dev(&B.str, &B.str_cap, len)) != DFA_OK) return rc;
-        if (cudaMemcpyAsync(B.str, str, len, cudaMemcpyHostToDevice, 0) != cudaSuccess)
-            return DFA_ECUDA;
-        use = B.str;
-    }
-    if ((rc = grow_dev(&B.ws, &B.ws_cap, s.ws.total + 256)) != DFA_OK) return rc;
-    dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(B.ws + s.ws.total);
-    s.lp.test1.str = use;
-    bind(s.lp, B.ws, s.ws);
-    s.lp.results = dres;
-    rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr,
-                     opts ? opts->match_begin_event : nullptr, opts ? opts->match_end_event : nullptr);
-    if (rc == DFA_OK && cudaMemcpy(out, dres, sizeof *out, cudaMemcpyDeviceToHost) != cudaSuccess)
-        rc = DFA_ECUDA;
-    if (rc == DFA_OK && out->status != DFA_OK) rc = out->status;
-    return rc;
+    return dfam::no_throw([&]() -> int {
+        if (!d || !out || (len && !str)) return DFA_EINVAL;
+        if (!d->on_device) return DFA_EHOSTONLY;
+        bool on_dev = false;
+        if (len) {
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, str) == cudaSuccess)
+                on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+            cudaGetLastError();
+        }
+        Single s;
+        int rc = plan_single(d, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DFA_ECUDA;
+        SyncBuffers& B = g_sync[dev];
+        std::lock_guard<std::mutex> lock(B.mu);
+        std::vector<uint64_t> seg;
+        if (len && !on_dev && !(opts && (opts->num_chunks || opts->multiplicity)) &&
+            d->h.qe <= kMaxSmallQe &&
+            host_segments(len, d->tuning.host_segment_bytes, segment_cap_div(d, opts), &seg))
+            return match_pipelined(d, str, seg, opts, B, out);
+        const uint8_t* use = str;
+        if (len && !on_dev) {
+            if ((rc = grow_dev(&B.str, &B.str_cap, len)) != DFA_OK) return rc;
+            if (cudaMemcpyAsync(B.str, str, len, cudaMemcpyHostToDevice, 0) != cudaSuccess)
+                return DFA_ECUDA;
+            use = B.str;
+        }
+        if ((rc = grow_dev(&B.ws, &B.ws_cap, s.ws.total + 256)) != DFA_OK) return rc;
+        dfa_result_t* dres = reinterpret_cast<dfa_result_t*>(B.ws + s.ws.total);
+        s.lp.test1.str = use;
+        bind(s.lp, B.ws, s.ws);
+        s.lp.results = dres;
+        rc = launch_plan(s.lp, s.kmax, s.smem, 0, nullptr,
+                         opts ? opts->match_begin_event : nullptr, opts ? opts->match_end_event : nullptr);
+        if (rc == DFA_OK && cudaMemcpy(out, dres, sizeof *out, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = DFA_ECUDA;
+        if (rc == DFA_OK && out->status != DFA_OK) rc = out->status;
+        return rc;
+    });
 }
 
 }  // extern "C"
@@ -1254,36 +1280,40 @@ extern "C" {
 
 int dfa_batch_prepare(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
                       const uint64_t* lens, const dfa_match_opts_t* opts, dfa_batch_t** out) {
-    if (!out) return DFA_EINVAL;
-    *out = nullptr;
-    dfa_batch_t* b = new (std::nothrow) dfa_batch_t();
-    if (!b) return DFA_ENOMEM;
-    uint64_t total = 0;
-    int rc = prepare_parts(count, dfas, strs, lens, opts, &b->parts, &b->ws_off, &total);
-    if (rc != DFA_OK) {
-        delete b;
-        return rc;
-    }
-    if (cudaMalloc(&b->ws, total) != cudaSuccess) {
-        cudaGetLastError();
-        delete b;
-        return DFA_ENOMEM;
-    }
-    for (size_t i = 0; i < b->parts.size(); ++i) {
-        rc = upload_desc(b->parts[i], b->ws + b->ws_off[i]);
+    return dfam::no_throw([&]() -> int {
+        if (!out) return DFA_EINVAL;
+        *out = nullptr;
+        dfa_batch_t* b = new (std::nothrow) dfa_batch_t();
+        if (!b) return DFA_ENOMEM;
+        uint64_t total = 0;
+        int rc = prepare_parts(count, dfas, strs, lens, opts, &b->parts, &b->ws_off, &total);
         if (rc != DFA_OK) {
-            cudaFree(b->ws);
             delete b;
             return rc;
         }
-    }
-    *out = b;
-    return DFA_OK;
+        if (cudaMalloc(&b->ws, total) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return DFA_ENOMEM;
+        }
+        for (size_t i = 0; i < b->parts.size(); ++i) {
+            rc = upload_desc(b->parts[i], b->ws + b->ws_off[i]);
+            if (rc != DFA_OK) {
+                cudaFree(b->ws);
+                delete b;
+                return rc;
+            }
+        }
+        *out = b;
+        return DFA_OK;
+    });
 }
 
 int dfa_batch_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) {
-    if (!b || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 3u)) return DFA_EINVAL;
-    return launch_parts(b, dev_out, static_cast<cudaStream_t>(stream), b->ev_begin, b->ev_end);
+    return dfam::no_throw([&]() -> int {
+        if (!b || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 3u)) return DFA_EINVAL;
+        return launch_parts(b, dev_out, static_cast<cudaStream_t>(stream), b->ev_begin, b->ev_end);
+    });
 }
 
 int dfa_batch_set_events(dfa_batch_t* b, void* ev_begin, void* ev_end) {
@@ -1294,38 +1324,40 @@ int dfa_batch_set_events(dfa_batch_t* b, void* ev_begin, void* ev_end) {
 }
 
 int dfa_batch_graph_launch(dfa_batch_t* b, dfa_result_t* dev_out, void* stream) {
-    if (!b || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 3u)) return DFA_EINVAL;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (!b->exec || b->graph_out != dev_out) {
-        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
-        cudaStream_t cap = st;
-        bool own = false;
-        if (!cap) {  // the legacy default stream cannot be captured
-            if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return DFA_ECUDA;
-            own = true;
-        }
-        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    return dfam::no_throw([&]() -> int {
+        if (!b || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 3u)) return DFA_EINVAL;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (!b->exec || b->graph_out != dev_out) {
+            if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+            if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+            cudaStream_t cap = st;
+            bool own = false;
+            if (!cap) {  // the legacy default stream cannot be captured
+                if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return DFA_ECUDA;
+                own = true;
+            }
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                if (own) cudaStreamDestroy(cap);
+                return DFA_ECUDA;
+            }
+            int rc = launch_parts(b, dev_out, cap, nullptr, nullptr);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cap, &g);
             if (own) cudaStreamDestroy(cap);
-            return DFA_ECUDA;
+            if (rc != DFA_OK || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return DFA_ECUDA;
+            }
+            if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return DFA_ECUDA;
+            }
+            b->graph = g;
+            b->graph_out = dev_out;
         }
-        int rc = launch_parts(b, dev_out, cap, nullptr, nullptr);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(cap, &g);
-        if (own) cudaStreamDestroy(cap);
-        if (rc != DFA_OK || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            return DFA_ECUDA;
-        }
-        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
-            cudaGraphDestroy(g);
-            return DFA_ECUDA;
-        }
-        b->graph = g;
-        b->graph_out = dev_out;
-    }
-    return cudaGraphLaunch(b->exec, st) == cudaSuccess ? DFA_OK : DFA_ECUDA;
+        return cudaGraphLaunch(b->exec, st) == cudaSuccess ? DFA_OK : DFA_ECUDA;
+    });
 }
 
 int dfa_batch_num_kernels(const dfa_batch_t* b, uint32_t* n) {
@@ -1347,14 +1379,16 @@ void dfa_batch_destroy(dfa_batch_t* b) {
 int dfa_match_batch(uint32_t count, const dfa_t* const* dfas, const uint8_t* const* strs,
                     const uint64_t* lens, const dfa_match_opts_t* opts, dfa_result_t* dev_out,
                     void* stream) {
-    dfa_batch_t* b = nullptr;
-    int rc = dfa_batch_prepare(count, dfas, strs, lens, opts, &b);
-    if (rc != DFA_OK) return rc;
-    rc = dfa_batch_launch(b, dev_out, stream);
-    if (rc == DFA_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
-        rc = DFA_ECUDA;
-    dfa_batch_destroy(b);
-    return rc;
+    return dfam::no_throw([&]() -> int {
+        dfa_batch_t* b = nullptr;
+        int rc = dfa_batch_prepare(count, dfas, strs, lens, opts, &b);
+        if (rc != DFA_OK) return rc;
+        rc = dfa_batch_launch(b, dev_out, stream);
+        if (rc == DFA_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+            rc = DFA_ECUDA;
+        dfa_batch_destroy(b);
+        return rc;
+    });
 }
 
 const char* dfa_strerror(int s) {

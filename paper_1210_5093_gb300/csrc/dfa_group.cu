@@ -934,165 +934,167 @@ uint32_t set_size(const HostDfa& h, uint32_t c) { return h.iset_off[c + 1] - h.i
 extern "C" {
 
 int dfa_group_create(const dfa_t* const* dfas, uint32_t count, dfa_group_t** out) {
-    if (!out) return DFA_EINVAL;
-    *out = nullptr;
-    if (!dfas || count == 0 || count > kMaxDfas) return DFA_EINVAL;
-    uint32_t on_dev = 0;
-    for (uint32_t i = 0; i < count; ++i) {
-        if (!dfas[i] || dfas[i]->h.qe > kMaxQe) return DFA_EINVAL;
-        on_dev += dfas[i]->on_device ? 1u : 0u;
-        if (dfas[i]->on_device && dfas[i]->device != dfas[0]->device) return DFA_EINVAL;
-    }
-    if (on_dev != 0 && on_dev != count) return DFA_EINVAL;  // all on one device, or all host-only
-    dfa_group_s* g = new (std::nothrow) dfa_group_s;
-    if (!g) return DFA_ENOMEM;
-    g->G = count;
-    g->dfas.assign(dfas, dfas + count);
-    // joint classes: distinct tuples (class in DFA 0, ..., class in DFA G-1) over the bytes
-    std::map<std::vector<uint16_t>, uint32_t> ids;
-    std::vector<uint32_t> rep;  // a byte of each joint class
-    g->jmap.assign(256, 0);
-    for (uint32_t b = 0; b < 256; ++b) {
-        std::vector<uint16_t> key(count);
-        for (uint32_t i = 0; i < count; ++i) key[i] = dfas[i]->h.byte_class[b];
-        auto it = ids.find(key);
-        if (it == ids.end()) {
-            it = ids.emplace(key, (uint32_t)rep.size()).first;
-            rep.push_back(b);
+    return dfam::no_throw([&]() -> int {
+        if (!out) return DFA_EINVAL;
+        *out = nullptr;
+        if (!dfas || count == 0 || count > kMaxDfas) return DFA_EINVAL;
+        uint32_t on_dev = 0;
+        for (uint32_t i = 0; i < count; ++i) {
+            if (!dfas[i] || dfas[i]->h.qe > kMaxQe) return DFA_EINVAL;
+            on_dev += dfas[i]->on_device ? 1u : 0u;
+            if (dfas[i]->on_device && dfas[i]->device != dfas[0]->device) return DFA_EINVAL;
         }
-        g->jmap[b] = (uint16_t)it->second;
-    }
-    g->J = (uint32_t)rep.size();
-    if (g->J > kMaxJoint) {
-        delete g;
-        return DFA_EINVAL;
-    }
-    g->jbad.assign(256, 0);
-    for (uint32_t j = 0; j < g->J; ++j)
-        for (uint32_t i = 0; i < count; ++i)
-            if (dfas[i]->h.byte_class[rep[j]] == kNone16) g->jbad[j] |= (uint16_t)(1u << i);
-    for (uint32_t b = 0; b < 256; ++b)
-        if (g->jbad[g->jmap[b]]) g->jmap[b] |= 0x8000u;
-    // joint tables: per DFA, J rows (one per joint class) and the identity row
-    g->sb = 1;
-    for (uint32_t i = 0; i < count; ++i) {
-        g->qe_max = std::max(g->qe_max, dfas[i]->h.qe);
-        if (dfas[i]->h.qe > 256) g->sb = 2;
-    }
-    g->seg_stride = (g->qe_max + 7) & ~7u;
-    std::vector<uint32_t> qpad(count), toff(count), vcap(count);
-    uint64_t tb = 0;
-    for (uint32_t i = 0; i < count; ++i) {
-        const uint32_t per16 = 16 / g->sb;
-        qpad[i] = (dfas[i]->h.qe + per16 - 1) / per16 * per16;
-        toff[i] = (uint32_t)tb;
-        tb += (uint64_t)(g->J + 1) * qpad[i] * g->sb;
-    }
-    if (tb > kTableMax) {
-        delete g;
-        return DFA_EINVAL;
-    }
-    g->tbytes = (uint32_t)tb;
-    g->tables.assign(tb, 0);
-    g->jinfo.assign((size_t)count * 256, 0);
-    g->mean_slots_by_k.assign(5, 0.0);
-    for (uint32_t i = 0; i < count; ++i) {
-        const HostDfa& h = dfas[i]->h;
-        uint8_t* t = g->tables.data() + toff[i];
-        for (uint32_t j = 0; j <= g->J; ++j) {
-            const uint32_t c = j < g->J ? h.byte_class[rep[j]] : kNone16;
-            for (uint32_t s = 0; s < h.qe; ++s) {
-                const uint32_t nx = c == kNone16 ? s : host_next(h, c, s);  // identity row or outside Sigma
-                const uint32_t v = nx * g->sb;
-                uint8_t* e = t + ((size_t)j * qpad[i] + s) * g->sb;
-                e[0] = (uint8_t)v;
-                if (g->sb == 2) e[1] = (uint8_t)(v >> 8);
+        if (on_dev != 0 && on_dev != count) return DFA_EINVAL;  // all on one device, or all host-only
+        dfa_group_s* g = new (std::nothrow) dfa_group_s;
+        if (!g) return DFA_ENOMEM;
+        g->G = count;
+        g->dfas.assign(dfas, dfas + count);
+        // joint classes: distinct tuples (class in DFA 0, ..., class in DFA G-1) over the bytes
+        std::map<std::vector<uint16_t>, uint32_t> ids;
+        std::vector<uint32_t> rep;  // a byte of each joint class
+        g->jmap.assign(256, 0);
+        for (uint32_t b = 0; b < 256; ++b) {
+            std::vector<uint16_t> key(count);
+            for (uint32_t i = 0; i < count; ++i) key[i] = dfas[i]->h.byte_class[b];
+            auto it = ids.find(key);
+            if (it == ids.end()) {
+                it = ids.emplace(key, (uint32_t)rep.size()).first;
+                rep.push_back(b);
             }
-            if (j < g->J) {
-                // a lookahead byte outside Sigma fails the test; its chunk takes the start set
-                const uint32_t cls = c == kNone16 ? h.C : c;
-                g->jinfo[(size_t)i * 256 + j] = (cls << 16) | set_size(h, cls);
-            }
+            g->jmap[b] = (uint16_t)it->second;
         }
-        vcap[i] = 0;
-        for (uint32_t c = 0; c <= h.C; ++c) vcap[i] = std::max(vcap[i], set_size(h, c));
-        g->vcap_sum += vcap[i];
-        for (uint32_t ki = 0; ki < 5; ++ki) {
-            const uint32_t K = 1u << ki;
-            double m = 0;
-            for (uint32_t c = 0; c < h.C; ++c) m += std::max(1u, (set_size(h, c) + K - 1) / K);
-            g->mean_slots_by_k[ki] += h.C ? m / h.C : 1.0;
-        }
-    }
-    if (g->vcap_sum > kVcapMax) {
-        delete g;
-        return DFA_EINVAL;
-    }
-    // default chains per thread: for one DFA the compiler's rule on its mean set
-    // size; for several, 2 (a warp then spans the fewest (chunk, DFA) items, whose
-    // rows differ: K = 2 ran 15% faster than K = 4 on the 8 protein-shaped DFAs
-    // of the bench), raised until one chunk's items fit a CTA
-    double mean_set = 0;
-    for (uint32_t i = 0; i < count; ++i) mean_set += dfas[i]->h.mean_iset;
-    g->K0 = count == 1 ? k_for_set_size(mean_set) : std::min(2u, k_for_set_size(mean_set / count));
-    while (g->K0 <= 16 && max_chunk_slots(g, g->K0) > kGThreads) g->K0 *= 2;
-    if (g->K0 > 16) {
-        delete g;
-        return DFA_EINVAL;
-    }
-    if (on_dev) {
-        int cur = -1;
-        if (cudaGetDevice(&cur) != cudaSuccess || cur != dfas[0]->device) {
+        g->J = (uint32_t)rep.size();
+        if (g->J > kMaxJoint) {
             delete g;
             return DFA_EINVAL;
         }
-        const uint64_t o_gd = 0, o_ji = al256(o_gd + sizeof(GDfa) * count),
-                       o_jm = al256(o_ji + 4ull * count * 256), o_jb = al256(o_jm + 512),
-                       o_tb = al256(o_jb + 512), total = al256(o_tb + tb);
-        void* blk = nullptr;
-        if (cudaMalloc(&blk, total) != cudaSuccess) {
-            cudaGetLastError();
-            delete g;
-            return DFA_ENOMEM;
-        }
-        uint8_t* base = static_cast<uint8_t*>(blk);
-        g->dev_block = blk;
-        g->dev_bytes = total;
-        g->device = cur;
-        g->d_gd = reinterpret_cast<GDfa*>(base + o_gd);
-        g->d_jinfo = reinterpret_cast<uint32_t*>(base + o_ji);
-        g->d_jmap = reinterpret_cast<uint16_t*>(base + o_jm);
-        g->d_jbad = reinterpret_cast<uint16_t*>(base + o_jb);
-        g->d_tables = base + o_tb;
-        g->gd.resize(count);
+        g->jbad.assign(256, 0);
+        for (uint32_t j = 0; j < g->J; ++j)
+            for (uint32_t i = 0; i < count; ++i)
+                if (dfas[i]->h.byte_class[rep[j]] == kNone16) g->jbad[j] |= (uint16_t)(1u << i);
+        for (uint32_t b = 0; b < 256; ++b)
+            if (g->jbad[g->jmap[b]]) g->jmap[b] |= 0x8000u;
+        // joint tables: per DFA, J rows (one per joint class) and the identity row
+        g->sb = 1;
         for (uint32_t i = 0; i < count; ++i) {
-            const DevDfa& x = dfas[i]->dev;
-            GDfa& d = g->gd[i];
-            std::memset(&d, 0, sizeof d);
-            d.iset_off = x.iset_off;
-            d.iset = x.iset;
-            d.pos = x.pos;
-            d.accept = x.accept;
-            d.qe = x.qe;
-            d.q0 = x.q0;
-            d.C = x.C;
-            d.qpad = qpad[i];
-            d.tbl_off = toff[i];
-            d.vcap = vcap[i];
+            g->qe_max = std::max(g->qe_max, dfas[i]->h.qe);
+            if (dfas[i]->h.qe > 256) g->sb = 2;
         }
-        if (cudaMemcpy(g->d_gd, g->gd.data(), sizeof(GDfa) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(g->d_jinfo, g->jinfo.data(), 4ull * count * 256, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(g->d_jmap, g->jmap.data(), 512, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(g->d_jbad, g->jbad.data(), 512, cudaMemcpyHostToDevice) != cudaSuccess ||
-            (tb && cudaMemcpy(g->d_tables, g->tables.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess)) {
-            cudaFree(blk);
+        g->seg_stride = (g->qe_max + 7) & ~7u;
+        std::vector<uint32_t> qpad(count), toff(count), vcap(count);
+        uint64_t tb = 0;
+        for (uint32_t i = 0; i < count; ++i) {
+            const uint32_t per16 = 16 / g->sb;
+            qpad[i] = (dfas[i]->h.qe + per16 - 1) / per16 * per16;
+            toff[i] = (uint32_t)tb;
+            tb += (uint64_t)(g->J + 1) * qpad[i] * g->sb;
+        }
+        if (tb > kTableMax) {
             delete g;
-            return DFA_ECUDA;
+            return DFA_EINVAL;
         }
-        g->on_device = true;
-    }
-    *out = g;
-    return DFA_OK;
+        g->tbytes = (uint32_t)tb;
+        g->tables.assign(tb, 0);
+        g->jinfo.assign((size_t)count * 256, 0);
+        g->mean_slots_by_k.assign(5, 0.0);
+        for (uint32_t i = 0; i < count; ++i) {
+            const HostDfa& h = dfas[i]->h;
+            uint8_t* t = g->tables.data() + toff[i];
+            for (uint32_t j = 0; j <= g->J; ++j) {
+                const uint32_t c = j < g->J ? h.byte_class[rep[j]] : kNone16;
+                for (uint32_t s = 0; s < h.qe; ++s) {
+                    const uint32_t nx = c == kNone16 ? s : host_next(h, c, s);  // identity row or outside Sigma
+                    const uint32_t v = nx * g->sb;
+                    uint8_t* e = t + ((size_t)j * qpad[i] + s) * g->sb;
+                    e[0] = (uint8_t)v;
+                    if (g->sb == 2) e[1] = (uint8_t)(v >> 8);
+                }
+                if (j < g->J) {
+                    // a lookahead byte outside Sigma fails the test; its chunk takes the start set
+                    const uint32_t cls = c == kNone16 ? h.C : c;
+                    g->jinfo[(size_t)i * 256 + j] = (cls << 16) | set_size(h, cls);
+                }
+            }
+            vcap[i] = 0;
+            for (uint32_t c = 0; c <= h.C; ++c) vcap[i] = std::max(vcap[i], set_size(h, c));
+            g->vcap_sum += vcap[i];
+            for (uint32_t ki = 0; ki < 5; ++ki) {
+                const uint32_t K = 1u << ki;
+                double m = 0;
+                for (uint32_t c = 0; c < h.C; ++c) m += std::max(1u, (set_size(h, c) + K - 1) / K);
+                g->mean_slots_by_k[ki] += h.C ? m / h.C : 1.0;
+            }
+        }
+        if (g->vcap_sum > kVcapMax) {
+            delete g;
+            return DFA_EINVAL;
+        }
+        // default chains per thread: for one DFA the compiler's rule on its mean set
+        // size; for several, 2 (a warp then spans the fewest (chunk, DFA) items, whose
+        // rows differ: K = 2 ran 15% faster than K = 4 on the 8 protein-shaped DFAs
+        // of the bench), raised until one chunk's items fit a CTA
+        double mean_set = 0;
+        for (uint32_t i = 0; i < count; ++i) mean_set += dfas[i]->h.mean_iset;
+        g->K0 = count == 1 ? k_for_set_size(mean_set) : std::min(2u, k_for_set_size(mean_set / count));
+        while (g->K0 <= 16 && max_chunk_slots(g, g->K0) > kGThreads) g->K0 *= 2;
+        if (g->K0 > 16) {
+            delete g;
+            return DFA_EINVAL;
+        }
+        if (on_dev) {
+            int cur = -1;
+            if (cudaGetDevice(&cur) != cudaSuccess || cur != dfas[0]->device) {
+                delete g;
+                return DFA_EINVAL;
+            }
+            const uint64_t o_gd = 0, o_ji = al256(o_gd + sizeof(GDfa) * count),
+                           o_jm = al256(o_ji + 4ull * count * 256), o_jb = al256(o_jm + 512),
+                           o_tb = al256(o_jb + 512), total = al256(o_tb + tb);
+            void* blk = nullptr;
+            if (cudaMalloc(&blk, total) != cudaSuccess) {
+                cudaGetLastError();
+                delete g;
+                return DFA_ENOMEM;
+            }
+            uint8_t* base = static_cast<uint8_t*>(blk);
+            g->dev_block = blk;
+            g->dev_bytes = total;
+            g->device = cur;
+            g->d_gd = reinterpret_cast<GDfa*>(base + o_gd);
+            g->d_jinfo = reinterpret_cast<uint32_t*>(base + o_ji);
+            g->d_jmap = reinterpret_cast<uint16_t*>(base + o_jm);
+            g->d_jbad = reinterpret_cast<uint16_t*>(base + o_jb);
+            g->d_tables = base + o_tb;
+            g->gd.resize(count);
+            for (uint32_t i = 0; i < count; ++i) {
+                const DevDfa& x = dfas[i]->dev;
+                GDfa& d = g->gd[i];
+                std::memset(&d, 0, sizeof d);
+                d.iset_off = x.iset_off;
+                d.iset = x.iset;
+                d.pos = x.pos;
+                d.accept = x.accept;
+                d.qe = x.qe;
+                d.q0 = x.q0;
+                d.C = x.C;
+                d.qpad = qpad[i];
+                d.tbl_off = toff[i];
+                d.vcap = vcap[i];
+            }
+            if (cudaMemcpy(g->d_gd, g->gd.data(), sizeof(GDfa) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(g->d_jinfo, g->jinfo.data(), 4ull * count * 256, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(g->d_jmap, g->jmap.data(), 512, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(g->d_jbad, g->jbad.data(), 512, cudaMemcpyHostToDevice) != cudaSuccess ||
+                (tb && cudaMemcpy(g->d_tables, g->tables.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess)) {
+                cudaFree(blk);
+                delete g;
+                return DFA_ECUDA;
+            }
+            g->on_device = true;
+        }
+        *out = g;
+        return DFA_OK;
+    });
 }
 
 void dfa_group_destroy(dfa_group_t* g) {
@@ -1133,161 +1135,171 @@ int dfa_group_joint_classes(const dfa_group_t* g, uint16_t* out) {
 
 int dfa_group_autotune(dfa_group_t* g, const uint8_t* dev_sample, uint64_t len, void* stream,
                        uint32_t* states_per_thread, uint32_t* ctas_per_sm, double* best_ms) {
-    if (!g || (len && !dev_sample)) return DFA_EINVAL;
-    if (!g->on_device) return DFA_EHOSTONLY;
-    struct Cand {
-        uint32_t K, ctas;
-        GLaunch l;
-    };
-    std::vector<Cand> cands;
-    uint64_t ws_need = 0;
-    for (uint32_t K : {1u, 2u, 4u, 8u, 16u})
-        for (uint32_t c : {1u, 2u}) {
-            dfa_group_opts_t o;
-            std::memset(&o, 0, sizeof o);
-            o.states_per_thread = K;
-            o.ctas_per_sm = c;
-            Cand x;
-            x.K = K;
-            x.ctas = c;
-            if (plan_launch(g, len, &o, &x.l) != DFA_OK) continue;
-            ws_need = std::max(ws_need, x.l.ws_total);
-            cands.push_back(x);
+    return dfam::no_throw([&]() -> int {
+        if (!g || (len && !dev_sample)) return DFA_EINVAL;
+        if (!g->on_device) return DFA_EHOSTONLY;
+        struct Cand {
+            uint32_t K, ctas;
+            GLaunch l;
+        };
+        std::vector<Cand> cands;
+        uint64_t ws_need = 0;
+        for (uint32_t K : {1u, 2u, 4u, 8u, 16u})
+            for (uint32_t c : {1u, 2u}) {
+                dfa_group_opts_t o;
+                std::memset(&o, 0, sizeof o);
+                o.states_per_thread = K;
+                o.ctas_per_sm = c;
+                Cand x;
+                x.K = K;
+                x.ctas = c;
+                if (plan_launch(g, len, &o, &x.l) != DFA_OK) continue;
+                ws_need = std::max(ws_need, x.l.ws_total);
+                cands.push_back(x);
+            }
+        if (cands.empty()) return DFA_EINVAL;
+        void *ws = nullptr, *res = nullptr;
+        if (cudaMalloc(&ws, ws_need) != cudaSuccess || cudaMalloc(&res, sizeof(dfa_result_t) * g->G) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(ws);
+            return DFA_ENOMEM;
         }
-    if (cands.empty()) return DFA_EINVAL;
-    void *ws = nullptr, *res = nullptr;
-    if (cudaMalloc(&ws, ws_need) != cudaSuccess || cudaMalloc(&res, sizeof(dfa_result_t) * g->G) != cudaSuccess) {
-        cudaGetLastError();
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int rc = (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) ? DFA_OK
+                                                                                              : DFA_ECUDA;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        double best = 1e30;
+        const Cand* win = nullptr;
+        for (Cand& x : cands) {
+            if (rc != DFA_OK) break;
+            bind_ws(x.l, static_cast<uint8_t*>(ws));
+            x.l.p.str = dev_sample;
+            x.l.p.results = static_cast<dfa_result_t*>(res);
+            float t = 1e30f;
+            for (int rep = 0; rep < 3 && rc == DFA_OK; ++rep) {  // the first launch warms up
+                if (cudaEventRecord(e0, st) != cudaSuccess) rc = DFA_ECUDA;
+                if (rc == DFA_OK) rc = issue(x.l, g->sb, nullptr, stream);
+                if (rc == DFA_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                     cudaEventSynchronize(e1) != cudaSuccess))
+                    rc = DFA_ECUDA;
+                float ms = 0;
+                if (rc == DFA_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    t = std::min(t, ms);
+            }
+            if (rc == DFA_OK && t < best) {
+                best = t;
+                win = &x;
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
         cudaFree(ws);
-        return DFA_ENOMEM;
-    }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int rc = (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) ? DFA_OK
-                                                                                          : DFA_ECUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    double best = 1e30;
-    const Cand* win = nullptr;
-    for (Cand& x : cands) {
-        if (rc != DFA_OK) break;
-        bind_ws(x.l, static_cast<uint8_t*>(ws));
-        x.l.p.str = dev_sample;
-        x.l.p.results = static_cast<dfa_result_t*>(res);
-        float t = 1e30f;
-        for (int rep = 0; rep < 3 && rc == DFA_OK; ++rep) {  // the first launch warms up
-            if (cudaEventRecord(e0, st) != cudaSuccess) rc = DFA_ECUDA;
-            if (rc == DFA_OK) rc = issue(x.l, g->sb, nullptr, stream);
-            if (rc == DFA_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
-                                 cudaEventSynchronize(e1) != cudaSuccess))
-                rc = DFA_ECUDA;
-            float ms = 0;
-            if (rc == DFA_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
-                t = std::min(t, ms);
-        }
-        if (rc == DFA_OK && t < best) {
-            best = t;
-            win = &x;
-        }
-    }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaFree(ws);
-    cudaFree(res);
-    if (rc != DFA_OK) return rc;
-    if (!win) return DFA_ECUDA;
-    g->K0 = win->K;
-    g->ctas0 = win->ctas;
-    if (states_per_thread) *states_per_thread = win->K;
-    if (ctas_per_sm) *ctas_per_sm = win->ctas;
-    if (best_ms) *best_ms = best;
-    return DFA_OK;
+        cudaFree(res);
+        if (rc != DFA_OK) return rc;
+        if (!win) return DFA_ECUDA;
+        g->K0 = win->K;
+        g->ctas0 = win->ctas;
+        if (states_per_thread) *states_per_thread = win->K;
+        if (ctas_per_sm) *ctas_per_sm = win->ctas;
+        if (best_ms) *best_ms = best;
+        return DFA_OK;
+    });
 }
 
 int dfa_group_plan_chunks(const dfa_group_t* g, uint64_t len, const dfa_group_opts_t* opts,
                           uint32_t* P) {
-    if (!P) return DFA_EINVAL;
-    GLaunch l;
-    const int rc = plan_launch(g, len, opts, &l);
-    if (rc != DFA_OK) return rc;
-    *P = l.p.P;
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!P) return DFA_EINVAL;
+        GLaunch l;
+        const int rc = plan_launch(g, len, opts, &l);
+        if (rc != DFA_OK) return rc;
+        *P = l.p.P;
+        return DFA_OK;
+    });
 }
 
 int dfa_group_workspace_size(const dfa_group_t* g, uint64_t len, const dfa_group_opts_t* opts,
                              uint64_t* bytes) {
-    if (!bytes) return DFA_EINVAL;
-    GLaunch l;
-    const int rc = plan_launch(g, len, opts, &l);
-    if (rc != DFA_OK) return rc;
-    *bytes = l.ws_total;
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!bytes) return DFA_EINVAL;
+        GLaunch l;
+        const int rc = plan_launch(g, len, opts, &l);
+        if (rc != DFA_OK) return rc;
+        *bytes = l.ws_total;
+        return DFA_OK;
+    });
 }
 
 int dfa_group_match_async(const dfa_group_t* g, const uint8_t* dev_str, uint64_t len,
                           const dfa_group_opts_t* opts, dfa_result_t* dev_out, void* dev_workspace,
                           uint64_t workspace_bytes, void* stream) {
-    if (!g || !dev_out || !dev_workspace || (len && !dev_str)) return DFA_EINVAL;
-    if (((uintptr_t)dev_out & 3u) || ((uintptr_t)dev_workspace & 255u)) return DFA_EINVAL;
-    if (opts && opts->dev_work && ((uintptr_t)opts->dev_work & 7u)) return DFA_EINVAL;
-    GLaunch l;
-    const int rc = plan_launch(g, len, opts, &l);
-    if (rc != DFA_OK) return rc;
-    if (workspace_bytes < l.ws_total) return DFA_ENOSPACE;
-    bind_ws(l, static_cast<uint8_t*>(dev_workspace));
-    l.p.str = dev_str;
-    l.p.results = dev_out;
-    l.p.work = opts ? reinterpret_cast<unsigned long long*>(opts->dev_work) : nullptr;
-    l.p.dbg = nullptr;
-    return issue(l, g->sb, opts, stream);
+    return dfam::no_throw([&]() -> int {
+        if (!g || !dev_out || !dev_workspace || (len && !dev_str)) return DFA_EINVAL;
+        if (((uintptr_t)dev_out & 3u) || ((uintptr_t)dev_workspace & 255u)) return DFA_EINVAL;
+        if (opts && opts->dev_work && ((uintptr_t)opts->dev_work & 7u)) return DFA_EINVAL;
+        GLaunch l;
+        const int rc = plan_launch(g, len, opts, &l);
+        if (rc != DFA_OK) return rc;
+        if (workspace_bytes < l.ws_total) return DFA_ENOSPACE;
+        bind_ws(l, static_cast<uint8_t*>(dev_workspace));
+        l.p.str = dev_str;
+        l.p.results = dev_out;
+        l.p.work = opts ? reinterpret_cast<unsigned long long*>(opts->dev_work) : nullptr;
+        l.p.dbg = nullptr;
+        return issue(l, g->sb, opts, stream);
+    });
 }
 
 int dfa_group_debug_chunk_maps(const dfa_group_t* g, const uint8_t* dev_str, uint64_t len,
                                const dfa_group_opts_t* opts, uint16_t* maps, uint32_t cap,
                                uint32_t* P, uint32_t* final_states) {
-    if (!g || !P || (len && !dev_str)) return DFA_EINVAL;
-    GLaunch l;
-    int rc = plan_launch(g, len, opts, &l);
-    if (rc != DFA_OK) return rc;
-    *P = l.p.P;
-    if (!maps && !final_states) return DFA_OK;
-    const uint64_t per = (uint64_t)g->G * l.p.P * g->qe_max;
-    std::vector<uint16_t> host(per);
-    for (uint64_t i = 0; i < per; ++i) host[i] = (uint16_t)(i % g->qe_max);  // identity outside I_k
-    void *ws = nullptr, *dbg = nullptr, *res = nullptr;
-    rc = DFA_OK;
-    if (cudaMalloc(&ws, l.ws_total) != cudaSuccess || cudaMalloc(&dbg, per * 2) != cudaSuccess ||
-        cudaMalloc(&res, sizeof(dfa_result_t) * g->G) != cudaSuccess) {
-        cudaGetLastError();
-        rc = DFA_ENOMEM;
-    }
-    if (rc == DFA_OK && cudaMemcpy(dbg, host.data(), per * 2, cudaMemcpyHostToDevice) != cudaSuccess)
-        rc = DFA_ECUDA;
-    if (rc == DFA_OK) {
-        bind_ws(l, static_cast<uint8_t*>(ws));
-        l.p.str = dev_str;
-        l.p.results = static_cast<dfa_result_t*>(res);
-        l.p.work = nullptr;
-        l.p.dbg = static_cast<uint16_t*>(dbg);
-        rc = issue(l, g->sb, opts, nullptr);
-        if (rc == DFA_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = DFA_ECUDA;
-    }
-    std::vector<dfa_result_t> r(g->G);
-    if (rc == DFA_OK &&
-        (cudaMemcpy(host.data(), dbg, per * 2, cudaMemcpyDeviceToHost) != cudaSuccess ||
-         cudaMemcpy(r.data(), res, sizeof(dfa_result_t) * g->G, cudaMemcpyDeviceToHost) != cudaSuccess))
-        rc = DFA_ECUDA;
-    cudaFree(ws);
-    cudaFree(dbg);
-    cudaFree(res);
-    if (rc != DFA_OK) return rc;
-    if (maps) {
-        const uint32_t np = std::min(cap, l.p.P);
-        for (uint32_t i = 0; i < g->G; ++i)
-            std::memcpy(maps + (uint64_t)i * np * g->qe_max, host.data() + (uint64_t)i * l.p.P * g->qe_max,
-                        2ull * np * g->qe_max);
-    }
-    if (final_states)
-        for (uint32_t i = 0; i < g->G; ++i) final_states[i] = r[i].status ? 0xFFFFFFFFu : r[i].final_state;
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!g || !P || (len && !dev_str)) return DFA_EINVAL;
+        GLaunch l;
+        int rc = plan_launch(g, len, opts, &l);
+        if (rc != DFA_OK) return rc;
+        *P = l.p.P;
+        if (!maps && !final_states) return DFA_OK;
+        const uint64_t per = (uint64_t)g->G * l.p.P * g->qe_max;
+        std::vector<uint16_t> host(per);
+        for (uint64_t i = 0; i < per; ++i) host[i] = (uint16_t)(i % g->qe_max);  // identity outside I_k
+        void *ws = nullptr, *dbg = nullptr, *res = nullptr;
+        rc = DFA_OK;
+        if (cudaMalloc(&ws, l.ws_total) != cudaSuccess || cudaMalloc(&dbg, per * 2) != cudaSuccess ||
+            cudaMalloc(&res, sizeof(dfa_result_t) * g->G) != cudaSuccess) {
+            cudaGetLastError();
+            rc = DFA_ENOMEM;
+        }
+        if (rc == DFA_OK && cudaMemcpy(dbg, host.data(), per * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = DFA_ECUDA;
+        if (rc == DFA_OK) {
+            bind_ws(l, static_cast<uint8_t*>(ws));
+            l.p.str = dev_str;
+            l.p.results = static_cast<dfa_result_t*>(res);
+            l.p.work = nullptr;
+            l.p.dbg = static_cast<uint16_t*>(dbg);
+            rc = issue(l, g->sb, opts, nullptr);
+            if (rc == DFA_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = DFA_ECUDA;
+        }
+        std::vector<dfa_result_t> r(g->G);
+        if (rc == DFA_OK &&
+            (cudaMemcpy(host.data(), dbg, per * 2, cudaMemcpyDeviceToHost) != cudaSuccess ||
+             cudaMemcpy(r.data(), res, sizeof(dfa_result_t) * g->G, cudaMemcpyDeviceToHost) != cudaSuccess))
+            rc = DFA_ECUDA;
+        cudaFree(ws);
+        cudaFree(dbg);
+        cudaFree(res);
+        if (rc != DFA_OK) return rc;
+        if (maps) {
+            const uint32_t np = std::min(cap, l.p.P);
+            for (uint32_t i = 0; i < g->G; ++i)
+                std::memcpy(maps + (uint64_t)i * np * g->qe_max, host.data() + (uint64_t)i * l.p.P * g->qe_max,
+                            2ull * np * g->qe_max);
+        }
+        if (final_states)
+            for (uint32_t i = 0; i < g->G; ++i) final_states[i] = r[i].status ? 0xFFFFFFFFu : r[i].final_state;
+        return DFA_OK;
+    });
 }
 
 }  // extern "C"

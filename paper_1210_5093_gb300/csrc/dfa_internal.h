@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -243,6 +244,19 @@ struct HostDfa {
     std::vector<uint32_t> byte_off32;   // 256
     std::vector<uint8_t> nib_rows;      // (C+1) x 16 when at most 16 states are live, else empty
 };
+
+// Runs an entry point's body; a failed host allocation becomes DFA_ENOMEM (and
+// any other C++ exception DFA_EINVAL), so no exception crosses the C ABI.
+template <typename F>
+inline int no_throw(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return DFA_ENOMEM;
+    } catch (...) {
+        return DFA_EINVAL;
+    }
+}
 
 // Compile (validation, classes, excluded states, I sets, table image).
 int compile_dfa(uint32_t num_states, uint32_t num_symbols, const int32_t* delta, uint32_t q0,

@@ -59,20 +59,22 @@ int scratch_ptr(void* stream, uint8_t** out) {
 extern "C" int dfa_match_noalloc(const dfa_t* dfa, const uint8_t* dev_str, uint64_t len,
                                  const dfa_match_opts_t* opts, dfa_result_t* dev_out,
                                  void* stream) {
-    if (!dfa || !dev_out || (len && !dev_str)) return DFA_EINVAL;
-    if (reinterpret_cast<uintptr_t>(dev_out) & 3u) return DFA_EINVAL;  // results are 4-byte aligned
-    dfam::Single s;
-    int rc = dfam::plan_single(dfa, len, opts, &s);
-    if (rc != DFA_OK) return rc;
-    if (s.ws.total > kScratchBytes) return DFA_ENOSPACE;
-    uint8_t* base = nullptr;
-    if ((rc = scratch_ptr(stream, &base)) != DFA_OK) return rc;
-    s.lp.test1.str = dev_str;
-    dfam::bind(s.lp, base, s.ws);
-    s.lp.results = dev_out;
-    // the per-test counters that must start at zero are cleared by the launch itself
-    return dfam::launch_single(s, stream, opts ? opts->match_begin_event : nullptr,
-                               opts ? opts->match_end_event : nullptr);
+    return dfam::no_throw([&]() -> int {
+        if (!dfa || !dev_out || (len && !dev_str)) return DFA_EINVAL;
+        if (reinterpret_cast<uintptr_t>(dev_out) & 3u) return DFA_EINVAL;  // results are 4-byte aligned
+        dfam::Single s;
+        int rc = dfam::plan_single(dfa, len, opts, &s);
+        if (rc != DFA_OK) return rc;
+        if (s.ws.total > kScratchBytes) return DFA_ENOSPACE;
+        uint8_t* base = nullptr;
+        if ((rc = scratch_ptr(stream, &base)) != DFA_OK) return rc;
+        s.lp.test1.str = dev_str;
+        dfam::bind(s.lp, base, s.ws);
+        s.lp.results = dev_out;
+        // the per-test counters that must start at zero are cleared by the launch itself
+        return dfam::launch_single(s, stream, opts ? opts->match_begin_event : nullptr,
+                                   opts ? opts->match_end_event : nullptr);
+    });
 }
 
 extern "C" uint64_t dfa_noalloc_scratch_bytes(void) { return kScratchBytes; }

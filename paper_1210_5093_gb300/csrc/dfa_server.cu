@@ -314,95 +314,103 @@ void dfa_server_s::run() {
 extern "C" {
 
 int dfa_server_create(uint64_t budget, uint32_t max_inflight, dfa_server_t** out) {
-    if (!out || budget == 0) return DFA_EINVAL;
-    *out = nullptr;
-    if (max_inflight == 0) max_inflight = 8;
-    if (max_inflight > 64) max_inflight = 64;
-    dfa_server_s* s = new (std::nothrow) dfa_server_s();
-    if (!s) return DFA_ENOMEM;
-    if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return DFA_ECUDA; }
-    if (cudaMalloc(&s->arena_mem, budget) != cudaSuccess) {
-        cudaGetLastError();
-        delete s;
-        return DFA_ENOMEM;
-    }
-    s->budget = budget;
-    s->opts.lookahead = 1;
-    s->arena.reset(budget);
-    s->slots.resize(max_inflight);
-    bool ok = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
-    for (Slot& sl : s->slots)
-        ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) == cudaSuccess;
-    for (Slot& sl : s->slots)
-        ok = ok && grow(&sl.ws, &sl.ws_bytes, kSlotWs, false) == DFA_OK &&
-             grow(&sl.pinned, &sl.pinned_bytes, kSlotPinned, true) == DFA_OK;
-    if (!ok) {
-        cudaGetLastError();
-        for (Slot& x : s->slots) {
-            if (x.ws) cudaFree(x.ws);
-            if (x.pinned) cudaFreeHost(x.pinned);
-            if (x.stream) cudaStreamDestroy(x.stream);
-            if (x.done) cudaEventDestroy(x.done);
-            if (x.copied) cudaEventDestroy(x.copied);
+    return dfam::no_throw([&]() -> int {
+        if (!out || budget == 0) return DFA_EINVAL;
+        *out = nullptr;
+        if (max_inflight == 0) max_inflight = 8;
+        if (max_inflight > 64) max_inflight = 64;
+        dfa_server_s* s = new (std::nothrow) dfa_server_s();
+        if (!s) return DFA_ENOMEM;
+        if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return DFA_ECUDA; }
+        if (cudaMalloc(&s->arena_mem, budget) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return DFA_ENOMEM;
         }
-        if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
-        cudaFree(s->arena_mem);
-        delete s;
-        return DFA_ECUDA;
-    }
-    s->worker = std::thread([s] { s->run(); });
-    *out = s;
-    return DFA_OK;
+        s->budget = budget;
+        s->opts.lookahead = 1;
+        s->arena.reset(budget);
+        s->slots.resize(max_inflight);
+        bool ok = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+        for (Slot& sl : s->slots)
+            ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) == cudaSuccess;
+        for (Slot& sl : s->slots)
+            ok = ok && grow(&sl.ws, &sl.ws_bytes, kSlotWs, false) == DFA_OK &&
+                 grow(&sl.pinned, &sl.pinned_bytes, kSlotPinned, true) == DFA_OK;
+        if (!ok) {
+            cudaGetLastError();
+            for (Slot& x : s->slots) {
+                if (x.ws) cudaFree(x.ws);
+                if (x.pinned) cudaFreeHost(x.pinned);
+                if (x.stream) cudaStreamDestroy(x.stream);
+                if (x.done) cudaEventDestroy(x.done);
+                if (x.copied) cudaEventDestroy(x.copied);
+            }
+            if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+            cudaFree(s->arena_mem);
+            delete s;
+            return DFA_ECUDA;
+        }
+        s->worker = std::thread([s] { s->run(); });
+        *out = s;
+        return DFA_OK;
+    });
 }
 
 int dfa_server_set_opts(dfa_server_t* s, const dfa_match_opts_t* opts) {
-    if (!s) return DFA_EINVAL;
-    dfa_match_opts_t o{};
-    o.lookahead = 1;
-    if (opts) {
-        if (opts->num_chunks || opts->multiplicity || opts->match_begin_event ||
-            opts->match_end_event || opts->lookahead > dfam::kMaxLookahead ||
-            opts->boundary_window > dfam::kMaxBoundaryWindow)
-            return DFA_EINVAL;
-        o.lookahead = opts->lookahead;
-        o.boundary_window = opts->boundary_window;
-    }
-    std::lock_guard<std::mutex> g(s->mu);
-    s->opts = o;
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!s) return DFA_EINVAL;
+        dfa_match_opts_t o{};
+        o.lookahead = 1;
+        if (opts) {
+            if (opts->num_chunks || opts->multiplicity || opts->match_begin_event ||
+                opts->match_end_event || opts->lookahead > dfam::kMaxLookahead ||
+                opts->boundary_window > dfam::kMaxBoundaryWindow)
+                return DFA_EINVAL;
+            o.lookahead = opts->lookahead;
+            o.boundary_window = opts->boundary_window;
+        }
+        std::lock_guard<std::mutex> g(s->mu);
+        s->opts = o;
+        return DFA_OK;
+    });
 }
 
 int dfa_server_submit(dfa_server_t* s, const dfa_t* dfa, const uint8_t* str, uint64_t len,
                       uint64_t* ticket) {
-    if (!s || !dfa || !ticket || (len && !str)) return DFA_EINVAL;
-    if (!dfa->on_device) return DFA_EHOSTONLY;
-    std::lock_guard<std::mutex> g(s->mu);
-    if (len > s->budget) {
-        s->st.rejected++;
-        return DFA_EBUDGET;
-    }
-    if (s->pending.size() >= kMaxPending) return DFA_EAGAIN;
-    Req r{s->next_ticket++, dfa, str, len, now_s(), 0};
-    s->pending.push_back(r);
-    s->pending_bytes += len;
-    s->st.submitted++;
-    *ticket = r.ticket;
-    s->cv.notify_one();
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!s || !dfa || !ticket || (len && !str)) return DFA_EINVAL;
+        if (!dfa->on_device) return DFA_EHOSTONLY;
+        std::lock_guard<std::mutex> g(s->mu);
+        if (len > s->budget) {
+            s->st.rejected++;
+            return DFA_EBUDGET;
+        }
+        if (s->pending.size() >= kMaxPending) return DFA_EAGAIN;
+        Req r{s->next_ticket++, dfa, str, len, now_s(), 0};
+        s->pending.push_back(r);
+        s->pending_bytes += len;
+        s->st.submitted++;
+        *ticket = r.ticket;
+        s->cv.notify_one();
+        return DFA_OK;
+    });
 }
 
 int dfa_server_poll(dfa_server_t* s, dfa_completion_t* out, uint32_t max, uint32_t* n) {
-    if (!s || !n || (max && !out)) return DFA_EINVAL;
-    std::lock_guard<std::mutex> g(s->mu);
-    uint32_t k = 0;
-    while (k < max && !s->done.empty()) {
-        out[k++] = s->done.front();
-        s->done.pop_front();
-    }
-    *n = k;
-    return DFA_OK;
+    return dfam::no_throw([&]() -> int {
+        if (!s || !n || (max && !out)) return DFA_EINVAL;
+        std::lock_guard<std::mutex> g(s->mu);
+        uint32_t k = 0;
+        while (k < max && !s->done.empty()) {
+            out[k++] = s->done.front();
+            s->done.pop_front();
+        }
+        *n = k;
+        return DFA_OK;
+    });
 }
 
 int dfa_server_drain(dfa_server_t* s, double timeout_s) {
