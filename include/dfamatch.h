@@ -13,9 +13,13 @@
  * Algorithm 1 for every input (the method is failure-free, Sec. 4.4).
  *
  * All entry points return an int status: DFA_OK (0) or a negative DFA_E*
- * code.  No function throws, exits or prints.  A dfa_t is immutable after
- * creation and may be used from several host threads at once; a
- * dfa_server_t is used from one host thread (its worker runs internally).
+ * code.  No function throws, exits or prints; a failed host allocation is
+ * DFA_ENOMEM.  A dfa_t changes only through the tuning calls (dfa_set_tuning*,
+ * dfa_autotune*), which must not run while another call uses the same dfa_t;
+ * every other call only reads it and may run from several host threads at
+ * once.  A dfa_group_t likewise changes only through dfa_group_autotune.  A
+ * dfa_batch_t and a dfa_server_t are each used from one host thread at a time
+ * (the server's worker runs internally).
  * Device pointers are CUDA device addresses of the current device; "stream"
  * arguments are cudaStream_t values passed as void* (NULL = legacy default
  * stream).
