@@ -70,6 +70,34 @@ def test_random_dfas_many_chunkings(dm, seed):
             _check(dm, d, spec, data[:n], num_chunks=P)
 
 
+def test_one_dfa_from_many_host_threads(dm):
+    """Matching calls only read a dfa_t: eight host threads matching host and
+    device strings through one dfa_t at once all get the oracle's answers."""
+    import threading
+    import torch
+    w = gen.regex_workload(2, 8 << 20)
+    d = dm.Dfa.from_spec(w.spec)
+    xs = [w.data[i * 700_001: i * 700_001 + 3_000_000 - 17 * i] for i in range(8)]
+    want = [oracle.Dfa.from_spec(w.spec).run(x) for x in xs]
+    devs = [torch.from_numpy(x.copy()).cuda() if i % 2 else x for i, x in enumerate(xs)]
+    got = [None] * len(xs)
+    errors = []
+
+    def one(i):
+        try:
+            for _ in range(3):
+                got[i] = d.match(devs[i], num_chunks=0 if i < 4 else 100 + i)
+        except Exception as e:      # reported below
+            errors.append(e)
+    ts = [threading.Thread(target=one, args=(i,)) for i in range(len(xs))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    assert got == want
+
+
 def test_random_options(dm):
     """Random DFAs, inputs and launch options together: sizes 1-700 states over
     1-40 symbols on random byte subsets, missing entries, bytes outside Sigma,
