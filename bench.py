@@ -588,6 +588,20 @@ def group_config(args, dm, torch, lookup_peak, n: int = 1 << 30, reps: int = 5, 
     assert dm.results_from(out) == res, "the answers changed between steps"
     km = statistics.median(a.elapsed_time(b) for a, b in zip(ev[0], ev[1]))
     sm_ = statistics.median(a.elapsed_time(b) for a, b in zip(ev[2], ev[3]))
+    # end to end through dfa_group_match on a pinned host buffer: the H2D copy of
+    # the input, both kernels and the results read back, per call
+    pinned = torch.from_numpy(data).pin_memory()
+    for _ in range(2):
+        g.match(pinned, **kw)
+    e2e_calls, e2e_res = [], []
+    for _ in range(max(3, reps)):
+        te = time.perf_counter()
+        e2e_res.append(g.match(pinned, **kw))
+        e2e_calls.append(time.perf_counter() - te)
+    assert expect is None or all(r == expect for r in e2e_res), \
+        "end-to-end group answers differ from the oracle"
+    del pinned
+    e2e_s = statistics.median(e2e_calls)
     total = n * len(specs)
     leg = {"workload": "protein_group_%ddfa_%s" % (len(specs), gen._size_name(n)),
            "states": [s.num_states for s in specs], "input_bytes": n,
@@ -600,7 +614,12 @@ def group_config(args, dm, torch, lookup_peak, n: int = 1 << 30, reps: int = 5, 
            "lookups_per_byte": round(W / n, 3),
            "lookup_roof_frac": round(W / (km / 1e3) / lookup_peak, 4),
            "launches": 2, "clocks": clocks,
-           "l2": "input larger than L2, not flushed" if n > L2_BYTES else "input fits in L2"}
+           "l2": "input larger than L2, not flushed" if n > L2_BYTES else "input fits in L2",
+           "e2e": {"value": round(total / e2e_s / 1e9, 3), "unit": "GB/s",
+                   "h2d_bytes_per_step": n, "d2h_bytes_per_step": 12 * len(specs),
+                   "api": "dfa_group_match (pinned host buffer, copied whole)",
+                   "calls": len(e2e_calls), "statistic": "median call time",
+                   "call_ms": [round(x * 1e3, 2) for x in e2e_calls]}}
     if compare:
         bl, res_b, res_p = batched_leg(dm, torch, dfas, [dev] * len(dfas), reps=reps)
         assert expect is None or [_as_answer(r) for r in res_b] == expect == \

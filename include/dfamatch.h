@@ -17,7 +17,8 @@
  * DFA_ENOMEM.  A dfa_t changes only through the tuning calls (dfa_set_tuning*,
  * dfa_autotune*), which must not run while another call uses the same dfa_t;
  * every other call only reads it and may run from several host threads at
- * once.  A dfa_group_t likewise changes only through dfa_group_autotune.  A
+ * once.  A dfa_group_t likewise changes only through dfa_group_autotune
+ * (dfa_group_match serialises its own use of the group's buffers).  A
  * dfa_batch_t and a dfa_server_t are each used from one host thread at a time
  * (the server's worker runs internally).
  * Device pointers are CUDA device addresses of the current device; "stream"
@@ -530,6 +531,20 @@ int dfa_group_workspace_size(const dfa_group_t *group, uint64_t len, const dfa_g
 int dfa_group_match_async(const dfa_group_t *group, const uint8_t *dev_str, uint64_t len,
                           const dfa_group_opts_t *opts, dfa_result_t *dev_out, void *dev_workspace,
                           uint64_t workspace_bytes, void *stream);
+
+/*
+ * Synchronous form of dfa_group_match_async for host or device input: str is
+ * len bytes of host memory (copied whole to the device first; pinned memory
+ * copies fastest) or a device pointer; out[i] (host, count entries) receives
+ * DFA i's result, its status DFA_ESYMBOL when the input holds a byte outside
+ * DFA i's Sigma.  The call returns DFA_OK when the launch ran, whatever the
+ * results' status.  The group keeps the input copy, workspace and results
+ * buffers between calls (freed by dfa_group_destroy); calls on one group are
+ * serialised.  Runs on the legacy default stream and synchronises it.
+ * Errors: DFA_EINVAL, DFA_EHOSTONLY, DFA_ENOMEM, DFA_ECUDA.
+ */
+int dfa_group_match(dfa_group_t *group, const uint8_t *str, uint64_t len,
+                    const dfa_group_opts_t *opts, dfa_result_t *out);
 
 /*
  * Inspection: the chunk maps L_k (Sec. 4.1) of every DFA of the group, as the

@@ -133,6 +133,7 @@ SIGNATURES = {
     "dfa_group_plan_chunks": (_I, [_P, _U64, _P, _P]),
     "dfa_group_workspace_size": (_I, [_P, _U64, _P, _P]),
     "dfa_group_match_async": (_I, [_P, _P, _U64, _P, _P, _P, _U64, _P]),
+    "dfa_group_match": (_I, [_P, _P, _U64, _P, _P]),
     "dfa_group_debug_chunk_maps": (_I, [_P, _P, _U64, _P, _P, _U32, _P, _P]),
     "dfa_server_create": (_I, [_U64, _U32, _P]),
     "dfa_server_set_opts": (_I, [_P, _P]),
@@ -561,21 +562,30 @@ class Group:
                                            workspace.numel(), _stream_ptr(stream)),
                "dfa_group_match_async")
 
-    def match(self, dev_data, num_chunks: int = 0, states_per_thread: int = 0,
+    def match(self, data, num_chunks: int = 0, states_per_thread: int = 0,
               ctas_per_sm: int = 0) -> list:
-        """Synchronous: one (status, final_state, accept) per DFA, in order
-        (final_state and accept are None for a failed test)."""
-        torch = _torch()
-        n = dev_data.numel()
-        ws = torch.empty(max(256, self.workspace_size(n, num_chunks, states_per_thread, ctas_per_sm)),
-                         dtype=torch.uint8, device=dev_data.device)
-        out = torch.zeros(12 * self.count, dtype=torch.uint8, device=dev_data.device)
-        self.match_async(dev_data, out, ws, None, num_chunks, states_per_thread, ctas_per_sm)
-        torch.cuda.current_stream().synchronize()
+        """Synchronous (dfa_group_match): data is bytes / numpy uint8 / a (pinned)
+        CPU tensor, or a CUDA uint8 tensor.  One (status, final_state, accept)
+        per DFA, in order (final_state and accept are None for a failed test)."""
+        if hasattr(data, "data_ptr"):
+            ptr, n, keep = data.data_ptr(), data.numel(), data
+            if data.is_cuda:   # the call runs on the legacy default stream
+                _torch().cuda.current_stream().synchronize()
+        else:
+            keep = np.ascontiguousarray(np.frombuffer(data, dtype=np.uint8)
+                                        if isinstance(data, (bytes, bytearray)) else
+                                        np.asarray(data, dtype=np.uint8))
+            ptr, n = keep.ctypes.data, keep.size
+        out = (Result * self.count)()
+        o = _gopts(num_chunks, states_per_thread, ctas_per_sm)
+        _check(lib().dfa_group_match(self._h, ptr if n else None, n, ctypes.byref(o), out),
+               "dfa_group_match")
+        del keep
         res = []
-        for f, a, st in results_from(out):
+        for r in out:
+            f, a, st = int(r.final_state), bool(r.accept), int(r.status)
             if st == EBOUNDS:
-                raise DfaError(st, "dfa_group_match_async (check at dfa_group.cu line %d)" % f)
+                raise DfaError(st, "dfa_group_match (check at dfa_group.cu line %d)" % f)
             res.append((st, f, a) if st == OK else (st, None, None))
         return res
 

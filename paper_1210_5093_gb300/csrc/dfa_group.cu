@@ -795,6 +795,13 @@ struct dfa_group_s {
     uint16_t* d_jmap = nullptr;
     uint16_t* d_jbad = nullptr;
     uint8_t* d_tables = nullptr;
+    // dfa_group_match's device buffers (input copy, workspace and results),
+    // grown as needed and reused; the mutex serialises those calls
+    std::mutex mu;
+    uint8_t* d_str = nullptr;
+    uint64_t str_cap = 0;
+    uint8_t* d_ws = nullptr;
+    uint64_t ws_cap = 0;
 };
 
 namespace {
@@ -1101,13 +1108,12 @@ void dfa_group_destroy(dfa_group_t* g) {
     if (!g) return;
     if (g->dev_block) {
         int cur = -1;
-        if (cudaGetDevice(&cur) == cudaSuccess && cur != g->device) {
-            cudaSetDevice(g->device);
-            cudaFree(g->dev_block);
-            cudaSetDevice(cur);
-        } else {
-            cudaFree(g->dev_block);
-        }
+        const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != g->device;
+        if (other) cudaSetDevice(g->device);
+        cudaFree(g->dev_block);
+        cudaFree(g->d_str);
+        cudaFree(g->d_ws);
+        if (other) cudaSetDevice(cur);
     }
     delete g;
 }
@@ -1247,6 +1253,55 @@ int dfa_group_match_async(const dfa_group_t* g, const uint8_t* dev_str, uint64_t
         l.p.work = opts ? reinterpret_cast<unsigned long long*>(opts->dev_work) : nullptr;
         l.p.dbg = nullptr;
         return issue(l, g->sb, opts, stream);
+    });
+}
+
+int dfa_group_match(dfa_group_t* g, const uint8_t* str, uint64_t len, const dfa_group_opts_t* opts,
+                    dfa_result_t* out) {
+    return dfam::no_throw([&]() -> int {
+        if (!g || !out || (len && !str)) return DFA_EINVAL;
+        if (!g->on_device) return DFA_EHOSTONLY;
+        bool on_dev = false;
+        if (len) {
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, str) == cudaSuccess)
+                on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+            cudaGetLastError();
+        }
+        GLaunch l;
+        int rc = plan_launch(g, len, opts, &l);
+        if (rc != DFA_OK) return rc;
+        std::lock_guard<std::mutex> lock(g->mu);
+        auto grow = [](uint8_t** p, uint64_t* cap, uint64_t need) -> int {
+            if (*cap >= need) return DFA_OK;
+            cudaFree(*p);
+            *p = nullptr;
+            *cap = 0;
+            if (cudaMalloc(p, need) != cudaSuccess) {
+                cudaGetLastError();
+                return DFA_ENOMEM;
+            }
+            *cap = need;
+            return DFA_OK;
+        };
+        const uint8_t* use = str;
+        if (len && !on_dev) {
+            if ((rc = grow(&g->d_str, &g->str_cap, len)) != DFA_OK) return rc;
+            if (cudaMemcpyAsync(g->d_str, str, len, cudaMemcpyHostToDevice, 0) != cudaSuccess)
+                return DFA_ECUDA;
+            use = g->d_str;
+        }
+        const uint64_t res_off = l.ws_total;
+        if ((rc = grow(&g->d_ws, &g->ws_cap, res_off + sizeof(dfa_result_t) * g->G)) != DFA_OK) return rc;
+        bind_ws(l, g->d_ws);
+        l.p.str = use;
+        l.p.results = reinterpret_cast<dfa_result_t*>(g->d_ws + res_off);
+        l.p.work = opts ? reinterpret_cast<unsigned long long*>(opts->dev_work) : nullptr;
+        l.p.dbg = nullptr;
+        if ((rc = issue(l, g->sb, opts, nullptr)) != DFA_OK) return rc;
+        if (cudaMemcpy(out, l.p.results, sizeof(dfa_result_t) * g->G, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return DFA_ECUDA;
+        return DFA_OK;
     });
 }
 

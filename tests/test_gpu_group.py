@@ -260,6 +260,22 @@ def test_group_sixteen_dfas(dm):
         assert np.array_equal(maps[i, :, :specs[i].num_states + 1].astype(np.uint32), want), i
 
 
+def test_group_host_input(dm, protein_group):
+    """dfa_group_match on host input (bytes, numpy, pinned and pageable CPU
+    tensors) gives the answers of device input and of the oracle; the group's
+    buffers grow and are reused across calls of different sizes."""
+    import torch
+    specs, _, g = protein_group
+    for n in (0, 1, 5_000, 3_000_001, 40_000):
+        x = gen.protein_text(80 + n % 7, n)
+        want = _expect(specs, x)
+        assert g.match(x) == want
+        assert g.match(bytes(x)) == want
+        assert g.match(torch.from_numpy(x)) == want
+        assert g.match(torch.from_numpy(x).pin_memory()) == want
+        assert g.match(torch.from_numpy(x).cuda()) == want
+
+
 def test_group_autotune(dm):
     """The tuner keeps one of the candidates as the group's default; answers
     with the tuned default equal the oracle's."""
