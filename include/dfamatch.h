@@ -534,8 +534,15 @@ int dfa_group_match_async(const dfa_group_t *group, const uint8_t *dev_str, uint
 
 /*
  * Synchronous form of dfa_group_match_async for host or device input: str is
- * len bytes of host memory (copied whole to the device first; pinned memory
- * copies fastest) or a device pointer; out[i] (host, count entries) receives
+ * len bytes of host memory or a device pointer.  Host input of at least
+ * 32 MiB is copied in segments (doubling from len/32, clamped to
+ * [16 MiB, 256 MiB], up to a quarter of the string) on a stream of the group
+ * while the earlier segments are matched on another: every segment after the
+ * first is matched from the sets of its lookahead byte and yields each DFA's
+ * state map of the segment, and Eq. (8) over those maps gives the answer
+ * (groups whose DFAs' |Q|+1, rounded up to 8, sum to at most 8192, and calls
+ * without num_chunks, dev_work or events; otherwise the string is copied
+ * whole first).  Pinned host memory copies fastest.  out[i] (host, count entries) receives
  * DFA i's result, its status DFA_ESYMBOL when the input holds a byte outside
  * DFA i's Sigma.  The call returns DFA_OK when the launch ran, whatever the
  * results' status.  The group keeps the input copy, workspace and results

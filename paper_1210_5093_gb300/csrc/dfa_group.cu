@@ -85,6 +85,13 @@ struct GPlan {
     dfa_result_t* results;    // [G]
     unsigned long long* work; // optional [1]: lookups of the launch
     uint16_t* dbg;            // optional [G * P * qe_max]: chunk maps L_k
+    // continuation of a longer string whose earlier bytes precede str on the
+    // device (chunk 0 takes the set of its lookahead byte str[-1], not {q0});
+    // with out_maps the launch publishes, per DFA g, the state map of its
+    // whole string, out_maps[g * seg_stride + x] = delta*(x, str), instead of
+    // a final state (results get only the status)
+    uint32_t cont;
+    uint16_t* out_maps;
 };
 
 // ------------------------------------------------------------ device helpers
@@ -150,10 +157,11 @@ __device__ __forceinline__ uint32_t g_slots(uint32_t size, uint32_t K) {
 }
 
 // Lookahead class of chunk k: the joint class of the byte before it, or
-// kStartSet for a chunk that starts the string.
+// kStartSet for a chunk that starts the string (a continuation's string
+// starts after the bytes of the earlier segments).
 __device__ __forceinline__ uint32_t g_lookahead(const GPlan& p, const uint16_t* jmap, uint32_t k,
                                                 uint64_t st) {
-    if (k == 0 || st == 0) return kStartSet;
+    if (k == 0 || st == 0) return p.cont ? (jmap[__ldg(p.str - 1)] & 0xFFu) : kStartSet;
     return jmap[__ldg(p.str + st - 1)] & 0xFFu;
 }
 
@@ -411,7 +419,19 @@ __device__ __forceinline__ uint32_t g_block_scan(uint32_t v, uint32_t* tmp) {
 __device__ void g_combine(const GPlan& p, const GDfa* gd, uint8_t* buf, uint32_t buf_bytes,
                           uint32_t* cur) {
     const uint32_t tid = threadIdx.x;
-    if (tid < p.G) cur[tid] = gd[tid].q0;
+    const bool maps = p.out_maps != nullptr;
+    // map mode: every state of every DFA is walked; their current values sit
+    // at the start of buf, the staged rows after them
+    uint16_t* walk = reinterpret_cast<uint16_t*>(buf);
+    const uint32_t nwalk = maps ? p.G * p.seg_stride : 0u;
+    if (maps) {
+        const uint32_t skip = g_align16(2u * nwalk);
+        buf += skip;
+        buf_bytes -= skip;
+        for (uint32_t f = tid; f < nwalk; f += kGThreads) walk[f] = (uint16_t)(f % p.seg_stride);
+    } else if (tid < p.G) {
+        cur[tid] = gd[tid].q0;
+    }
     const uint32_t row_bytes = p.seg_stride * 2u;   // a multiple of 16
     const uint32_t rows = p.grid * p.G;
     // rows per batch; the last kBatchMax bytes of buf hold the batch's valid flags
@@ -438,9 +458,23 @@ __device__ void g_combine(const GPlan& p, const GDfa* gd, uint8_t* buf, uint32_t
                              :: "r"(dst + 16u * i), "l"(src + i) : "memory");
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
-        if (tid < p.G) {
+        const uint16_t* m = reinterpret_cast<const uint16_t*>(buf);
+        if (maps) {
+            // thread f walks state x of DFA g (f = g * seg_stride + x) through
+            // this batch's rows of DFA g, in order of b
+            for (uint32_t f = tid; f < nwalk; f += kGThreads) {
+                const uint32_t g = f / p.seg_stride;
+                if (f - g * p.seg_stride >= gd[g].qe) continue;
+                uint32_t s = walk[f];
+                for (uint32_t r = r0 + (g + p.G - r0 % p.G) % p.G; r < r1; r += p.G) {
+                    if (!valid[r - r0]) continue;
+                    const uint32_t nx = m[(size_t)(r - r0) * p.seg_stride + s];
+                    if (GRP_OK(nx < gd[g].qe, p.err + g)) s = nx;
+                }
+                walk[f] = (uint16_t)s;
+            }
+        } else if (tid < p.G) {
             uint32_t s = cur[tid];
-            const uint16_t* m = reinterpret_cast<const uint16_t*>(buf);
             // rows r of this batch with r % G == tid, in increasing r (hence b)
             uint32_t r = r0 + (tid + p.G - r0 % p.G) % p.G;
             for (; r < r1; r += p.G) {
@@ -452,16 +486,45 @@ __device__ void g_combine(const GPlan& p, const GDfa* gd, uint8_t* buf, uint32_t
         }
         __syncthreads();
     }
+    if (maps)
+        for (uint32_t f = tid; f < nwalk; f += kGThreads) p.out_maps[f] = walk[f];
     if (tid < p.G) {
-        const uint32_t s = cur[tid];
         const uint32_t err = atomicOr(p.err + tid, 0u);
         dfa_result_t r;
+        const uint32_t s = maps ? 0u : cur[tid];
         r.final_state = g_final(err, s);
-        r.accept = err ? 0 : gd[tid].accept[s];
+        r.accept = (err || maps) ? 0 : gd[tid].accept[s];
         r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
         r.status = g_status(err);
         p.results[tid] = r;
     }
+}
+
+// Eq. (8) over the segments of one string, for every DFA of a group (thread g,
+// DFA g): the first segment's final state pushed through the state maps of the
+// later segments (maps + (s - 1) * G * seg_stride), their statuses combined.
+__global__ void k_group_compose(const dfa_result_t* seg_res, const uint16_t* maps, uint32_t nseg,
+                                uint32_t G, uint32_t seg_stride, const GDfa* gd, dfa_result_t* out) {
+    const uint32_t g = threadIdx.x;
+    if (g >= G) return;
+    uint32_t err = 0;
+    for (uint32_t s = 0; s < nseg; ++s) {
+        const int32_t st = seg_res[(size_t)s * G + g].status;
+        err |= st == DFA_OK ? 0u : (st == DFA_EBOUNDS ? 2u : 1u);
+    }
+    uint32_t q = seg_res[g].final_state;
+    const uint32_t qe = gd[g].qe;
+    if (err || q >= qe) q = 0;
+    for (uint32_t s = 1; s < nseg && !err; ++s) {
+        const uint32_t nx = maps[((size_t)(s - 1) * G + g) * seg_stride + q];
+        q = nx < qe ? nx : 0u;
+    }
+    dfa_result_t r;
+    r.final_state = err ? 0u : q;
+    r.accept = err ? 0 : gd[g].accept[q];
+    r.reserved[0] = r.reserved[1] = r.reserved[2] = 0;
+    r.status = err ? ((err & 2u) ? DFA_EBOUNDS : DFA_ESYMBOL) : DFA_OK;
+    out[g] = r;
 }
 
 template <int K, int SB>
@@ -802,6 +865,8 @@ struct dfa_group_s {
     uint64_t str_cap = 0;
     uint8_t* d_ws = nullptr;
     uint64_t ws_cap = 0;
+    cudaStream_t copy_stream = nullptr;   // host input copies of the pipelined path
+    cudaStream_t match_stream = nullptr;  // its launches
 };
 
 namespace {
@@ -935,6 +1000,120 @@ uint32_t host_next(const HostDfa& h, uint32_t c, uint32_t s) {
 }
 
 uint32_t set_size(const HostDfa& h, uint32_t c) { return h.iset_off[c + 1] - h.iset_off[c]; }
+
+// Host input of a group is copied in segments on a copy stream while the
+// earlier segments are matched: segment lengths double from len/32 (clamped
+// to [16 MiB, 256 MiB]) up to a quarter of the string.  Every segment after
+// the first is a continuation launch (its chunk 0 looks back into the bytes
+// before it) that publishes each DFA's state map of the segment; one thread
+// per DFA then applies those maps to the first segment's final state (Eq. 8).
+// Returns false (copy the string whole) when the string is too short or a
+// map-mode combine does not fit.
+bool group_segments(const dfa_group_s* g, uint64_t len, std::vector<uint64_t>* seg) {
+    const uint64_t MiB = 1ull << 20;
+    const uint64_t first = std::min<uint64_t>(std::max<uint64_t>(len / 32, 16 * MiB), 256 * MiB);
+    if (len < 2 * first || (uint64_t)g->G * g->seg_stride > 8192) return false;
+    const uint64_t cap = std::max<uint64_t>(first, len / 4);
+    seg->clear();
+    uint64_t at = 0, next = first;
+    while (at < len) {
+        uint64_t l = std::min<uint64_t>(next, len - at);
+        if (len - at - l < first / 2) l = len - at;  // no short last segment
+        seg->push_back(l);
+        at += l;
+        next = std::min<uint64_t>(2 * next, cap);
+    }
+    return seg->size() >= 2;
+}
+
+int grow_buf(uint8_t** p, uint64_t* cap, uint64_t need) {
+    if (*cap >= need) return DFA_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        cudaGetLastError();
+        return DFA_ENOMEM;
+    }
+    *cap = need;
+    return DFA_OK;
+}
+
+// The pipelined path of dfa_group_match (caller holds g->mu).
+int group_match_pipelined(dfa_group_s* g, const uint8_t* str, const std::vector<uint64_t>& seg,
+                          const dfa_group_opts_t* opts, dfa_result_t* out) {
+    const uint32_t nseg = (uint32_t)seg.size();
+    uint64_t len = 0;
+    for (uint64_t l : seg) len += l;
+    std::vector<GLaunch> ls(nseg);
+    uint64_t ws_need = 0;
+    for (uint32_t i = 0; i < nseg; ++i) {
+        int rc = plan_launch(g, seg[i], opts, &ls[i]);
+        if (rc != DFA_OK) return rc;
+        const GSmem L = g_layout(g->tbytes, ls[i].K, g->vcap_sum, ls[i].p.stage_bytes);
+        if (L.misc < g_align16(2u * g->G * g->seg_stride) + g->seg_stride * 2u + 1024u) return DFA_EINVAL;
+        ws_need = std::max(ws_need, ls[i].ws_total);
+    }
+    // workspace | results of every segment (nseg * G) | final results (G) | maps
+    const uint64_t res_off = ws_need;
+    const uint64_t fin_off = al256(res_off + sizeof(dfa_result_t) * nseg * g->G);
+    const uint64_t map_off = al256(fin_off + sizeof(dfa_result_t) * g->G);
+    const uint64_t total = map_off + 2ull * (nseg - 1) * g->G * g->seg_stride;
+    int rc;
+    if ((rc = grow_buf(&g->d_str, &g->str_cap, len)) != DFA_OK) return rc;
+    if ((rc = grow_buf(&g->d_ws, &g->ws_cap, total)) != DFA_OK) return rc;
+    if (!g->copy_stream &&
+        cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return DFA_ECUDA;
+    if (!g->match_stream &&
+        cudaStreamCreateWithFlags(&g->match_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return DFA_ECUDA;
+    std::vector<cudaEvent_t> ev(nseg, nullptr);
+    rc = DFA_OK;
+    for (uint32_t i = 0; i < nseg && rc == DFA_OK; ++i)
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) rc = DFA_ECUDA;
+    dfa_result_t* res = reinterpret_cast<dfa_result_t*>(g->d_ws + res_off);
+    dfa_result_t* fin = reinterpret_cast<dfa_result_t*>(g->d_ws + fin_off);
+    uint16_t* maps = reinterpret_cast<uint16_t*>(g->d_ws + map_off);
+    uint64_t at = 0;
+    for (uint32_t i = 0; i < nseg && rc == DFA_OK; ++i) {
+        if (cudaMemcpyAsync(g->d_str + at, str + at, seg[i], cudaMemcpyHostToDevice, g->copy_stream) !=
+                cudaSuccess ||
+            cudaEventRecord(ev[i], g->copy_stream) != cudaSuccess)
+            rc = DFA_ECUDA;
+        at += seg[i];
+    }
+    at = 0;
+    for (uint32_t i = 0; i < nseg && rc == DFA_OK; ++i) {
+        if (cudaStreamWaitEvent(g->match_stream, ev[i], 0) != cudaSuccess) {
+            rc = DFA_ECUDA;
+            break;
+        }
+        GLaunch& l = ls[i];
+        bind_ws(l, g->d_ws);  // launches on one stream run one after the other
+        l.p.str = g->d_str + at;
+        l.p.results = res + (size_t)i * g->G;
+        l.p.work = nullptr;
+        l.p.dbg = nullptr;
+        l.p.cont = i > 0 ? 1u : 0u;
+        l.p.out_maps = i > 0 ? maps + (size_t)(i - 1) * g->G * g->seg_stride : nullptr;
+        rc = issue(l, g->sb, nullptr, g->match_stream);
+        at += seg[i];
+    }
+    if (rc == DFA_OK) {
+        k_group_compose<<<1, 32, 0, g->match_stream>>>(res, maps, nseg, g->G, g->seg_stride, g->d_gd, fin);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(out, fin, sizeof(dfa_result_t) * g->G, cudaMemcpyDeviceToHost,
+                            g->match_stream) != cudaSuccess)
+            rc = DFA_ECUDA;
+    }
+    // wait for everything issued, whatever happened
+    if (cudaStreamSynchronize(g->copy_stream) != cudaSuccess) rc = DFA_ECUDA;
+    if (cudaStreamSynchronize(g->match_stream) != cudaSuccess) rc = DFA_ECUDA;
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    return rc;
+}
 
 }  // namespace
 
@@ -1113,6 +1292,8 @@ void dfa_group_destroy(dfa_group_t* g) {
         cudaFree(g->dev_block);
         cudaFree(g->d_str);
         cudaFree(g->d_ws);
+        if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+        if (g->match_stream) cudaStreamDestroy(g->match_stream);
         if (other) cudaSetDevice(cur);
     }
     delete g;
@@ -1272,27 +1453,21 @@ int dfa_group_match(dfa_group_t* g, const uint8_t* str, uint64_t len, const dfa_
         int rc = plan_launch(g, len, opts, &l);
         if (rc != DFA_OK) return rc;
         std::lock_guard<std::mutex> lock(g->mu);
-        auto grow = [](uint8_t** p, uint64_t* cap, uint64_t need) -> int {
-            if (*cap >= need) return DFA_OK;
-            cudaFree(*p);
-            *p = nullptr;
-            *cap = 0;
-            if (cudaMalloc(p, need) != cudaSuccess) {
-                cudaGetLastError();
-                return DFA_ENOMEM;
-            }
-            *cap = need;
-            return DFA_OK;
-        };
+        std::vector<uint64_t> seg;
+        if (len && !on_dev && !(opts && (opts->num_chunks || opts->dev_work ||
+                                          opts->match_begin_event || opts->match_end_event)) &&
+            group_segments(g, len, &seg))
+            return group_match_pipelined(g, str, seg, opts, out);
         const uint8_t* use = str;
         if (len && !on_dev) {
-            if ((rc = grow(&g->d_str, &g->str_cap, len)) != DFA_OK) return rc;
+            if ((rc = grow_buf(&g->d_str, &g->str_cap, len)) != DFA_OK) return rc;
             if (cudaMemcpyAsync(g->d_str, str, len, cudaMemcpyHostToDevice, 0) != cudaSuccess)
                 return DFA_ECUDA;
             use = g->d_str;
         }
         const uint64_t res_off = l.ws_total;
-        if ((rc = grow(&g->d_ws, &g->ws_cap, res_off + sizeof(dfa_result_t) * g->G)) != DFA_OK) return rc;
+        if ((rc = grow_buf(&g->d_ws, &g->ws_cap, res_off + sizeof(dfa_result_t) * g->G)) != DFA_OK)
+            return rc;
         bind_ws(l, g->d_ws);
         l.p.str = use;
         l.p.results = reinterpret_cast<dfa_result_t*>(g->d_ws + res_off);

@@ -276,6 +276,29 @@ def test_group_host_input(dm, protein_group):
         assert g.match(torch.from_numpy(x).cuda()) == want
 
 
+def test_group_host_input_pipelined(dm, protein_group):
+    """Host input of 32 MiB and more is copied in segments while the earlier
+    segments are matched (continuation launches and Eq. 8 over their state
+    maps): answers against the oracle, also with a byte outside Sigma at a
+    segment boundary (the last byte of one segment, the first of the next)."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    specs, _, g = protein_group
+    n = (64 << 20) + 7                      # segments of 16, 16, 16 and 16 MiB + 7
+    base = gen.protein_text(85, n)
+    cases = [base]
+    for pos in ((16 << 20) - 1, 32 << 20):
+        x = base.copy()
+        x[pos] = ord("#")
+        cases.append(x)
+    with ThreadPoolExecutor(len(specs)) as ex:
+        for x in cases:
+            want = list(ex.map(lambda s: oracle.Dfa.from_spec(s).run(x), specs))
+            assert g.match(x) == want
+            assert g.match(torch.from_numpy(x).pin_memory()) == want
+            assert g.match(torch.from_numpy(x).cuda()) == want
+
+
 def test_group_autotune(dm):
     """The tuner keeps one of the candidates as the group's default; answers
     with the tuned default equal the oracle's."""
