@@ -617,7 +617,8 @@ def group_config(args, dm, torch, lookup_peak, n: int = 1 << 30, reps: int = 5, 
            "l2": "input larger than L2, not flushed" if n > L2_BYTES else "input fits in L2",
            "e2e": {"value": round(total / e2e_s / 1e9, 3), "unit": "GB/s",
                    "h2d_bytes_per_step": n, "d2h_bytes_per_step": 12 * len(specs),
-                   "api": "dfa_group_match (pinned host buffer, copied whole)",
+                   "api": "dfa_group_match (pinned host buffer, copied in segments while "
+                          "earlier segments are matched)",
                    "calls": len(e2e_calls), "statistic": "median call time",
                    "call_ms": [round(x * 1e3, 2) for x in e2e_calls]}}
     if compare:
