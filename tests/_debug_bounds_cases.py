@@ -116,6 +116,19 @@ def main():
             assert got == want, (kw, got, want)
             checked += len(gspecs)
         g.close()
+    # a group on host input of 40 MiB: segments copied while earlier ones are
+    # matched (continuation launches publishing state maps, Eq. 8 over them)
+    gspecs = gen.protein_group_dfas(7, (16, 100, 480))
+    g = dm.Group([dm.Dfa.from_spec(s) for s in gspecs])
+    x = gen.protein_text(13, 40 << 20)
+    x[(16 << 20) - 1] = ord("#")       # the lookahead byte of the second segment
+    want = [oracle.Dfa.from_spec(s).run(x) for s in gspecs]
+    assert g.match(x) == want
+    x[(16 << 20) - 1] = ord("A")
+    want = [oracle.Dfa.from_spec(s).run(x) for s in gspecs]
+    assert g.match(x) == want
+    checked += 2 * len(gspecs)
+    g.close()
     print("debug-bounds parity ok: %d checks" % checked)
 
 
